@@ -1,0 +1,159 @@
+/*
+ * su3.h -- C ABI of libsu3: checkerboard heatbath sweeps of pure SU(3)
+ * lattice gauge theory with the Wilson action on a periodic 4D lattice, on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The operation is the one Berg & Wu time in "Fortran MPI Checkerboard Code
+ * for SU(3) Lattice Gauge Theory II" (arXiv:0904.1179):
+ *   - MCMC of pure SU(3) LGT with the Wilson action and periodic boundary
+ *     conditions (Sec. 1, Introduction);
+ *   - checkerboard updating: the links of one direction mu and one site parity
+ *     do not share staples and are updated together (Abstract; Sec. 1;
+ *     Appendix A, Eq. (mscb18): the checkerboard half-lattice storage);
+ *   - every SU(3) matrix update is a one-hit heatbath (Sec. 2.1, remark on
+ *     the 97.2% one-hit acceptance at beta = 5.7);
+ *   - a timing run performs `nequi` sweeps with no measurement and no I/O, and
+ *     the start configuration is created and timed separately (Sec. 2, the
+ *     timing programs cbsu3time2mpi{a,b,c}.f and the lswp switch).
+ * The paper leaves the update itself to its predecessor; this library reads
+ * it as: Wilson action S = beta * sum_P (1 - Re Tr U_P / 3); for each link the
+ * staple A (sum of the six three-link paths closing a plaquette with it);
+ * Cabibbo-Marinari over the SU(2) subgroups (0,1), (0,2), (1,2) in that order,
+ * each with one Kennedy-Pendleton proposal at alpha = 2*beta*k/3 that is
+ * accepted or leaves the subgroup unchanged; then Gram-Schmidt
+ * reunitarisation.  One sweep = for mu = 0..3: even sites, then odd sites.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = 64-bit seed,
+ * counter = (site, mu | subgroup<<2 | call<<4, sweep index low word,
+ * tag | (sweep index high word)<<4), tag 0 = update, 1 = hot start.  The
+ * sweep index is the only RNG state, so (seed, sweep count, links) is a
+ * complete checkpoint and results do not depend on launch configuration.
+ *
+ * Conventions for every entry point:
+ *   - Site x = (x0,x1,x2,x3), canonical index s = x0 + L0*(x1 + L1*(x2 + L2*x3)).
+ *   - Canonical host layout of a configuration (links_get/set):
+ *       double U[L3][L2][L1][L0][4 mu][3 row][3 col][2 re/im], x0 fastest.
+ *     The paper's direction 1 is mu = 0.  n_doubles = V * 4 * 18.
+ *   - Extents must be even and >= 2 (the checkerboard with periodic boundaries
+ *     needs even extents) and 4*V must fit in 31 bits.
+ *   - Every int-returning call returns SU3_OK (0) or a negative SU3_E* code;
+ *     su3_last_error() then describes the failure (thread-local, static
+ *     storage, valid until the next failing call on the same thread).
+ *   - No C++ exception crosses this boundary.  No call traps or asserts on the
+ *     device.
+ *   - A handle is not re-entrant: calls on one handle must not overlap in time
+ *     from several host threads.  Distinct handles are independent.
+ *   - The library owns all device memory of a handle (allocated at create,
+ *     freed at destroy).  Host pointers passed in stay owned by the caller and
+ *     are not retained after the call returns.
+ *   - Work is enqueued on the handle's stream.  Calls that return data to the
+ *     host (su3_plaquette, su3_links_get, su3_stats, ...) synchronise that
+ *     stream; asynchronous failures of earlier work are reported there.
+ */
+#ifndef SU3_H
+#define SU3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SU3_API __attribute__((visibility("default")))
+#else
+#define SU3_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct su3_lattice* su3_handle;
+
+enum { SU3_COLD = 0, SU3_HOT = 1 };
+enum { SU3_FP64 = 0, SU3_FP32_MIXED = 1 };
+enum {
+  SU3_OK = 0,
+  SU3_EINVAL = -1,   /* bad argument: NULL handle/pointer, odd or too large extent, beta <= 0, bad enum */
+  SU3_ENOMEM = -2,   /* device or pinned-host allocation failed */
+  SU3_ECUDA = -3,    /* a CUDA runtime call or kernel failed */
+  SU3_ETIMEOUT = -4, /* a bounded device-side wait gave up (batched sweep) */
+  SU3_ESIZE = -5     /* caller buffer size does not match the lattice */
+};
+
+/* Create a lattice of extents L0..L3 at coupling beta with the given Philox
+ * seed and start (SU3_COLD: every link the identity; SU3_HOT: Haar-random
+ * SU(3) links drawn from Philox tag 1).  Precision SU3_FP64 stores 18 reals
+ * per link in FP64 and computes in FP64.  On success *out receives the
+ * handle. */
+SU3_API int su3_create(int L0, int L1, int L2, int L3, double beta, uint64_t seed, int start, su3_handle* out);
+
+/* As su3_create, with a precision and a stream.
+ * precision SU3_FP32_MIXED: links stored as FP32 rows 0 and 1 (12 reals; row
+ *   2 = conj(row0 x row1) is rebuilt on every read), staple and SU(2)
+ *   heatbath in FP32, Gram-Schmidt of every updated link in FP64, plaquette
+ *   sums in FP64.  Uniforms use 23-bit FP32 draws (one Philox word each).
+ * cuda_stream: a cudaStream_t to enqueue all work on (for example PyTorch's
+ *   current stream); NULL lets the library create and own a stream.  A
+ *   caller-supplied stream must outlive the handle. */
+SU3_API int su3_create_ex(int L0, int L1, int L2, int L3, double beta, uint64_t seed, int start, int precision,
+                  void* cuda_stream, su3_handle* out);
+
+/* Release the handle and its device memory.  NULL is accepted and ignored. */
+SU3_API int su3_destroy(su3_handle h);
+
+/* Perform nsweeps full checkerboard sweeps (nsweeps >= 0).  Asynchronous on
+ * the handle's stream: each sweep replays a captured CUDA graph of eight
+ * half-sweep kernels followed by the sweep-counter increment. */
+SU3_API int su3_sweep(su3_handle h, int nsweeps);
+
+/* One checkerboard half-sweep: update every U_mu(x) with parity(x) == parity
+ * at the current sweep index, without advancing it.  A full sweep equals the
+ * eight calls mu = 0..3, parity 0 then 1, followed by
+ * su3_set_sweep_count(h, count + 1).  Asynchronous. */
+SU3_API int su3_half_sweep(su3_handle h, int mu, int parity);
+
+/* Mean plaquette (1/(6V)) sum_x sum_{mu<nu} (1/3) Re Tr U_mu(x) U_nu(x+mu)
+ * U_mu(x+nu)^+ U_nu(x)^+, products in the storage precision, accumulated in
+ * FP64 with a fixed-order reduction (the result is reproducible).
+ * Synchronises.  Returns NaN on failure (see su3_last_error). */
+SU3_API double su3_plaquette(su3_handle h);
+
+/* Copy the configuration to/from a caller-owned host buffer in the canonical
+ * layout (n_doubles must equal V*4*18, else SU3_ESIZE).  Synchronises.
+ * For SU3_FP32_MIXED, set rounds rows 0 and 1 to FP32 (round to nearest) and
+ * ignores row 2; get returns rows 0 and 1 exactly and row 2 computed in FP64
+ * as conj(row0 x row1).  Page-locked buffers transfer fastest. */
+SU3_API int su3_links_get(su3_handle h, double* host, size_t n_doubles);
+SU3_API int su3_links_set(su3_handle h, const double* host, size_t n_doubles);
+
+/* Sweep index (the RNG position).  With the seed and the links it is the full
+ * resume state. */
+SU3_API int su3_sweep_count(su3_handle h, uint64_t* out);
+SU3_API int su3_set_sweep_count(su3_handle h, uint64_t n);
+
+/* Acceptance statistics of the one-hit SU(2) proposals.  Counting is off by
+ * default (it costs a warp reduction and an atomic per warp); enabling resets
+ * the counters.  su3_stats synchronises and returns the totals since the last
+ * enable or reset. */
+SU3_API int su3_set_stats(su3_handle h, int enable);
+SU3_API int su3_stats(su3_handle h, uint64_t* accepted, uint64_t* proposed);
+
+/* Lattice properties of a handle. */
+SU3_API int su3_info(su3_handle h, int dims[4], double* beta, uint64_t* seed, int* precision);
+
+/* Threads per block of the half-sweep kernels (a multiple of 32 in
+ * [32, 256]); 0 restores the default.  Results do not depend on it: every
+ * link update is independent inside a half-sweep and its random numbers are
+ * keyed by its site. */
+SU3_API int su3_set_block_size(su3_handle h, int threads);
+
+/* Description of the last failure on the calling thread ("" if none). */
+SU3_API const char* su3_last_error(void);
+
+/* Library version string. */
+SU3_API const char* su3_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SU3_H */

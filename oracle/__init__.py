@@ -73,7 +73,7 @@ def _load():
         lib.oracle_update_links.argtypes = [_i32p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                             _i64p, ctypes.c_int64, ctypes.c_int, _f64p, _u64p]
         lib.oracle_updated_links.argtypes = [_i32p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
-                                             ctypes.c_int, _i64p, ctypes.c_int64, ctypes.c_int, _f64p, _f64p]
+                                             ctypes.c_int, _i64p, ctypes.c_int64, ctypes.c_int, _f64p, _f64p, _f64p]
         lib.oracle_gauge_transform.argtypes = [_i32p, ctypes.c_uint64, _f64p]
         lib.oracle_kp_draws.argtypes = [ctypes.c_double, ctypes.c_uint64, ctypes.c_int64, _f64p, _u8p]
         lib.oracle_kp_draws.restype = ctypes.c_int64
@@ -185,15 +185,19 @@ def update_links(L, beta, seed, t, mu, sites, U, f32=False):
     return int(st[0]), int(st[1])
 
 
-def updated_links(L, beta, seed, t, mu, sites, U, f32=False):
-    """Updated values of the listed links of direction mu, each from the unchanged U; shape (n, 3, 3, 2)."""
+def updated_links(L, beta, seed, t, mu, sites, U, f32=False, with_margins=False):
+    """Updated values of the listed links of direction mu, each from the unchanged U; shape (n, 3, 3, 2).
+
+    With with_margins, also returns (n, 3) accept margins u3^2 - (1 - delta/2) per subgroup
+    (accepted iff <= 0; NaN where the subgroup was skipped)."""
     _check_links(L, U)
     s = np.ascontiguousarray(np.asarray(sites, dtype=np.int64))
     out = np.empty((s.size, 3, 3, 2), dtype=np.float64)
+    marg = np.empty((s.size, 3), dtype=np.float64)
     _rc(_load().oracle_updated_links(_dims(L), float(beta), ctypes.c_uint64(seed), ctypes.c_uint64(t), int(mu),
                                      _ptr(s, ctypes.c_int64), s.size, int(bool(f32)), _ptr(U, ctypes.c_double),
-                                     _ptr(out, ctypes.c_double)))
-    return out
+                                     _ptr(out, ctypes.c_double), _ptr(marg, ctypes.c_double)))
+    return (out, marg) if with_margins else out
 
 
 def gauge_transform(L, seed, U):

@@ -392,7 +392,7 @@ static void su2_from_quaternion(const double a[4], cplx m[2][2])
 /* One Cabibbo-Marinari update of link (s, mu): three SU(2) subgroups, each
  * with a one-hit KP heatbath in the field of the staple A, then GS. */
 static mat3 update_link(const geom* g, const double* U, double beta, uint64_t seed, uint64_t t, int64_t s, int mu,
-                        int f32, uint64_t* stats)
+                        int f32, uint64_t* stats, double* margins)
 {
     static const int sub_rows[3][2] = {{0, 1}, {0, 2}, {1, 2}};
     mat3 A = staple(g, U, s, mu, f32);
@@ -409,7 +409,14 @@ static mat3 update_link(const geom* g, const double* U, double beta, uint64_t se
         k = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
         subgroup_uniforms(seed, s, mu, sub, t, f32, uu);
         if (stats) stats[1]++;
+        if (margins) margins[sub] = NAN;
         if (!(k > 1e-300)) continue; /* degenerate staple: measure zero, leave the subgroup */
+        if (margins) {
+            /* distance of the one-hit accept test from its threshold */
+            double c = cos(2.0 * ORACLE_PI * uu[1]);
+            double delta = -(log(uu[0]) + c * c * log(uu[2])) / (2.0 * beta * k / 3.0);
+            margins[sub] = uu[3] * uu[3] - (1.0 - 0.5 * delta);
+        }
         if (kp_one_hit(2.0 * beta * k / 3.0, uu, a)) {
             cplx y[2][2], v[2][2], vd[2][2], R[2][2];
             double rn[4];
@@ -551,7 +558,7 @@ int oracle_half_sweep(const int L[4], double beta, uint64_t seed, uint64_t t, in
     for (i = 0; i < g.V; i++) {
         int64_t s = reverse ? g.V - 1 - i : i;
         if (site_parity(L, s) != parity) continue;
-        store_link(U, s, mu, update_link(&g, U, beta, seed, t, s, mu, f32, stats), f32);
+        store_link(U, s, mu, update_link(&g, U, beta, seed, t, s, mu, f32, stats, NULL), f32);
     }
     geom_free(&g);
     return 0;
@@ -588,15 +595,18 @@ int oracle_update_links(const int L[4], double beta, uint64_t seed, uint64_t t, 
     for (i = 0; i < n; i++) {
         if (sites[i] < 0 || sites[i] >= g.V) { geom_free(&g); return -1; }
     }
-    for (i = 0; i < n; i++) store_link(U, sites[i], mu, update_link(&g, U, beta, seed, t, sites[i], mu, f32, stats), f32);
+    for (i = 0; i < n; i++) store_link(U, sites[i], mu, update_link(&g, U, beta, seed, t, sites[i], mu, f32, stats, NULL), f32);
     geom_free(&g);
     return 0;
 }
 
 /* Like oracle_update_links but returns the updated links in `out` (18 doubles
- * each) and leaves U untouched: every update sees the same configuration. */
+ * each) and leaves U untouched: every update sees the same configuration.
+ * margins (may be NULL) receives, per link and subgroup, u3^2 - (1 - delta/2):
+ * the one-hit proposal is accepted iff it is <= 0 (NaN for a skipped
+ * degenerate subgroup). */
 int oracle_updated_links(const int L[4], double beta, uint64_t seed, uint64_t t, int mu, const int64_t* sites, int64_t n,
-                         int f32, const double* U, double* out)
+                         int f32, const double* U, double* out, double* margins)
 {
     geom g;
     int64_t i;
@@ -606,7 +616,7 @@ int oracle_updated_links(const int L[4], double beta, uint64_t seed, uint64_t t,
         mat3 m;
         int r, c;
         if (sites[i] < 0 || sites[i] >= g.V) { geom_free(&g); return -1; }
-        m = update_link(&g, U, beta, seed, t, sites[i], mu, f32, NULL);
+        m = update_link(&g, U, beta, seed, t, sites[i], mu, f32, NULL, margins ? margins + 3 * i : NULL);
         if (f32) {
             for (r = 0; r < 2; r++)
                 for (c = 0; c < 3; c++) {

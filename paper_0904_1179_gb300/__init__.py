@@ -1,0 +1,259 @@
+"""GB300-native checkerboard SU(3) heatbath sweep (Berg & Wu, arXiv:0904.1179).
+
+Thin ctypes binding of libsu3 (``include/su3.h``): argument marshalling only.
+Every step of the sweep, the start configurations, the plaquette and the layout
+conversions run in the library's sm_103a kernels.  There is no CPU fallback:
+importing the binding without the built library, or calling it without a CUDA
+device, raises.
+
+The function names are those of the C ABI.  ``Lattice`` wraps a handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "SU3_COLD", "SU3_HOT", "SU3_FP64", "SU3_FP32_MIXED", "Su3Error", "load_library", "library_path",
+    "su3_create", "su3_create_ex", "su3_destroy", "su3_sweep", "su3_half_sweep", "su3_plaquette",
+    "su3_links_get", "su3_links_set", "su3_sweep_count", "su3_set_sweep_count", "su3_set_stats", "su3_stats",
+    "su3_info", "su3_set_block_size", "su3_last_error", "su3_version", "Lattice", "links_shape", "EXPORTS",
+]
+
+SU3_COLD, SU3_HOT = 0, 1
+SU3_FP64, SU3_FP32_MIXED = 0, 1
+SU3_OK, SU3_EINVAL, SU3_ENOMEM, SU3_ECUDA, SU3_ETIMEOUT, SU3_ESIZE = 0, -1, -2, -3, -4, -5
+_CODES = {SU3_EINVAL: "SU3_EINVAL", SU3_ENOMEM: "SU3_ENOMEM", SU3_ECUDA: "SU3_ECUDA",
+          SU3_ETIMEOUT: "SU3_ETIMEOUT", SU3_ESIZE: "SU3_ESIZE"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libsu3.so")
+_lock = threading.Lock()
+_lib = None
+
+_h = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+_pu64 = ctypes.POINTER(ctypes.c_uint64)
+_pd = ctypes.POINTER(ctypes.c_double)
+_pi = ctypes.POINTER(ctypes.c_int)
+
+# (name, restype, argtypes) of every C entry point declared in include/su3.h.
+EXPORTS = [
+    ("su3_create", ctypes.c_int, [ctypes.c_int] * 4 + [ctypes.c_double, _u64, ctypes.c_int, ctypes.POINTER(_h)]),
+    ("su3_create_ex", ctypes.c_int, [ctypes.c_int] * 4 + [ctypes.c_double, _u64, ctypes.c_int, ctypes.c_int,
+                                                            ctypes.c_void_p, ctypes.POINTER(_h)]),
+    ("su3_destroy", ctypes.c_int, [_h]),
+    ("su3_sweep", ctypes.c_int, [_h, ctypes.c_int]),
+    ("su3_half_sweep", ctypes.c_int, [_h, ctypes.c_int, ctypes.c_int]),
+    ("su3_plaquette", ctypes.c_double, [_h]),
+    ("su3_links_get", ctypes.c_int, [_h, _pd, ctypes.c_size_t]),
+    ("su3_links_set", ctypes.c_int, [_h, _pd, ctypes.c_size_t]),
+    ("su3_sweep_count", ctypes.c_int, [_h, _pu64]),
+    ("su3_set_sweep_count", ctypes.c_int, [_h, _u64]),
+    ("su3_set_stats", ctypes.c_int, [_h, ctypes.c_int]),
+    ("su3_stats", ctypes.c_int, [_h, _pu64, _pu64]),
+    ("su3_info", ctypes.c_int, [_h, _pi, _pd, _pu64, _pi]),
+    ("su3_set_block_size", ctypes.c_int, [_h, ctypes.c_int]),
+    ("su3_last_error", ctypes.c_char_p, []),
+    ("su3_version", ctypes.c_char_p, []),
+]
+
+
+class Su3Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_CODES.get(code, str(code)), msg))
+        self.code = code
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libsu3.so (built by paper_0904_1179_gb300.build); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError("libsu3.so is not built (run `python -m paper_0904_1179_gb300.build` or "
+                              "__graft_entry__.build()); there is no CPU fallback")
+        lib = ctypes.CDLL(_LIB_PATH)
+        for name, res, args in EXPORTS:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != SU3_OK:
+        raise Su3Error(rc, su3_last_error())
+
+
+def su3_last_error() -> str:
+    return load_library().su3_last_error().decode()
+
+
+def su3_version() -> str:
+    return load_library().su3_version().decode()
+
+
+def su3_create(L0, L1, L2, L3, beta, seed, start):
+    h = _h()
+    _check(load_library().su3_create(L0, L1, L2, L3, beta, seed, start, ctypes.byref(h)))
+    return h
+
+
+def su3_create_ex(L0, L1, L2, L3, beta, seed, start, precision, cuda_stream=None):
+    """cuda_stream: a raw cudaStream_t (int), e.g. ``torch.cuda.current_stream().cuda_stream``, or None."""
+    h = _h()
+    _check(load_library().su3_create_ex(L0, L1, L2, L3, beta, seed, start, precision,
+                                        ctypes.c_void_p(cuda_stream or None), ctypes.byref(h)))
+    return h
+
+
+def su3_destroy(h):
+    _check(load_library().su3_destroy(h))
+
+
+def su3_sweep(h, nsweeps):
+    _check(load_library().su3_sweep(h, nsweeps))
+
+
+def su3_half_sweep(h, mu, parity):
+    _check(load_library().su3_half_sweep(h, mu, parity))
+
+
+def su3_plaquette(h) -> float:
+    v = load_library().su3_plaquette(h)
+    if v != v:  # NaN signals failure
+        raise Su3Error(SU3_ECUDA, su3_last_error())
+    return v
+
+
+def _host_buffer(buf, writable):
+    if not isinstance(buf, np.ndarray) or buf.dtype != np.float64 or not buf.flags.c_contiguous:
+        raise TypeError("links buffer must be a C-contiguous float64 numpy array")
+    if writable and not buf.flags.writeable:
+        raise TypeError("links buffer is read-only")
+    return buf.ctypes.data_as(_pd), buf.size
+
+
+def su3_links_get(h, out):
+    ptr, n = _host_buffer(out, True)
+    _check(load_library().su3_links_get(h, ptr, n))
+    return out
+
+
+def su3_links_set(h, links):
+    ptr, n = _host_buffer(links, False)
+    _check(load_library().su3_links_set(h, ptr, n))
+
+
+def su3_sweep_count(h) -> int:
+    v = ctypes.c_uint64()
+    _check(load_library().su3_sweep_count(h, ctypes.byref(v)))
+    return v.value
+
+
+def su3_set_sweep_count(h, n):
+    _check(load_library().su3_set_sweep_count(h, n))
+
+
+def su3_set_stats(h, enable):
+    _check(load_library().su3_set_stats(h, int(bool(enable))))
+
+
+def su3_stats(h):
+    a, p = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load_library().su3_stats(h, ctypes.byref(a), ctypes.byref(p)))
+    return a.value, p.value
+
+
+def su3_info(h):
+    dims = (ctypes.c_int * 4)()
+    beta = ctypes.c_double()
+    seed = ctypes.c_uint64()
+    prec = ctypes.c_int()
+    _check(load_library().su3_info(h, dims, ctypes.byref(beta), ctypes.byref(seed), ctypes.byref(prec)))
+    return tuple(dims), beta.value, seed.value, prec.value
+
+
+def su3_set_block_size(h, threads):
+    _check(load_library().su3_set_block_size(h, threads))
+
+
+def links_shape(L):
+    """Canonical host layout of a configuration: U[L3][L2][L1][L0][mu][row][col][re/im]."""
+    return (L[3], L[2], L[1], L[0], 4, 3, 3, 2)
+
+
+class Lattice:
+    """Owning wrapper of one su3 handle."""
+
+    def __init__(self, dims, beta, seed, start=SU3_HOT, precision=SU3_FP64, stream=None):
+        self.dims = tuple(int(x) for x in dims)
+        self.handle = su3_create_ex(*self.dims, float(beta), int(seed), int(start), int(precision), stream)
+        self.beta = float(beta)
+        self.seed = int(seed)
+        self.precision = int(precision)
+
+    def close(self):
+        if self.handle is not None:
+            su3_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def volume(self):
+        return int(np.prod(self.dims))
+
+    def sweep(self, n=1):
+        su3_sweep(self.handle, n)
+
+    def half_sweep(self, mu, parity):
+        su3_half_sweep(self.handle, mu, parity)
+
+    def plaquette(self):
+        return su3_plaquette(self.handle)
+
+    def get_links(self, out=None):
+        if out is None:
+            out = np.empty(links_shape(self.dims), dtype=np.float64)
+        return su3_links_get(self.handle, out)
+
+    def set_links(self, links):
+        su3_links_set(self.handle, np.ascontiguousarray(links, dtype=np.float64))
+
+    @property
+    def sweep_count(self):
+        return su3_sweep_count(self.handle)
+
+    @sweep_count.setter
+    def sweep_count(self, n):
+        su3_set_sweep_count(self.handle, int(n))
+
+    def set_stats(self, enable=True):
+        su3_set_stats(self.handle, enable)
+
+    def stats(self):
+        return su3_stats(self.handle)
+
+    def set_block_size(self, threads):
+        su3_set_block_size(self.handle, threads)

@@ -1,0 +1,361 @@
+// su3_api.cu -- host runtime of libsu3 and its C ABI (include/su3.h).
+//
+// A handle owns the device link store, the sweep counter (the RNG position),
+// the plaquette scratch, the acceptance counters, a staging buffer for layout
+// conversion and the instantiated CUDA graphs of one sweep.  The timing
+// programs of Berg & Wu (Sec. 2) run `nequi` sweeps with nothing else in the
+// loop; su3_sweep replays a graph of the eight half-sweeps for each of them.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "su3.h"
+#include "su3_kernels.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return fail(SU3_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(SU3_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SU3_CUDA(call, what)                   \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+constexpr int kDefaultThreads = 128;
+constexpr long long kChunkSites = 1LL << 16;  // layout-conversion chunk (37.7 MB of FP64 links)
+
+}  // namespace
+
+struct su3_lattice {
+  int L[4] = {0, 0, 0, 0};
+  long long V = 0;
+  double beta = 0.0;
+  uint64_t seed = 0;
+  int precision = SU3_FP64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* links = nullptr;
+  size_t link_bytes = 0;
+  uint64_t* d_sweep = nullptr;
+  uint64_t sweep_host = 0;
+  unsigned long long* d_stats = nullptr;
+  bool stats_on = false;
+  double* d_partials = nullptr;
+  double* d_plaq = nullptr;
+  double* h_plaq = nullptr;  // pinned
+  unsigned long long* h_stats = nullptr;  // pinned, 2 words
+  double* d_stage = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // indexed by stats_on
+  int threads = kDefaultThreads;
+  su3dev::Geometry geom{};
+  su3dev::PhiloxKey key{};
+};
+
+namespace {
+
+void drop_graphs(su3_lattice* h) {
+  for (auto& g : h->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+void release(su3_lattice* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
+  cudaFree(h->links);
+  cudaFree(h->d_sweep);
+  cudaFree(h->d_stats);
+  cudaFree(h->d_partials);
+  cudaFree(h->d_plaq);
+  cudaFree(h->d_stage);
+  cudaFreeHost(h->h_plaq);
+  cudaFreeHost(h->h_stats);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+HalfSweepArgs half_sweep_args(const su3_lattice* h, int parity) {
+  HalfSweepArgs a{};
+  a.geom = h->geom;
+  a.key = h->key;
+  a.parity = parity;
+  a.beta = h->beta;
+  a.inv_beta15 = (float)(1.5 / h->beta);
+  a.sweep = h->d_sweep;
+  a.links = h->links;
+  a.stats = h->d_stats;
+  return a;
+}
+
+int enqueue_sweep_body(su3_lattice* h) {
+  for (int mu = 0; mu < 4; ++mu)
+    for (int p = 0; p < 2; ++p)
+      SU3_CUDA(su3k_launch_half_sweep(half_sweep_args(h, p), mu, h->precision, h->stats_on, h->threads, h->stream),
+               "half-sweep launch");
+  SU3_CUDA(su3k_launch_increment(h->d_sweep, 1, h->stream), "sweep counter launch");
+  return SU3_OK;
+}
+
+int ensure_graph(su3_lattice* h) {
+  cudaGraphExec_t& exec = h->graph[h->stats_on ? 1 : 0];
+  if (exec) return SU3_OK;
+  cudaGraph_t graph = nullptr;
+  SU3_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
+  const int rc = enqueue_sweep_body(h);
+  const cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  if (rc != SU3_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "graph capture end");
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    exec = nullptr;
+    return cuda_fail(ei, "graph instantiate");
+  }
+  return SU3_OK;
+}
+
+int sync(su3_lattice* h, const char* what) {
+  SU3_CUDA(cudaStreamSynchronize(h->stream), what);
+  SU3_CUDA(cudaGetLastError(), what);
+  return SU3_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* su3_last_error(void) { return g_err; }
+
+const char* su3_version(void) { return "libsu3 1.0 (sm_103a)"; }
+
+int su3_create_ex(int L0, int L1, int L2, int L3, double beta, uint64_t seed, int start, int precision, void* cuda_stream,
+                  su3_handle* out) {
+  if (!out) return fail(SU3_EINVAL, "su3_create: out is NULL");
+  *out = nullptr;
+  const int L[4] = {L0, L1, L2, L3};
+  for (int mu = 0; mu < 4; ++mu)
+    if (L[mu] < 2 || (L[mu] & 1))
+      return fail(SU3_EINVAL, "su3_create: extent L%d = %d must be even and >= 2", mu, L[mu]);
+  const long long V = (long long)L0 * L1 * L2 * L3;
+  if (4 * V > 0x7fffffffLL) return fail(SU3_EINVAL, "su3_create: 4*V = %lld exceeds 2^31-1", 4 * V);
+  if (!(beta > 0.0) || !std::isfinite(beta)) return fail(SU3_EINVAL, "su3_create: beta must be finite and > 0");
+  if (start != SU3_COLD && start != SU3_HOT) return fail(SU3_EINVAL, "su3_create: bad start %d", start);
+  if (precision != SU3_FP64 && precision != SU3_FP32_MIXED)
+    return fail(SU3_EINVAL, "su3_create: bad precision %d", precision);
+
+  su3_lattice* h = new (std::nothrow) su3_lattice;
+  if (!h) return fail(SU3_ENOMEM, "su3_create: host allocation failed");
+  for (int mu = 0; mu < 4; ++mu) h->L[mu] = L[mu];
+  h->V = V;
+  h->beta = beta;
+  h->seed = seed;
+  h->precision = precision;
+  h->geom.L0 = L0;
+  h->geom.L1 = L1;
+  h->geom.L2 = L2;
+  h->geom.L3 = L3;
+  h->geom.hL0 = L0 / 2;
+  h->geom.Vh = (int)(V / 2);
+  h->geom.s1 = L0;
+  h->geom.s2 = L0 * L1;
+  h->geom.s3 = L0 * L1 * L2;
+  h->key.k0 = (uint32_t)seed;
+  h->key.k1 = (uint32_t)(seed >> 32);
+
+  cudaError_t e;
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete h;
+      return cuda_fail(e, "su3_create: stream");
+    }
+    h->own_stream = true;
+  }
+  h->link_bytes = (size_t)V * 4 * (precision == SU3_FP64 ? 18 * sizeof(double) : 12 * sizeof(float));
+  const int nparts = su3k_plaquette_blocks(h->geom);
+  const long long chunk = V < kChunkSites ? V : kChunkSites;
+  if ((e = cudaMalloc(&h->links, h->link_bytes)) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_sweep, sizeof(uint64_t))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_stats, 2 * sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_partials, (size_t)nparts * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_plaq, sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_stage, (size_t)chunk * 4 * 18 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_plaq, sizeof(double))) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_stats, 2 * sizeof(unsigned long long))) != cudaSuccess) {
+    const int rc = cuda_fail(e, "su3_create: allocation");
+    cudaGetLastError();
+    release(h);
+    return rc;
+  }
+  int rc = SU3_OK;
+  if ((e = cudaMemsetAsync(h->d_sweep, 0, sizeof(uint64_t), h->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(unsigned long long), h->stream)) != cudaSuccess) {
+    rc = cuda_fail(e, "su3_create: memset");
+  }
+  if (rc == SU3_OK) {
+    InitArgs ia{h->geom, h->key, precision, h->links};
+    e = su3k_launch_init(ia, start == SU3_HOT, h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "su3_create: start configuration");
+  }
+  if (rc == SU3_OK) rc = sync(h, "su3_create");
+  if (rc != SU3_OK) {
+    release(h);
+    return rc;
+  }
+  *out = h;
+  return SU3_OK;
+}
+
+int su3_create(int L0, int L1, int L2, int L3, double beta, uint64_t seed, int start, su3_handle* out) {
+  return su3_create_ex(L0, L1, L2, L3, beta, seed, start, SU3_FP64, nullptr, out);
+}
+
+int su3_destroy(su3_handle h) {
+  release(h);
+  return SU3_OK;
+}
+
+int su3_sweep(su3_handle h, int nsweeps) {
+  if (!h) return fail(SU3_EINVAL, "su3_sweep: NULL handle");
+  if (nsweeps < 0) return fail(SU3_EINVAL, "su3_sweep: nsweeps < 0");
+  if (nsweeps == 0) return SU3_OK;
+  int rc = ensure_graph(h);
+  if (rc != SU3_OK) return rc;
+  cudaGraphExec_t exec = h->graph[h->stats_on ? 1 : 0];
+  for (int n = 0; n < nsweeps; ++n) SU3_CUDA(cudaGraphLaunch(exec, h->stream), "su3_sweep: graph launch");
+  h->sweep_host += (uint64_t)nsweeps;
+  return SU3_OK;
+}
+
+int su3_half_sweep(su3_handle h, int mu, int parity) {
+  if (!h) return fail(SU3_EINVAL, "su3_half_sweep: NULL handle");
+  if (mu < 0 || mu > 3 || parity < 0 || parity > 1) return fail(SU3_EINVAL, "su3_half_sweep: bad mu/parity");
+  SU3_CUDA(su3k_launch_half_sweep(half_sweep_args(h, parity), mu, h->precision, h->stats_on, h->threads, h->stream),
+           "su3_half_sweep");
+  return SU3_OK;
+}
+
+double su3_plaquette(su3_handle h) {
+  if (!h) {
+    fail(SU3_EINVAL, "su3_plaquette: NULL handle");
+    return NAN;
+  }
+  PlaqArgs a{h->geom, h->links, h->d_partials};
+  cudaError_t e = su3k_launch_plaquette(a, h->precision, h->d_plaq, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_plaq, h->d_plaq, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "su3_plaquette");
+    return NAN;
+  }
+  return *h->h_plaq;
+}
+
+int su3_links_get(su3_handle h, double* host, size_t n_doubles) {
+  if (!h || !host) return fail(SU3_EINVAL, "su3_links_get: NULL argument");
+  if (n_doubles != (size_t)h->V * 72) return fail(SU3_ESIZE, "su3_links_get: n = %zu, expected %lld", n_doubles, h->V * 72);
+  for (long long s0 = 0; s0 < h->V; s0 += kChunkSites) {
+    const long long n = (h->V - s0) < kChunkSites ? (h->V - s0) : kChunkSites;
+    ConvArgs a{h->geom, h->precision, s0, n, h->d_stage, h->links};
+    SU3_CUDA(su3k_launch_conv(a, false, h->stream), "su3_links_get: convert");
+    SU3_CUDA(cudaMemcpyAsync(host + s0 * 72, h->d_stage, (size_t)n * 72 * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream),
+             "su3_links_get: copy");
+  }
+  return sync(h, "su3_links_get");
+}
+
+int su3_links_set(su3_handle h, const double* host, size_t n_doubles) {
+  if (!h || !host) return fail(SU3_EINVAL, "su3_links_set: NULL argument");
+  if (n_doubles != (size_t)h->V * 72) return fail(SU3_ESIZE, "su3_links_set: n = %zu, expected %lld", n_doubles, h->V * 72);
+  for (long long s0 = 0; s0 < h->V; s0 += kChunkSites) {
+    const long long n = (h->V - s0) < kChunkSites ? (h->V - s0) : kChunkSites;
+    SU3_CUDA(cudaMemcpyAsync(h->d_stage, host + s0 * 72, (size_t)n * 72 * sizeof(double), cudaMemcpyHostToDevice,
+                             h->stream),
+             "su3_links_set: copy");
+    ConvArgs a{h->geom, h->precision, s0, n, h->d_stage, h->links};
+    SU3_CUDA(su3k_launch_conv(a, true, h->stream), "su3_links_set: convert");
+  }
+  return sync(h, "su3_links_set");
+}
+
+int su3_sweep_count(su3_handle h, uint64_t* out) {
+  if (!h || !out) return fail(SU3_EINVAL, "su3_sweep_count: NULL argument");
+  *out = h->sweep_host;
+  return SU3_OK;
+}
+
+int su3_set_sweep_count(su3_handle h, uint64_t n) {
+  if (!h) return fail(SU3_EINVAL, "su3_set_sweep_count: NULL handle");
+  SU3_CUDA(su3k_launch_set_counter(h->d_sweep, n, h->stream), "su3_set_sweep_count");
+  h->sweep_host = n;
+  return SU3_OK;
+}
+
+int su3_set_stats(su3_handle h, int enable) {
+  if (!h) return fail(SU3_EINVAL, "su3_set_stats: NULL handle");
+  h->stats_on = enable != 0;
+  if (h->stats_on)
+    SU3_CUDA(cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(unsigned long long), h->stream), "su3_set_stats");
+  return SU3_OK;
+}
+
+int su3_stats(su3_handle h, uint64_t* accepted, uint64_t* proposed) {
+  if (!h || !accepted || !proposed) return fail(SU3_EINVAL, "su3_stats: NULL argument");
+  SU3_CUDA(cudaMemcpyAsync(h->h_stats, h->d_stats, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream),
+           "su3_stats");
+  const int rc = sync(h, "su3_stats");
+  if (rc != SU3_OK) return rc;
+  *accepted = h->h_stats[0];
+  *proposed = h->h_stats[1];
+  return SU3_OK;
+}
+
+int su3_info(su3_handle h, int dims[4], double* beta, uint64_t* seed, int* precision) {
+  if (!h) return fail(SU3_EINVAL, "su3_info: NULL handle");
+  if (dims)
+    for (int mu = 0; mu < 4; ++mu) dims[mu] = h->L[mu];
+  if (beta) *beta = h->beta;
+  if (seed) *seed = h->seed;
+  if (precision) *precision = h->precision;
+  return SU3_OK;
+}
+
+int su3_set_block_size(su3_handle h, int threads) {
+  if (!h) return fail(SU3_EINVAL, "su3_set_block_size: NULL handle");
+  if (threads == 0) threads = kDefaultThreads;
+  if (threads < 32 || threads > kMaxSweepThreads || (threads & 31))
+    return fail(SU3_EINVAL, "su3_set_block_size: %d is not a multiple of 32 in [32, %d]", threads, kMaxSweepThreads);
+  if (threads != h->threads) {
+    SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_set_block_size");
+    drop_graphs(h);
+    h->threads = threads;
+  }
+  return SU3_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,341 @@
+// su3_device.cuh -- device building blocks of the checkerboard SU(3) heatbath
+// sweep for sm_103a: complex 3x3 algebra on CUDA cores, Philox4x32-10, the
+// uniform maps, checkerboard index arithmetic and the link store.
+//
+// The method is the pure SU(3) Wilson-action checkerboard update of Berg & Wu
+// (arXiv:0904.1179, Abstract and Sec. 1): the links of one direction mu and one
+// site parity never share a staple, so each (mu, parity) half-sweep updates
+// all of its links in parallel, one thread per link.  Each update is a
+// one-hit heatbath (Sec. 2.1) built as Cabibbo-Marinari over the SU(2)
+// subgroups (0,1), (0,2), (1,2) with the Kennedy-Pendleton sampler, followed
+// by Gram-Schmidt reunitarisation.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace su3dev {
+
+// ---------------------------------------------------------------------------
+// Link store.  Half-lattice structure of arrays, one array per (mu, parity,
+// component group), indexed by the checkerboard half index h = s / 2 where
+// s = x0 + L0*(x1 + L1*(x2 + L2*x3)) and L0 is even, so each parity holds
+// exactly one site of every pair (2h, 2h+1).
+//   FP64:       double2 [4 mu][2 parity][9 entries (row*3+col)][Vh]
+//   FP32-mixed: float4  [4 mu][2 parity][3 groups][Vh], rows 0 and 1 only:
+//               g0 = (u00, u01), g1 = (u02, u10), g2 = (u11, u12) as re,im pairs.
+// ---------------------------------------------------------------------------
+constexpr int kEntriesF64 = 9;
+constexpr int kGroupsF32 = 3;
+
+// Philox4x32-10 constants (Salmon, Moraes, Dror, Shaw, SC'11).
+constexpr uint32_t kPhiloxMulA = 0xD2511F53u;
+constexpr uint32_t kPhiloxMulB = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxWeylA = 0x9E3779B9u;
+constexpr uint32_t kPhiloxWeylB = 0xBB67AE85u;
+
+// RNG stream tags (fourth counter word, low 4 bits).
+constexpr uint32_t kTagUpdate = 0u;
+constexpr uint32_t kTagHotStart = 1u;
+
+struct Geometry {
+  int L0, L1, L2, L3;
+  int hL0;      // L0 / 2
+  int Vh;       // V / 2
+  int s1, s2, s3;  // strides of x1, x2, x3 in the canonical index: L0, L0*L1, L0*L1*L2
+};
+
+struct PhiloxKey {
+  uint32_t k0, k1;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 block function.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key) {
+  uint32_t k0 = key.k0, k1 = key.k1;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += kPhiloxWeylA;
+      k1 += kPhiloxWeylB;
+    }
+    const uint32_t lo_a = kPhiloxMulA * c.x;
+    const uint32_t hi_a = __umulhi(kPhiloxMulA, c.x);
+    const uint32_t lo_b = kPhiloxMulB * c.z;
+    const uint32_t hi_b = __umulhi(kPhiloxMulB, c.z);
+    c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+  }
+  return c;
+}
+
+// Counter of draw `w1` (= mu | sub<<2 | call<<4) of site s at sweep t.
+__device__ __forceinline__ uint4 rng_counter(uint32_t site, uint32_t w1, uint64_t t, uint32_t tag) {
+  return make_uint4(site, w1, (uint32_t)t, tag | ((uint32_t)(t >> 32) << 4));
+}
+
+// Uniform in [2^-53, 1-2^-53]: 52 bits (a<<20 | b>>12) centred in its bin.
+__device__ __forceinline__ double u01_f64(uint32_t a, uint32_t b) {
+  const uint64_t x = ((uint64_t)a << 20) | (uint64_t)(b >> 12);
+  return ((double)x + 0.5) * 0x1p-52;
+}
+
+// Uniform in [2^-24, 1-2^-24]: 23 bits centred in the bin, exact in float.
+__device__ __forceinline__ float u01_f32(uint32_t a) {
+  return ((float)(a >> 9) + 0.5f) * 0x1p-23f;
+}
+
+// ---------------------------------------------------------------------------
+// Complex numbers and 3x3 matrices held in registers.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct cx {
+  T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> mk(T re, T im) {
+  cx<T> r;
+  r.re = re;
+  r.im = im;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ cx<T> conj(cx<T> a) {
+  return mk(a.re, -a.im);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> add(cx<T> a, cx<T> b) {
+  return mk(a.re + b.re, a.im + b.im);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> mul(cx<T> a, cx<T> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+// acc + a*b
+template <typename T>
+__device__ __forceinline__ cx<T> mac(cx<T> acc, cx<T> a, cx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+// acc + a*conj(b)
+template <typename T>
+__device__ __forceinline__ cx<T> mac_cb(cx<T> acc, cx<T> a, cx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(-a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+// acc + conj(a)*b
+template <typename T>
+__device__ __forceinline__ cx<T> mac_ca(cx<T> acc, cx<T> a, cx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+
+template <typename T>
+struct mat3 {
+  cx<T> e[3][3];
+};
+
+// Row 2 of an SU(3) matrix from rows 0 and 1: conj(row0 x row1).
+template <typename T>
+__device__ __forceinline__ void complete_row2(mat3<T>& m) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int a = (k + 1) % 3, b = (k + 2) % 3;
+    cx<T> v = mul(m.e[0][a], m.e[1][b]);
+    v = mac(v, mk(-m.e[0][b].re, -m.e[0][b].im), m.e[1][a]);
+    m.e[2][k] = conj(v);
+  }
+}
+
+// Rows 0,1 of X * Y^+ (Y complete).
+template <typename T>
+__device__ __forceinline__ void mul_nd_rows01(const mat3<T>& X, const mat3<T>& Y, mat3<T>& Z) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cx<T> s = mk(T(0), T(0));
+#pragma unroll
+      for (int j = 0; j < 3; ++j) s = mac_cb(s, X.e[i][j], Y.e[k][j]);
+      Z.e[i][k] = s;
+    }
+}
+
+// Rows 0,1 of X * Y (Y complete).
+template <typename T>
+__device__ __forceinline__ void mul_nn_rows01(const mat3<T>& X, const mat3<T>& Y, mat3<T>& Z) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cx<T> s = mk(T(0), T(0));
+#pragma unroll
+      for (int j = 0; j < 3; ++j) s = mac(s, X.e[i][j], Y.e[j][k]);
+      Z.e[i][k] = s;
+    }
+}
+
+// Rows 0,1 of X^+ * Y (X and Y complete).
+template <typename T>
+__device__ __forceinline__ void mul_dn_rows01(const mat3<T>& X, const mat3<T>& Y, mat3<T>& Z) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cx<T> s = mk(T(0), T(0));
+#pragma unroll
+      for (int j = 0; j < 3; ++j) s = mac_ca(s, X.e[j][i], Y.e[j][k]);
+      Z.e[i][k] = s;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void acc_full(mat3<T>& A, const mat3<T>& B) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) A.e[i][k] = add(A.e[i][k], B.e[i][k]);
+}
+
+// ---------------------------------------------------------------------------
+// Checkerboard geometry.  A thread owns half index h and parity p; its site
+// has x0 = 2*(h mod hL0) + ((p + x1 + x2 + x3) & 1).
+// ---------------------------------------------------------------------------
+struct Site {
+  int x0, x1, x2, x3;
+  int r;  // x1 + L1*(x2 + L2*x3)
+};
+
+__device__ __forceinline__ Site site_of(const Geometry& g, int h, int p) {
+  Site st;
+  const int r = h / g.hL0;
+  const int x0e = 2 * (h - r * g.hL0);
+  st.r = r;
+  const int q = r / g.L1;
+  st.x1 = r - q * g.L1;
+  st.x3 = q / g.L2;
+  st.x2 = q - st.x3 * g.L2;
+  st.x0 = x0e + ((p + st.x1 + st.x2 + st.x3) & 1);
+  return st;
+}
+
+__device__ __forceinline__ int canon(const Geometry& g, const Site& s) { return s.x0 + g.L0 * s.r; }
+
+// Half index of the neighbour x + d*nu-hat (d = +1 or -1), periodic.
+__device__ __forceinline__ int nb_half(const Geometry& g, const Site& s, int nu, int d) {
+  int x0 = s.x0, r = s.r;
+  if (nu == 0) {
+    x0 += d;
+    x0 = x0 < 0 ? x0 + g.L0 : (x0 >= g.L0 ? x0 - g.L0 : x0);
+  } else if (nu == 1) {
+    const int x = s.x1 + d;
+    r += (x < 0 ? g.L1 - 1 : (x >= g.L1 ? 1 - g.L1 : d));
+  } else if (nu == 2) {
+    const int x = s.x2 + d;
+    r += g.L1 * (x < 0 ? g.L2 - 1 : (x >= g.L2 ? 1 - g.L2 : d));
+  } else {
+    const int x = s.x3 + d;
+    r += g.L1 * g.L2 * (x < 0 ? g.L3 - 1 : (x >= g.L3 ? 1 - g.L3 : d));
+  }
+  return (x0 >> 1) + g.hL0 * r;
+}
+
+// Half index of x + nu-hat - rho-hat for nu != rho.
+__device__ __forceinline__ int nb_half2(const Geometry& g, const Site& s, int nu, int rho) {
+  Site t = s;
+  int* xs[4] = {&t.x0, &t.x1, &t.x2, &t.x3};
+  const int Ls[4] = {g.L0, g.L1, g.L2, g.L3};
+  int v = *xs[nu] + 1;
+  *xs[nu] = v >= Ls[nu] ? v - Ls[nu] : v;
+  v = *xs[rho] - 1;
+  *xs[rho] = v < 0 ? v + Ls[rho] : v;
+  t.r = t.x1 + g.L1 * (t.x2 + g.L2 * t.x3);
+  return (t.x0 >> 1) + g.hL0 * t.r;
+}
+
+// ---------------------------------------------------------------------------
+// Link loads and stores.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ size_t link_base(int mu, int p, int Vh, int ncomp) {
+  return ((size_t)(mu * 2 + p) * ncomp) * (size_t)Vh;
+}
+
+__device__ __forceinline__ mat3<double> load_f64(const double2* __restrict__ U, int mu, int p, int h, int Vh) {
+  mat3<double> m;
+  const double2* b = U + link_base(mu, p, Vh, kEntriesF64) + h;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    const double2 v = __ldg(b + (size_t)c * Vh);
+    m.e[c / 3][c % 3] = mk(v.x, v.y);
+  }
+  return m;
+}
+
+__device__ __forceinline__ void store_f64(double2* U, int mu, int p, int h, int Vh, const mat3<double>& m) {
+  double2* b = U + link_base(mu, p, Vh, kEntriesF64) + h;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) b[(size_t)c * Vh] = make_double2(m.e[c / 3][c % 3].re, m.e[c / 3][c % 3].im);
+}
+
+// Rows 0 and 1 only; the caller completes row 2 when it needs it.
+__device__ __forceinline__ mat3<float> load_f32_rows01(const float4* __restrict__ U, int mu, int p, int h, int Vh) {
+  mat3<float> m;
+  const float4* b = U + link_base(mu, p, Vh, kGroupsF32) + h;
+  const float4 g0 = __ldg(b), g1 = __ldg(b + Vh), g2 = __ldg(b + 2 * (size_t)Vh);
+  m.e[0][0] = mk(g0.x, g0.y);
+  m.e[0][1] = mk(g0.z, g0.w);
+  m.e[0][2] = mk(g1.x, g1.y);
+  m.e[1][0] = mk(g1.z, g1.w);
+  m.e[1][1] = mk(g2.x, g2.y);
+  m.e[1][2] = mk(g2.z, g2.w);
+  return m;
+}
+
+__device__ __forceinline__ mat3<float> load_f32(const float4* __restrict__ U, int mu, int p, int h, int Vh) {
+  mat3<float> m = load_f32_rows01(U, mu, p, h, Vh);
+  complete_row2(m);
+  return m;
+}
+
+__device__ __forceinline__ void store_f32_rows01(float4* U, int mu, int p, int h, int Vh, float r[12]) {
+  float4* b = U + link_base(mu, p, Vh, kGroupsF32) + h;
+  b[0] = make_float4(r[0], r[1], r[2], r[3]);
+  b[Vh] = make_float4(r[4], r[5], r[6], r[7]);
+  b[2 * (size_t)Vh] = make_float4(r[8], r[9], r[10], r[11]);
+}
+
+// ---------------------------------------------------------------------------
+// Gram-Schmidt reunitarisation in FP64 of rows 0 and 1 (row 2 follows as
+// conj(row0 x row1)).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void gram_schmidt_rows01(cx<double> r0[3], cx<double> r1[3]) {
+  double n0 = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) n0 = fma(r0[k].re, r0[k].re, fma(r0[k].im, r0[k].im, n0));
+  const double i0 = 1.0 / sqrt(n0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r0[k] = mk(r0[k].re * i0, r0[k].im * i0);
+  cx<double> d = mk(0.0, 0.0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d = mac_ca(d, r0[k], r1[k]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r1[k] = mac(r1[k], mk(-d.re, -d.im), r0[k]);
+  double n1 = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) n1 = fma(r1[k].re, r1[k].re, fma(r1[k].im, r1[k].im, n1));
+  const double i1 = 1.0 / sqrt(n1);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r1[k] = mk(r1[k].re * i1, r1[k].im * i1);
+}
+
+}  // namespace su3dev

@@ -1,0 +1,598 @@
+// su3_kernels.cu -- sm_103a kernels of the checkerboard SU(3) heatbath sweep.
+//
+// One thread updates one link U_mu(x) of the half-sweep (mu, parity): it
+// gathers the six-staple sum from the 18 neighbouring links, runs the one-hit
+// Kennedy-Pendleton heatbath in the SU(2) subgroups (0,1), (0,2), (1,2)
+// (Cabibbo-Marinari), reunitarises in FP64 and stores the link.  Links of one
+// (mu, parity) never enter each other's staples (checkerboard updating,
+// Abstract and Sec. 1 of Berg & Wu, arXiv:0904.1179), so threads are
+// independent; the counter-based Philox stream makes the result independent of
+// the launch configuration.  The work is a 4D stencil of 3x3 complex products,
+// not a dense contraction, so it runs on the FP32/FP64 CUDA cores.
+#include "su3_kernels.h"
+
+#include "su3_device.cuh"
+
+using namespace su3dev;
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+template <typename T>
+__device__ __forceinline__ mat3<T> zero3() {
+  mat3<T> m;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) m.e[i][k] = mk(T(0), T(0));
+  return m;
+}
+
+// Link loader for the two storage forms.
+template <typename T>
+struct Store;
+
+template <>
+struct Store<double> {
+  __device__ __forceinline__ static mat3<double> load(const void* U, int mu, int p, int h, int Vh) {
+    return load_f64((const double2*)U, mu, p, h, Vh);
+  }
+};
+
+template <>
+struct Store<float> {
+  __device__ __forceinline__ static mat3<float> load(const void* U, int mu, int p, int h, int Vh) {
+    return load_f32((const float4*)U, mu, p, h, Vh);
+  }
+};
+
+// Six-staple sum A for U_mu(x), x = st of parity p:
+//   sum_{nu != mu} U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ + U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu).
+// Each three-link path is an SU(3) matrix, so only its rows 0 and 1 are
+// multiplied out and row 2 is completed as conj(row0 x row1).
+template <typename T, int MU>
+__device__ __forceinline__ mat3<T> staple(const Geometry& g, const void* U, const Site& st, int h, int p) {
+  const int q = p ^ 1;
+  mat3<T> A = zero3<T>();
+  const int h_pmu = nb_half(g, st, MU, +1);
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == MU) continue;
+    const int h_pnu = nb_half(g, st, nu, +1);
+    const int h_mnu = nb_half(g, st, nu, -1);
+    const int h_pmu_mnu = nb_half2(g, st, MU, nu);
+    {
+      const mat3<T> a = Store<T>::load(U, nu, q, h_pmu, g.Vh);  // U_nu(x+mu)
+      const mat3<T> b = Store<T>::load(U, MU, q, h_pnu, g.Vh);  // U_mu(x+nu)
+      mat3<T> t;
+      mul_nd_rows01(a, b, t);
+      const mat3<T> c = Store<T>::load(U, nu, p, h, g.Vh);  // U_nu(x)
+      mat3<T> f;
+      mul_nd_rows01(t, c, f);
+      complete_row2(f);
+      acc_full(A, f);
+    }
+    {
+      const mat3<T> d = Store<T>::load(U, nu, p, h_pmu_mnu, g.Vh);  // U_nu(x+mu-nu)
+      const mat3<T> e = Store<T>::load(U, MU, q, h_mnu, g.Vh);      // U_mu(x-nu)
+      mat3<T> hm;
+      mul_nn_rows01(e, d, hm);
+      complete_row2(hm);
+      const mat3<T> f = Store<T>::load(U, nu, q, h_mnu, g.Vh);  // U_nu(x-nu)
+      mat3<T> b;
+      mul_dn_rows01(hm, f, b);
+      complete_row2(b);
+      acc_full(A, b);
+    }
+  }
+  return A;
+}
+
+// 2x2 block of W = U A in rows/columns (i, j), projected on the SU(2) direction:
+// r = (Re(W_ii+W_jj), Im(W_ij+W_ji), Re(W_ij-W_ji), Im(W_ii-W_jj)) / 2.
+template <typename T>
+__device__ __forceinline__ void su2_projection(const mat3<T>& u, const mat3<T>& A, int i, int j, T r[4]) {
+  cx<T> wii = mk(T(0), T(0)), wij = wii, wji = wii, wjj = wii;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    wii = mac(wii, u.e[i][c], A.e[c][i]);
+    wij = mac(wij, u.e[i][c], A.e[c][j]);
+    wji = mac(wji, u.e[j][c], A.e[c][i]);
+    wjj = mac(wjj, u.e[j][c], A.e[c][j]);
+  }
+  r[0] = T(0.5) * (wii.re + wjj.re);
+  r[1] = T(0.5) * (wij.im + wji.im);
+  r[2] = T(0.5) * (wij.re - wji.re);
+  r[3] = T(0.5) * (wii.im - wjj.im);
+}
+
+// rows (i, j) of u <- R rows (i, j), R = Y V^+ with Y = m(a), V = m(v),
+// m(q) = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]].
+template <typename T>
+__device__ __forceinline__ void apply_su2(mat3<T>& u, int i, int j, const T a[4], const T v[4]) {
+  const cx<T> y00 = mk(a[0], a[3]), y01 = mk(a[2], a[1]), y10 = mk(-a[2], a[1]), y11 = mk(a[0], -a[3]);
+  const cx<T> v00 = mk(v[0], v[3]), v01 = mk(v[2], v[1]), v10 = mk(-v[2], v[1]), v11 = mk(v[0], -v[3]);
+  // (V^+)_{pq} = conj(V_{qp})
+  cx<T> R00 = mac_cb(mac_cb(mk(T(0), T(0)), y00, v00), y01, v01);
+  cx<T> R01 = mac_cb(mac_cb(mk(T(0), T(0)), y00, v10), y01, v11);
+  cx<T> R10 = mac_cb(mac_cb(mk(T(0), T(0)), y10, v00), y11, v01);
+  cx<T> R11 = mac_cb(mac_cb(mk(T(0), T(0)), y10, v10), y11, v11);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cx<T> ui = u.e[i][c], uj = u.e[j][c];
+    u.e[i][c] = mac(mul(R00, ui), R01, uj);
+    u.e[j][c] = mac(mul(R10, ui), R11, uj);
+  }
+}
+
+__device__ __forceinline__ int subrow_i(int sub) { return sub == 2 ? 1 : 0; }
+__device__ __forceinline__ int subrow_j(int sub) { return sub == 0 ? 1 : 2; }
+
+// ---------------------------------------------------------------------------
+// FP64 half-sweep.
+// ---------------------------------------------------------------------------
+template <int MU, bool STATS>
+__global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64(HalfSweepArgs args) {
+  const Geometry g = args.geom;
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  int accepted = 0;
+  if (h < g.Vh) {
+    const int p = args.parity;
+    const Site st = site_of(g, h, p);
+    const uint32_t s = (uint32_t)canon(g, st);
+    const uint64_t t = *args.sweep;
+    double2* U = (double2*)args.links;
+    const mat3<double> A = staple<double, MU>(g, U, st, h, p);
+    mat3<double> u = load_f64(U, MU, p, h, g.Vh);
+#pragma unroll
+    for (int sub = 0; sub < 3; ++sub) {
+      const int i = subrow_i(sub), j = subrow_j(sub);
+      double r[4];
+      su2_projection(u, A, i, j, r);
+      const double k = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+      double uu[6];
+#pragma unroll
+      for (int call = 0; call < 3; ++call) {
+        const uint4 w = philox4x32_10(rng_counter(s, (uint32_t)(MU | (sub << 2) | (call << 4)), t, kTagUpdate), args.key);
+        uu[2 * call] = u01_f64(w.x, w.y);
+        uu[2 * call + 1] = u01_f64(w.z, w.w);
+      }
+      if (!(k > 1e-300)) continue;
+      const double alpha = 2.0 * args.beta * k / 3.0;
+      const double c = cos(kTwoPi * uu[1]);
+      const double delta = -(log(uu[0]) + c * c * log(uu[2])) / alpha;
+      if (uu[3] * uu[3] > 1.0 - 0.5 * delta) continue;
+      const double a0 = 1.0 - delta;
+      double rho = 1.0 - a0 * a0;
+      rho = rho > 0.0 ? sqrt(rho) : 0.0;
+      const double ct = 1.0 - 2.0 * uu[4];
+      double sn = 1.0 - ct * ct;
+      sn = sn > 0.0 ? sqrt(sn) : 0.0;
+      double sphi, cphi;
+      sincos(kTwoPi * uu[5], &sphi, &cphi);
+      const double a[4] = {a0, rho * sn * cphi, rho * sn * sphi, rho * ct};
+      const double v[4] = {r[0] / k, r[1] / k, r[2] / k, r[3] / k};
+      apply_su2(u, i, j, a, v);
+      ++accepted;
+    }
+    cx<double> r0[3] = {u.e[0][0], u.e[0][1], u.e[0][2]};
+    cx<double> r1[3] = {u.e[1][0], u.e[1][1], u.e[1][2]};
+    gram_schmidt_rows01(r0, r1);
+    mat3<double> out;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      out.e[0][k] = r0[k];
+      out.e[1][k] = r1[k];
+    }
+    complete_row2(out);
+    store_f64(U, MU, p, h, g.Vh, out);
+  }
+  if (STATS) {
+    const unsigned m = __ballot_sync(0xffffffffu, h < g.Vh);
+    const int acc = __reduce_add_sync(0xffffffffu, accepted);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&args.stats[0], (unsigned long long)acc);
+      atomicAdd(&args.stats[1], 3ull * (unsigned long long)__popc(m));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32-mixed half-sweep: FP32 storage (rows 0,1), FP32 staple and heatbath,
+// FP64 Gram-Schmidt.
+// ---------------------------------------------------------------------------
+template <int MU, bool STATS>
+__global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f32(HalfSweepArgs args) {
+  const Geometry g = args.geom;
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  int accepted = 0;
+  if (h < g.Vh) {
+    const int p = args.parity;
+    const Site st = site_of(g, h, p);
+    const uint32_t s = (uint32_t)canon(g, st);
+    const uint64_t t = *args.sweep;
+    float4* U = (float4*)args.links;
+    const mat3<float> A = staple<float, MU>(g, U, st, h, p);
+    mat3<float> u = load_f32(U, MU, p, h, g.Vh);
+    const float inv_beta15 = args.inv_beta15;
+#pragma unroll
+    for (int sub = 0; sub < 3; ++sub) {
+      const int i = subrow_i(sub), j = subrow_j(sub);
+      float r[4];
+      su2_projection(u, A, i, j, r);
+      const float kk = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
+      const uint4 w0 = philox4x32_10(rng_counter(s, (uint32_t)(MU | (sub << 2)), t, kTagUpdate), args.key);
+      const uint4 w1 = philox4x32_10(rng_counter(s, (uint32_t)(MU | (sub << 2) | (1 << 4)), t, kTagUpdate), args.key);
+      if (!(kk > 1e-30f)) continue;  // degenerate staple (measure zero): leave the subgroup
+      const float ik = rsqrtf(kk);
+      // 1/alpha = 3 / (2 beta k)
+      const float ia = inv_beta15 * ik;
+      const float u0 = u01_f32(w0.x), u1 = u01_f32(w0.y), u2 = u01_f32(w0.z), u3 = u01_f32(w0.w);
+      const float cc = __cosf(fmaf(6.2831853f, u1, -3.14159265f));  // -cos(2 pi u1); only its square is used
+      const float delta = -(__logf(u0) + cc * cc * __logf(u2)) * ia;
+      if (u3 * u3 > 1.0f - 0.5f * delta) continue;
+      const float u4 = u01_f32(w1.x), u5 = u01_f32(w1.y);
+      const float a0 = 1.0f - delta;
+      const float rho = sqrtf(fmaxf(0.0f, delta * (2.0f - delta)));  // sqrt(1 - a0^2)
+      const float ct = 1.0f - 2.0f * u4;
+      const float sn = 2.0f * sqrtf(u4 * (1.0f - u4));  // sqrt(1 - ct^2)
+      float sphi, cphi;
+      __sincosf(fmaf(6.2831853f, u5, -3.14159265f), &sphi, &cphi);  // angle 2 pi u5 - pi
+      const float rs = -rho * sn;                                     // undo the shift by pi
+      const float a[4] = {a0, rs * cphi, rs * sphi, rho * ct};
+      const float v[4] = {r[0] * ik, r[1] * ik, r[2] * ik, r[3] * ik};
+      apply_su2(u, i, j, a, v);
+      ++accepted;
+    }
+    cx<double> r0[3], r1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      r0[k] = mk((double)u.e[0][k].re, (double)u.e[0][k].im);
+      r1[k] = mk((double)u.e[1][k].re, (double)u.e[1][k].im);
+    }
+    gram_schmidt_rows01(r0, r1);
+    float o[12];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      o[2 * k] = (float)r0[k].re;
+      o[2 * k + 1] = (float)r0[k].im;
+      o[6 + 2 * k] = (float)r1[k].re;
+      o[6 + 2 * k + 1] = (float)r1[k].im;
+    }
+    store_f32_rows01(U, MU, p, h, g.Vh, o);
+  }
+  if (STATS) {
+    const unsigned m = __ballot_sync(0xffffffffu, h < g.Vh);
+    const int acc = __reduce_add_sync(0xffffffffu, accepted);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&args.stats[0], (unsigned long long)acc);
+      atomicAdd(&args.stats[1], 3ull * (unsigned long long)__popc(m));
+    }
+  }
+}
+
+__global__ void k_increment(uint64_t* counter, uint64_t n) { *counter += n; }
+__global__ void k_set_counter(uint64_t* counter, uint64_t n) { *counter = n; }
+
+// ---------------------------------------------------------------------------
+// Start configurations.
+// ---------------------------------------------------------------------------
+__global__ void k_cold_start(InitArgs args) {
+  const Geometry g = args.geom;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // over 8 * Vh (mu, parity, h)
+  if (idx >= 8 * g.Vh) return;
+  const int mp = idx / g.Vh, h = idx - mp * g.Vh;
+  const int mu = mp >> 1, p = mp & 1;
+  if (args.precision == 0) {
+    mat3<double> m = zero3<double>();
+    m.e[0][0] = m.e[1][1] = m.e[2][2] = mk(1.0, 0.0);
+    store_f64((double2*)args.links, mu, p, h, g.Vh, m);
+  } else {
+    float o[12] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f};
+    store_f32_rows01((float4*)args.links, mu, p, h, g.Vh, o);
+  }
+}
+
+// Haar SU(3): two complex Gaussian rows (Box-Muller on Philox tag 1 words,
+// counter (s, mu | call<<4, 0, 1), call = 0..5), Gram-Schmidt, row 2 completed.
+__global__ void k_hot_start(InitArgs args) {
+  const Geometry g = args.geom;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 8 * g.Vh) return;
+  const int mp = idx / g.Vh, h = idx - mp * g.Vh;
+  const int mu = mp >> 1, p = mp & 1;
+  const Site st = site_of(g, h, p);
+  const uint32_t s = (uint32_t)canon(g, st);
+  double gz[12];
+#pragma unroll
+  for (int call = 0; call < 6; ++call) {
+    const uint4 w = philox4x32_10(rng_counter(s, (uint32_t)(mu | (call << 4)), 0, kTagHotStart), args.key);
+    const double ua = u01_f64(w.x, w.y), ub = u01_f64(w.z, w.w);
+    const double rad = sqrt(-2.0 * log(ua));
+    double sn, cs;
+    sincos(kTwoPi * ub, &sn, &cs);
+    gz[2 * call] = rad * cs;
+    gz[2 * call + 1] = rad * sn;
+  }
+  cx<double> r0[3], r1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    r0[k] = mk(gz[2 * k], gz[2 * k + 1]);
+    r1[k] = mk(gz[6 + 2 * k], gz[6 + 2 * k + 1]);
+  }
+  gram_schmidt_rows01(r0, r1);
+  if (args.precision == 0) {
+    mat3<double> m;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      m.e[0][k] = r0[k];
+      m.e[1][k] = r1[k];
+    }
+    complete_row2(m);
+    store_f64((double2*)args.links, mu, p, h, g.Vh, m);
+  } else {
+    float o[12];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      o[2 * k] = (float)r0[k].re;
+      o[2 * k + 1] = (float)r0[k].im;
+      o[6 + 2 * k] = (float)r1[k].re;
+      o[6 + 2 * k + 1] = (float)r1[k].im;
+    }
+    store_f32_rows01((float4*)args.links, mu, p, h, g.Vh, o);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Plaquette: one thread per site, six planes, FP64 accumulation, fixed-order
+// block reduction into partials[blockIdx.x], then one block sums the partials.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ mat3<T> load_any(const void* U, int mu, int p, int h, int Vh);
+template <>
+__device__ __forceinline__ mat3<double> load_any<double>(const void* U, int mu, int p, int h, int Vh) {
+  return load_f64((const double2*)U, mu, p, h, Vh);
+}
+template <>
+__device__ __forceinline__ mat3<float> load_any<float>(const void* U, int mu, int p, int h, int Vh) {
+  return load_f32((const float4*)U, mu, p, h, Vh);
+}
+
+// Re Tr(X Y^+) with X = U_mu(x) U_nu(x+mu), Y = U_nu(x) U_mu(x+nu).
+template <typename T>
+__device__ __forceinline__ double plaq_site(const Geometry& g, const void* U, const Site& st, int h, int p) {
+  const int q = p ^ 1;
+  double sum = 0.0;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+    for (int nu = mu + 1; nu < 4; ++nu) {
+      const mat3<T> a = load_any<T>(U, mu, p, h, g.Vh);
+      const mat3<T> b = load_any<T>(U, nu, q, nb_half(g, st, mu, +1), g.Vh);
+      const mat3<T> c = load_any<T>(U, nu, p, h, g.Vh);
+      const mat3<T> d = load_any<T>(U, mu, q, nb_half(g, st, nu, +1), g.Vh);
+      T tr = T(0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          cx<T> x = mk(T(0), T(0)), y = x;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            x = mac(x, a.e[i][j], b.e[j][k]);
+            y = mac(y, c.e[i][j], d.e[j][k]);
+          }
+          tr = fma(x.re, y.re, tr);
+          tr = fma(x.im, y.im, tr);
+        }
+      sum += (double)tr;
+    }
+  return sum;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_plaquette_partial(PlaqArgs args) {
+  const Geometry g = args.geom;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // over 2 * Vh: (parity, h)
+  double v = 0.0;
+  if (idx < 2 * g.Vh) {
+    const int p = idx >= g.Vh ? 1 : 0;
+    const int h = idx - p * g.Vh;
+    const Site st = site_of(g, h, p);
+    v = plaq_site<T>(g, args.links, st, h, p);
+  }
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x >> 5;
+    double w = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) args.partials[blockIdx.x] = w;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_plaquette_final(const double* partials, int n, double scale, double* out) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += partials[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) *out = w * scale;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Canonical host layout <-> device store, for a chunk of sites [s_begin, s_begin + n).
+// Canonical: double[s][mu][row][col][re/im].
+// ---------------------------------------------------------------------------
+// Row 2 from FP32 rows 0,1 in FP64 with every product and sum rounded
+// separately (no contraction): conj(row0 x row1).
+__device__ __forceinline__ cx<double> cmul_rn(cx<double> a, cx<double> b) {
+  return mk(__dsub_rn(__dmul_rn(a.re, b.re), __dmul_rn(a.im, b.im)), __dadd_rn(__dmul_rn(a.re, b.im), __dmul_rn(a.im, b.re)));
+}
+
+__global__ void k_canon_to_store(ConvArgs args) {
+  const Geometry g = args.geom;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 4LL * args.n_sites) return;
+  const int mu = (int)(idx / args.n_sites);
+  const long long i = idx - (long long)mu * args.n_sites;
+  const long long s = args.s_begin + i;
+  const int h = (int)(s >> 1);
+  const int x0 = (int)(s % g.L0);
+  const int r = (int)(s / g.L0);
+  const int x1 = r % g.L1, x2 = (r / g.L1) % g.L2, x3 = r / (g.L1 * g.L2);
+  const int p = (x0 + x1 + x2 + x3) & 1;
+  const double* src = args.canon + (i * 4 + mu) * 18;
+  if (args.precision == 0) {
+    mat3<double> m;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) m.e[c / 3][c % 3] = mk(src[2 * c], src[2 * c + 1]);
+    store_f64((double2*)args.links, mu, p, h, g.Vh, m);
+  } else {
+    float o[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) o[c] = (float)src[c];
+    store_f32_rows01((float4*)args.links, mu, p, h, g.Vh, o);
+  }
+}
+
+__global__ void k_store_to_canon(ConvArgs args) {
+  const Geometry g = args.geom;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 4LL * args.n_sites) return;
+  const int mu = (int)(idx / args.n_sites);
+  const long long i = idx - (long long)mu * args.n_sites;
+  const long long s = args.s_begin + i;
+  const int h = (int)(s >> 1);
+  const int x0 = (int)(s % g.L0);
+  const int r = (int)(s / g.L0);
+  const int x1 = r % g.L1, x2 = (r / g.L1) % g.L2, x3 = r / (g.L1 * g.L2);
+  const int p = (x0 + x1 + x2 + x3) & 1;
+  double* dst = args.canon + (i * 4 + mu) * 18;
+  if (args.precision == 0) {
+    const mat3<double> m = load_f64((const double2*)args.links, mu, p, h, g.Vh);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      dst[2 * c] = m.e[c / 3][c % 3].re;
+      dst[2 * c + 1] = m.e[c / 3][c % 3].im;
+    }
+  } else {
+    const mat3<float> m = load_f32_rows01((const float4*)args.links, mu, p, h, g.Vh);
+    cx<double> a[3], b[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      a[k] = mk((double)m.e[0][k].re, (double)m.e[0][k].im);
+      b[k] = mk((double)m.e[1][k].re, (double)m.e[1][k].im);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      dst[2 * k] = a[k].re;
+      dst[2 * k + 1] = a[k].im;
+      dst[6 + 2 * k] = b[k].re;
+      dst[6 + 2 * k + 1] = b[k].im;
+    }
+    const cx<double> x = cmul_rn(a[1], b[2]), y = cmul_rn(a[2], b[1]);
+    const cx<double> z0 = mk(__dsub_rn(x.re, y.re), __dsub_rn(x.im, y.im));
+    const cx<double> x1c = cmul_rn(a[2], b[0]), y1 = cmul_rn(a[0], b[2]);
+    const cx<double> z1 = mk(__dsub_rn(x1c.re, y1.re), __dsub_rn(x1c.im, y1.im));
+    const cx<double> x2c = cmul_rn(a[0], b[1]), y2 = cmul_rn(a[1], b[0]);
+    const cx<double> z2 = mk(__dsub_rn(x2c.re, y2.re), __dsub_rn(x2c.im, y2.im));
+    dst[12] = z0.re;
+    dst[13] = -z0.im;
+    dst[14] = z1.re;
+    dst[15] = -z1.im;
+    dst[16] = z2.re;
+    dst[17] = -z2.im;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+template <int MU>
+static cudaError_t launch_half_sweep_mu(const HalfSweepArgs& a, int precision, bool stats, int threads, cudaStream_t s) {
+  const int blocks = (a.geom.Vh + threads - 1) / threads;
+  if (precision == 0) {
+    if (stats)
+      k_half_sweep_f64<MU, true><<<blocks, threads, 0, s>>>(a);
+    else
+      k_half_sweep_f64<MU, false><<<blocks, threads, 0, s>>>(a);
+  } else {
+    if (stats)
+      k_half_sweep_f32<MU, true><<<blocks, threads, 0, s>>>(a);
+    else
+      k_half_sweep_f32<MU, false><<<blocks, threads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t su3k_launch_half_sweep(const HalfSweepArgs& a, int mu, int precision, bool stats, int threads, cudaStream_t s) {
+  switch (mu) {
+    case 0: return launch_half_sweep_mu<0>(a, precision, stats, threads, s);
+    case 1: return launch_half_sweep_mu<1>(a, precision, stats, threads, s);
+    case 2: return launch_half_sweep_mu<2>(a, precision, stats, threads, s);
+    default: return launch_half_sweep_mu<3>(a, precision, stats, threads, s);
+  }
+}
+
+cudaError_t su3k_launch_increment(uint64_t* counter, uint64_t n, cudaStream_t s) {
+  k_increment<<<1, 1, 0, s>>>(counter, n);
+  return cudaGetLastError();
+}
+
+cudaError_t su3k_launch_set_counter(uint64_t* counter, uint64_t n, cudaStream_t s) {
+  k_set_counter<<<1, 1, 0, s>>>(counter, n);
+  return cudaGetLastError();
+}
+
+cudaError_t su3k_launch_init(const InitArgs& a, bool hot, cudaStream_t s) {
+  const long long n = 8LL * a.geom.Vh;
+  const int threads = 128;
+  const int blocks = (int)((n + threads - 1) / threads);
+  if (hot)
+    k_hot_start<<<blocks, threads, 0, s>>>(a);
+  else
+    k_cold_start<<<blocks, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+int su3k_plaquette_blocks(const Geometry& g) { return (2 * g.Vh + 255) / 256; }
+
+cudaError_t su3k_launch_plaquette(const PlaqArgs& a, int precision, double* out, cudaStream_t s) {
+  const int blocks = su3k_plaquette_blocks(a.geom);
+  if (precision == 0)
+    k_plaquette_partial<double><<<blocks, 256, 0, s>>>(a);
+  else
+    k_plaquette_partial<float><<<blocks, 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const double V = 2.0 * (double)a.geom.Vh;
+  k_plaquette_final<<<1, 1024, 0, s>>>(a.partials, blocks, 1.0 / (3.0 * 6.0 * V), out);
+  return cudaGetLastError();
+}
+
+cudaError_t su3k_launch_conv(const ConvArgs& a, bool to_store, cudaStream_t s) {
+  const long long n = 4LL * a.n_sites;
+  if (n == 0) return cudaSuccess;
+  const int threads = 256;
+  const long long blocks = (n + threads - 1) / threads;
+  if (to_store)
+    k_canon_to_store<<<(unsigned)blocks, threads, 0, s>>>(a);
+  else
+    k_store_to_canon<<<(unsigned)blocks, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}

@@ -1,0 +1,51 @@
+// su3_kernels.h -- launch interface between the host runtime (su3_api.cu) and
+// the sm_103a kernels (su3_kernels.cu).  Internal to libsu3.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "su3_device.cuh"
+
+// Largest block of the half-sweep kernels (their register budget assumes it).
+constexpr int kMaxSweepThreads = 256;
+
+struct HalfSweepArgs {
+  su3dev::Geometry geom;
+  su3dev::PhiloxKey key;
+  int parity;
+  double beta;        // FP64 path
+  float inv_beta15;   // FP32 path: 1.5 / beta, so that 1/alpha = inv_beta15 / k
+  const uint64_t* sweep;  // device sweep counter (RNG position)
+  void* links;
+  unsigned long long* stats;  // [accepted, proposed], used when counting
+};
+
+struct InitArgs {
+  su3dev::Geometry geom;
+  su3dev::PhiloxKey key;
+  int precision;
+  void* links;
+};
+
+struct PlaqArgs {
+  su3dev::Geometry geom;
+  const void* links;
+  double* partials;
+};
+
+struct ConvArgs {
+  su3dev::Geometry geom;
+  int precision;
+  long long s_begin, n_sites;
+  double* canon;  // device staging buffer, canonical layout of the chunk
+  void* links;
+};
+
+cudaError_t su3k_launch_half_sweep(const HalfSweepArgs& a, int mu, int precision, bool stats, int threads, cudaStream_t s);
+cudaError_t su3k_launch_increment(uint64_t* counter, uint64_t n, cudaStream_t s);
+cudaError_t su3k_launch_set_counter(uint64_t* counter, uint64_t n, cudaStream_t s);
+cudaError_t su3k_launch_init(const InitArgs& a, bool hot, cudaStream_t s);
+int su3k_plaquette_blocks(const su3dev::Geometry& g);
+cudaError_t su3k_launch_plaquette(const PlaqArgs& a, int precision, double* out, cudaStream_t s);
+cudaError_t su3k_launch_conv(const ConvArgs& a, bool to_store, cudaStream_t s);

@@ -1,0 +1,98 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every symbol
+declared in include/su3.h, and host-side argument validation rejects bad input
+before any CUDA call.  No compute call is made here (no GPU in this
+environment)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_0904_1179_gb300 as su3
+from paper_0904_1179_gb300 import build as su3_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    su3_build.build()
+    return su3.load_library()
+
+
+def declared_symbols():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"^SU3_API\s+[\w\s\*]+?\b(su3_\w+)\s*\(", text, flags=re.M)
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 16
+    out = subprocess.run(["nm", "-D", "--defined-only", su3.library_path()], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (su3_\w+)$", out, flags=re.M))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    # the binding wraps exactly the declared entry points
+    assert sorted(n for n, _, _ in su3.EXPORTS) == sorted(names)
+
+
+def test_version(lib):
+    assert "sm_103a" in su3.su3_version()
+
+
+def _create(lib, dims, beta=5.7, start=0, prec=0):
+    h = ctypes.c_void_p()
+    rc = lib.su3_create_ex(*dims, beta, 1, start, prec, None, ctypes.byref(h))
+    return rc, h
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 5), (3, 4, 4, 4), (0, 4, 4, 4), (4, 4, -2, 4)])
+def test_create_rejects_bad_extents(lib, dims):
+    rc, h = _create(lib, dims)
+    assert rc == su3.SU3_EINVAL and not h.value
+    assert "extent" in su3.su3_last_error()
+
+
+def test_create_rejects_oversized_volume(lib):
+    rc, _ = _create(lib, (256, 256, 256, 256))
+    assert rc == su3.SU3_EINVAL and "2^31" in su3.su3_last_error()
+
+
+@pytest.mark.parametrize("beta", [0.0, -1.0, float("inf"), float("nan")])
+def test_create_rejects_bad_beta(lib, beta):
+    rc, _ = _create(lib, (4, 4, 4, 4), beta=beta)
+    assert rc == su3.SU3_EINVAL and "beta" in su3.su3_last_error()
+
+
+def test_create_rejects_bad_enums(lib):
+    assert _create(lib, (4, 4, 4, 4), start=2)[0] == su3.SU3_EINVAL
+    assert _create(lib, (4, 4, 4, 4), prec=7)[0] == su3.SU3_EINVAL
+    assert lib.su3_create_ex(4, 4, 4, 4, 5.7, 1, 0, 0, None, None) == su3.SU3_EINVAL
+
+
+def test_null_handle_calls(lib):
+    assert lib.su3_destroy(None) == su3.SU3_OK
+    assert lib.su3_sweep(None, 1) == su3.SU3_EINVAL
+    assert lib.su3_half_sweep(None, 0, 0) == su3.SU3_EINVAL
+    assert lib.su3_links_get(None, None, 0) == su3.SU3_EINVAL
+    assert lib.su3_links_set(None, None, 0) == su3.SU3_EINVAL
+    assert lib.su3_set_sweep_count(None, 0) == su3.SU3_EINVAL
+    assert lib.su3_set_block_size(None, 64) == su3.SU3_EINVAL
+    v = lib.su3_plaquette(None)
+    assert v != v
+
+
+def test_binding_has_no_fallback_and_no_oracle():
+    # the product path never imports the oracle
+    pkg = os.path.join(ROOT, "paper_0904_1179_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, fn)).read()
+                assert "import oracle" not in text and "su3_oracle" not in text, fn

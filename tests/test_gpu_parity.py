@@ -1,0 +1,437 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 CPU oracle.
+
+Every oracle input is produced by the oracle itself (its hot/cold start) or by
+the seeded recipes below; no expected value comes from the CUDA path.
+
+Tolerances:
+  FP64 path: link by link <= 1e-12 after one half-sweep and after one full
+    sweep (same config, same Philox key): both sides run the same FP64
+    arithmetic; they differ only by FMA contraction and libm-vs-CUDA
+    transcendental rounding (~1e-16 relative per operation, a few hundred
+    operations per update).
+  FP32-mixed path vs the oracle's FP64 reading of it (same FP32 uniforms,
+    storage rounded to FP32 after an FP64 Gram-Schmidt): link by link
+    <= 5e-5.  FP32 rounding of the staple (6 paths of 3 products of O(1)
+    entries) and of the heatbath gives ~1e-6; the bound leaves headroom for
+    the larger |A| of cold-ish configurations.  A one-hit accept decision may
+    differ from the oracle's only where the oracle's decision margin is within
+    FP32 rounding of the threshold (|margin| < 1e-4); such flips are counted
+    and bounded.
+"""
+import math
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_0904_1179_gb300 as su3
+from paper_0904_1179_gb300 import build as su3_build
+
+pytestmark = pytest.mark.gpu
+
+BETA = 5.7
+F64_TOL = 1e-12
+F32_TOL = 5e-5
+F32_MARGIN = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    su3_build.build()
+    oracle.build()
+
+
+def parity_mask(L):
+    x = np.indices((L[3], L[2], L[1], L[0]))
+    return (x.sum(axis=0) % 2).astype(bool)
+
+
+def site_list(L, parity):
+    """Canonical indices of the sites of one parity, in canonical order."""
+    mask = parity_mask(L).reshape(-1)
+    s = np.arange(mask.size)
+    return s[mask == bool(parity)]
+
+
+def flat_links(U):
+    return U.reshape(-1, 4, 3, 3, 2)
+
+
+def su3_defects(U):
+    M = (U[..., 0] + 1j * U[..., 1]).reshape(-1, 3, 3)
+    unit = np.abs(np.einsum("nki,nkj->nij", M.conj(), M) - np.eye(3)).max()
+    det = np.abs(np.linalg.det(M) - 1.0).max()
+    return unit, det
+
+
+DIMS_SMALL = [(4, 4, 4, 4), (8, 8, 8, 8), (8, 8, 8, 16), (6, 4, 10, 8), (2, 2, 2, 2)]
+
+
+# ---------------------------------------------------------------------------
+# start configurations, layout, plaquette
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [su3.SU3_FP64, su3.SU3_FP32_MIXED])
+def test_cold_start(prec):
+    L = (4, 6, 4, 8)
+    with su3.Lattice(L, BETA, 1, start=su3.SU3_COLD, precision=prec) as lat:
+        U = lat.get_links()
+        assert np.array_equal(U, oracle.cold_start(L))
+        assert lat.plaquette() == 1.0
+
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (8, 8, 8, 16), (6, 4, 10, 8)])
+def test_hot_start_matches_oracle(L):
+    with su3.Lattice(L, BETA, 7, start=su3.SU3_HOT, precision=su3.SU3_FP64) as lat:
+        G = lat.get_links()
+    O = oracle.hot_start(L, 7)
+    assert np.abs(G - O).max() < 1e-14
+    with su3.Lattice(L, BETA, 7, start=su3.SU3_HOT, precision=su3.SU3_FP32_MIXED) as lat:
+        G = lat.get_links()
+    O = oracle.hot_start(L, 7, f32=True)
+    # rows 0,1 are the FP32 roundings of the same FP64 numbers: equal, or one
+    # float ulp apart where the FP64 values straddle a rounding boundary
+    d = np.abs(G - O)
+    assert d.max() < 2.5e-7
+    assert (d[..., :2, :, :] == 0).mean() > 0.999
+
+
+@pytest.mark.parametrize("prec", [su3.SU3_FP64, su3.SU3_FP32_MIXED])
+def test_links_roundtrip_exact(prec):
+    L = (6, 4, 10, 8)
+    f32 = prec == su3.SU3_FP32_MIXED
+    O = oracle.hot_start(L, 3, f32=f32)
+    with su3.Lattice(L, BETA, 1, start=su3.SU3_COLD, precision=prec) as lat:
+        lat.set_links(O)
+        assert np.array_equal(lat.get_links(), O)
+
+
+def test_fp32_set_rounds_and_rebuilds_row2():
+    L = (4, 4, 4, 4)
+    O = oracle.hot_start(L, 3)
+    with su3.Lattice(L, BETA, 1, start=su3.SU3_COLD, precision=su3.SU3_FP32_MIXED) as lat:
+        lat.set_links(O)
+        G = lat.get_links()
+    assert np.array_equal(G[..., :2, :, :], O[..., :2, :, :].astype(np.float32).astype(np.float64))
+    assert np.abs(G - O).max() < 3e-7
+
+
+@pytest.mark.parametrize("L", DIMS_SMALL)
+def test_plaquette_matches_oracle(L):
+    O = oracle.hot_start(L, 11)
+    oracle.sweep(L, BETA, 5, 0, 3, O)
+    with su3.Lattice(L, BETA, 1, start=su3.SU3_COLD) as lat:
+        lat.set_links(O)
+        assert abs(lat.plaquette() - oracle.plaquette(L, O)) < 1e-13
+    Of = oracle.hot_start(L, 11, f32=True)
+    oracle.sweep(L, BETA, 5, 0, 3, Of, f32=True)
+    with su3.Lattice(L, BETA, 1, start=su3.SU3_COLD, precision=su3.SU3_FP32_MIXED) as lat:
+        lat.set_links(Of)
+        assert abs(lat.plaquette() - oracle.plaquette(L, Of, f32=True)) < 2e-6
+
+
+# ---------------------------------------------------------------------------
+# the FP64 sweep
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", DIMS_SMALL)
+def test_fp64_half_sweeps_match_oracle(L):
+    seed, t = 19, 3
+    U0 = oracle.hot_start(L, 5)
+    oracle.sweep(L, BETA, 8, 0, 1, U0)
+    pm = parity_mask(L)
+    with su3.Lattice(L, BETA, seed, start=su3.SU3_COLD) as lat:
+        for mu in range(4):
+            for p in range(2):
+                lat.set_links(U0)
+                lat.sweep_count = t
+                lat.half_sweep(mu, p)
+                G = lat.get_links()
+                O = U0.copy()
+                oracle.half_sweep(L, BETA, seed, t, mu, p, O)
+                assert np.abs(G - O).max() < F64_TOL, (mu, p, np.abs(G - O).max())
+                # only the links of (mu, p) changed
+                other = np.ones((L[3], L[2], L[1], L[0], 4), dtype=bool)
+                other[pm == bool(p), mu] = False
+                assert np.array_equal(G[other], U0[other])
+
+
+@pytest.mark.parametrize("L", DIMS_SMALL)
+def test_fp64_sweep_matches_oracle(L):
+    seed = 23
+    U0 = oracle.hot_start(L, 6)
+    O = U0.copy()
+    (acc, prop), plaq = oracle.sweep(L, BETA, seed, 0, 2, O)
+    with su3.Lattice(L, BETA, seed, start=su3.SU3_COLD) as lat:
+        lat.set_links(U0)
+        lat.set_stats(True)
+        lat.sweep(2)
+        G = lat.get_links()
+        assert lat.sweep_count == 2
+        assert np.abs(G - O).max() < F64_TOL
+        assert lat.stats() == (acc, prop)
+        assert abs(lat.plaquette() - plaq[-1]) < 1e-13
+
+
+def test_fp64_cold_start_chain_config0():
+    # 4^4, beta 5.7, cold start, Philox seed 1, 20 sweeps, plaquette after each sweep
+    L = (4, 4, 4, 4)
+    O = oracle.cold_start(L)
+    _, plaq = oracle.sweep(L, BETA, 1, 0, 20, O)
+    with su3.Lattice(L, BETA, 1, start=su3.SU3_COLD) as lat:
+        gp = []
+        for _ in range(20):
+            lat.sweep(1)
+            gp.append(lat.plaquette())
+        assert np.abs(lat.get_links() - O).max() < F64_TOL
+    assert np.abs(np.array(gp) - plaq).max() < 1e-13
+
+
+def test_graph_replay_equals_eager_half_sweeps():
+    L = (8, 8, 8, 16)
+    for prec in (su3.SU3_FP64, su3.SU3_FP32_MIXED):
+        with su3.Lattice(L, BETA, 4, start=su3.SU3_HOT, precision=prec) as a, \
+                su3.Lattice(L, BETA, 4, start=su3.SU3_HOT, precision=prec) as b:
+            a.sweep(3)
+            for t in range(3):
+                for mu in range(4):
+                    for p in range(2):
+                        b.half_sweep(mu, p)
+                b.sweep_count = t + 1
+            assert np.array_equal(a.get_links(), b.get_links())
+
+
+@pytest.mark.parametrize("prec", [su3.SU3_FP64, su3.SU3_FP32_MIXED])
+def test_block_size_does_not_change_results(prec):
+    L = (6, 4, 10, 8)
+    ref = None
+    for threads in (32, 64, 96, 128, 256):
+        with su3.Lattice(L, BETA, 9, start=su3.SU3_HOT, precision=prec) as lat:
+            lat.set_block_size(threads)
+            lat.sweep(2)
+            U = lat.get_links()
+        if ref is None:
+            ref = U
+        assert np.array_equal(U, ref), threads
+
+
+@pytest.mark.parametrize("prec", [su3.SU3_FP64, su3.SU3_FP32_MIXED])
+def test_resume_from_checkpoint(prec):
+    L = (8, 8, 8, 8)
+    with su3.Lattice(L, BETA, 31, start=su3.SU3_HOT, precision=prec) as a:
+        a.sweep(4)
+        ref = a.get_links()
+    with su3.Lattice(L, BETA, 31, start=su3.SU3_HOT, precision=prec) as b:
+        b.sweep(2)
+        ck = b.get_links()
+        n = b.sweep_count
+    with su3.Lattice(L, BETA, 31, start=su3.SU3_COLD, precision=prec) as c:
+        c.set_links(ck)
+        c.sweep_count = n
+        c.sweep(2)
+        assert np.array_equal(c.get_links(), ref)
+
+
+# ---------------------------------------------------------------------------
+# the FP32-mixed sweep
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (8, 8, 8, 8), (6, 4, 10, 8)])
+def test_fp32_half_sweeps_match_oracle_reading(L):
+    seed, t = 29, 5
+    U0 = oracle.hot_start(L, 7, f32=True)
+    oracle.sweep(L, BETA, 2, 0, 2, U0, f32=True)
+    pm = parity_mask(L)
+    flips = 0
+    total = 0
+    worst = 0.0
+    with su3.Lattice(L, BETA, seed, start=su3.SU3_COLD, precision=su3.SU3_FP32_MIXED) as lat:
+        for mu in range(4):
+            for p in range(2):
+                lat.set_links(U0)
+                lat.sweep_count = t
+                lat.half_sweep(mu, p)
+                G = flat_links(lat.get_links())
+                sites = site_list(L, p)
+                O, marg = oracle.updated_links(L, BETA, seed, t, mu, sites, U0, f32=True, with_margins=True)
+                d = np.abs(G[sites, mu] - O).max(axis=(1, 2, 3))
+                bad = d > F32_TOL
+                if bad.any():
+                    m = np.nanmin(np.abs(marg[bad]), axis=1)
+                    assert (m < F32_MARGIN).all(), (mu, p, d[bad], m)
+                flips += int(bad.sum())
+                total += sites.size
+                worst = max(worst, float(d[~bad].max()))
+                other = np.ones((L[3], L[2], L[1], L[0], 4), dtype=bool)
+                other[pm == bool(p), mu] = False
+                assert np.array_equal(lat.get_links()[other], U0[other])
+    assert flips <= max(2, total // 2000), (flips, total)
+    print("fp32 half-sweeps %s: worst |dU| %.2e, flips %d of %d" % (L, worst, flips, total))
+
+
+def test_fp32_links_stay_su3_and_float():
+    L = (8, 8, 8, 8)
+    with su3.Lattice(L, BETA, 3, start=su3.SU3_HOT, precision=su3.SU3_FP32_MIXED) as lat:
+        lat.sweep(10)
+        U = lat.get_links()
+    rows = U[..., :2, :, :]
+    assert np.array_equal(rows, rows.astype(np.float32).astype(np.float64))
+    unit, det = su3_defects(U)
+    assert unit < 5e-7 and det < 5e-7
+
+
+# ---------------------------------------------------------------------------
+# full-size lattice (32^4, the benchmark's workload), sampled against the oracle
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [su3.SU3_FP64, su3.SU3_FP32_MIXED])
+def test_full_size_32x4_sampled(prec):
+    L = (32, 32, 32, 32)
+    f32 = prec == su3.SU3_FP32_MIXED
+    seed = 7
+    U0 = oracle.hot_start(L, seed, f32=f32)
+    rng = np.random.default_rng(1)
+    with su3.Lattice(L, BETA, seed, start=su3.SU3_HOT, precision=prec) as lat:
+        G0 = lat.get_links()
+        # GPU hot start = oracle hot start
+        assert np.abs(G0 - U0).max() < (2.5e-7 if f32 else 1e-14)
+        lat.set_links(U0)
+        for mu, p in ((0, 0), (3, 1)):
+            lat.set_links(U0)
+            lat.half_sweep(mu, p)
+            G = flat_links(lat.get_links())
+            sites = rng.choice(site_list(L, p), size=1500, replace=False)
+            O, marg = oracle.updated_links(L, BETA, seed, 0, mu, sites, U0, f32=f32, with_margins=True)
+            d = np.abs(G[sites, mu] - O).max(axis=(1, 2, 3))
+            if f32:
+                bad = d > F32_TOL
+                assert bad.sum() <= 2
+                if bad.any():
+                    assert (np.nanmin(np.abs(marg[bad]), axis=1) < F32_MARGIN).all()
+            else:
+                assert d.max() < F64_TOL
+        # the graphed sweep at full size equals eight eager half-sweeps, and keeps SU(3)
+        lat.set_links(U0)
+        lat.sweep_count = 0
+        lat.sweep(1)
+        A = lat.get_links()
+        lat.set_links(U0)
+        lat.sweep_count = 0
+        for mu in range(4):
+            for p in range(2):
+                lat.half_sweep(mu, p)
+        B = lat.get_links()
+        assert np.array_equal(A, B)
+        sample = flat_links(A)[rng.choice(np.prod(L), size=20000, replace=False)]
+        unit, det = su3_defects(sample)
+        assert unit < (5e-7 if f32 else 1e-13) and det < (5e-7 if f32 else 1e-13)
+
+
+# ---------------------------------------------------------------------------
+# statistical agreement over long chains
+# ---------------------------------------------------------------------------
+
+def binned(x, nb=20):
+    x = np.asarray(x)
+    b = x[: (x.size // nb) * nb].reshape(nb, -1).mean(axis=1)
+    return b.mean(), b.std(ddof=1) / math.sqrt(nb)
+
+
+def test_fp64_chain_agrees_with_oracle_chain():
+    # independent chains (different seeds), 6^4 at beta 5.7, binned means within 3 sigma
+    L = (6, 6, 6, 6)
+    O = oracle.hot_start(L, 100)
+    _, po = oracle.sweep(L, BETA, 101, 0, 600, O)
+    with su3.Lattice(L, BETA, 202, start=su3.SU3_HOT) as lat:
+        lat.sweep(100)
+        pg = []
+        for _ in range(2000):
+            lat.sweep(1)
+            pg.append(lat.plaquette())
+    mo, eo = binned(po[100:])
+    mg, eg = binned(pg)
+    assert abs(mo - mg) < 3 * math.hypot(eo, eg), (mo, eo, mg, eg)
+
+
+def test_fp32_chain_agrees_with_fp64_chain():
+    L = (8, 8, 8, 8)
+    res = {}
+    for prec in (su3.SU3_FP64, su3.SU3_FP32_MIXED):
+        with su3.Lattice(L, BETA, 300 + prec, start=su3.SU3_HOT, precision=prec) as lat:
+            lat.sweep(200)
+            p = []
+            for _ in range(2000):
+                lat.sweep(1)
+                p.append(lat.plaquette())
+        res[prec] = binned(p)
+    (m64, e64), (m32, e32) = res[su3.SU3_FP64], res[su3.SU3_FP32_MIXED]
+    assert abs(m64 - m32) < 3 * math.hypot(e64, e32), res
+    print("plaquette 8^4 beta 5.7: FP64 %.6f(%d)  FP32-mixed %.6f(%d)" % (m64, round(e64 * 1e6), m32, round(e32 * 1e6)))
+
+
+def test_acceptance_rate_reported():
+    L = (8, 8, 8, 8)
+    with su3.Lattice(L, BETA, 5, start=su3.SU3_HOT) as lat:
+        lat.sweep(100)
+        lat.set_stats(True)
+        lat.sweep(20)
+        acc, prop = lat.stats()
+    rate = acc / prop
+    assert prop == 20 * 4 * np.prod(L) * 3
+    assert 0.95 < rate < 0.99
+    print("one-hit acceptance at beta 5.7: %.4f (paper: 0.972)" % rate)
+
+
+# ---------------------------------------------------------------------------
+# the oracle's Philox against cuRAND's (a third-party implementation)
+# ---------------------------------------------------------------------------
+
+CURAND_PROBE = r"""
+#include <cstdio>
+#include <curand_philox4x32_x.h>
+__global__ void k(const uint4* c, const uint2* key, uint4* o, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] = curand_Philox4x32_10(c[i], key[i]);
+}
+int main() {
+  const int n = 256;
+  uint4 hc[n]; uint2 hk[n]; uint4 ho[n];
+  unsigned s = 12345u;
+  for (int i = 0; i < n; ++i) {
+    unsigned w[6];
+    for (int j = 0; j < 6; ++j) { s = s * 1664525u + 1013904223u; w[j] = s; }
+    hc[i] = make_uint4(w[0], w[1], w[2], w[3]); hk[i] = make_uint2(w[4], w[5]);
+  }
+  uint4 *dc, *dout; uint2* dk;
+  cudaMalloc(&dc, sizeof hc); cudaMalloc(&dk, sizeof hk); cudaMalloc(&dout, sizeof ho);
+  cudaMemcpy(dc, hc, sizeof hc, cudaMemcpyHostToDevice);
+  cudaMemcpy(dk, hk, sizeof hk, cudaMemcpyHostToDevice);
+  k<<<(n + 127) / 128, 128>>>(dc, dk, dout, n);
+  if (cudaMemcpy(ho, dout, sizeof ho, cudaMemcpyDeviceToHost) != cudaSuccess) return 1;
+  for (int i = 0; i < n; ++i)
+    printf("%u %u %u %u %u %u %u %u %u %u\n", hc[i].x, hc[i].y, hc[i].z, hc[i].w, hk[i].x, hk[i].y,
+           ho[i].x, ho[i].y, ho[i].z, ho[i].w);
+  return 0;
+}
+"""
+
+
+def test_philox_matches_curand():
+    nvcc = su3_build.nvcc()
+    d = tempfile.mkdtemp()
+    try:
+        src = os.path.join(d, "probe.cu")
+        exe = os.path.join(d, "probe")
+        open(src, "w").write(CURAND_PROBE)
+        subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-o", exe, src], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+        rows = [list(map(int, ln.split())) for ln in out if ln.strip()]
+        assert len(rows) == 256
+        for r in rows:
+            assert oracle.philox4x32_10(r[0:4], r[4:6]) == r[6:10]
+    finally:
+        shutil.rmtree(d)
