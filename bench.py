@@ -1,0 +1,372 @@
+"""Benchmark: SU(3) checkerboard heatbath link updates per second on GB300.
+
+Workload (the paper's own timing workload, Berg & Wu Sec. 2.1, Table 1, 32^4
+column): a 32^4 periodic lattice at beta = 5.7, hot start from Philox seed 7,
+FP64 links; one step = 2 full checkerboard sweeps (4 * 32^4 * 2 link updates)
+with no measurement inside the step, start-configuration creation outside the
+timed region (Sec. 2).  The FP32-mixed form of the same workload is reported
+under "variants".
+
+Timing: W untimed warm-up steps, then K steps between a barrier and a device
+synchronise, CUDA events on the library's stream around every sweep graph,
+maximum over ranks.  The link store (604 MB FP64, 201 MB FP32-mixed) exceeds
+the 129 MB L2, so no flush is needed between steps.
+
+Multi-GPU: replicas only -- each rank runs its own lattice (weak scaling), no
+collective on the data path; value = all ranks' link updates / slowest rank's
+time.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (one half-sweep of the 32^4 lattice per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SU(3) link updates/s at 32^4 (FP64 vs FP32-mixed vs batched); % HBM roofline"
+UNIT = "link updates/s"
+DIMS = (32, 32, 32, 32)
+BETA = 5.7
+SEED = 7
+SWEEPS_PER_STEP = 2
+# Paper, Table 1: 32^4, 2 sweeps, non-MPI program on one 2 GHz Intel E5405 core: 48.9 s.
+PAPER_UPS = 4 * 32 ** 4 * 2 / 48.9
+
+# Algorithmic cost per link update of one half-sweep (mu, parity): the V/2
+# updated links, the V/2 opposite-parity links of direction mu and the 3V links
+# of the other directions are read once, the V/2 updated links written once:
+# 9 links moved per update.
+BYTES_PER_UPDATE = {"fp64": 9 * 18 * 8, "fp32_mixed": 9 * 12 * 4}
+# FP64 floating-point operations per link update of the FP64 kernel as written
+# (staple 6 paths x 2 three-row-pair products + 6 row completions, accumulation,
+# three SU(2) projections and rotations, Gram-Schmidt); transcendental calls
+# are not counted.  See the design notes for the breakdown.
+FP64_FLOP_PER_UPDATE = 3208
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# Peak FP64 FMA rate of GB300: 1.006 TFLOP/s measured by an FMA loop at the
+# 2070 MHz maximum SM clock (the nominal figure is 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 1.006
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max_sum(world, seconds, units, device):
+    """Slowest rank's time and the sum of all ranks' units (host logic shared with the CPU tests)."""
+    if world == 1:
+        return seconds, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def time_sweeps(lat, stream, steps, warmup, sweeps_per_step, world, sampler=None):
+    """W warm-up steps, then K steps; CUDA events on the lattice's stream around every sweep graph."""
+    import torch
+    for _ in range(warmup):
+        lat.sweep(sweeps_per_step)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    n = steps * sweeps_per_step
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+    if sampler:
+        sampler.start()
+    evs[0].record(stream)
+    for i in range(n):
+        lat.sweep(1)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    barrier(world)
+    total_ms = evs[0].elapsed_time(evs[-1])
+    sweep_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(n)]
+    return total_ms, sweep_ms, clocks
+
+
+def time_e2e(su3, L, prec, steps, warmup, sweeps_per_step):
+    """End to end through the public API with page-locked host buffers: per step, copy the
+    configuration in (su3_links_set), run the sweeps, read the plaquette back, copy the
+    configuration out (su3_links_get)."""
+    import numpy as np
+    import torch
+    shape = su3.links_shape(L)
+    host_in = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    host_out = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    with su3.Lattice(L, BETA, SEED, start=su3.SU3_HOT, precision=prec) as lat:
+        lat.get_links(host_in)  # the host-side start configuration
+        for _ in range(warmup):
+            lat.set_links(host_in)
+            lat.sweep(sweeps_per_step)
+            lat.plaquette()
+            lat.get_links(host_out)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            lat.set_links(host_in)
+            lat.sweep(sweeps_per_step)
+            lat.plaquette()
+            lat.get_links(host_out)
+        dt = time.perf_counter() - t0
+    ups = 4 * int(np.prod(L)) * sweeps_per_step * steps / dt
+    return {"value": ups, "unit": UNIT, "h2d_bytes_per_step": int(host_in.nbytes),
+            "d2h_bytes_per_step": int(host_out.nbytes) + 8, "ms_per_step": dt / steps * 1e3,
+            "step": "su3_links_set(host) + %d sweeps + su3_plaquette + su3_links_get(host)" % sweeps_per_step}
+
+
+def cpu_baseline_sample(f32):
+    """The oracle as it stands (single thread) on one full sweep of the same 32^4 workload."""
+    import oracle
+    oracle.build()
+    U = oracle.hot_start(DIMS, SEED, f32=f32)
+    t0 = time.perf_counter()
+    oracle.sweep(DIMS, BETA, SEED, 0, 1, U, f32=f32)
+    dt = time.perf_counter() - t0
+    ups = 4 * 32 ** 4 / dt
+    return {"value": ups, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one full sweep (4*32^4 link updates) of the 32^4 beta=5.7 hot-start lattice, %s, "
+                      "single thread, %.1f s" % ("FP32-mixed reading" if f32 else "FP64", dt),
+            "us_per_update": dt / (4 * 32 ** 4) * 1e6}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    U = oracle.hot_start(DIMS, SEED)
+    phases = [(mu, p) for mu in range(4) for p in range(2)]
+    for i in range(args.warmup):
+        mu, p = phases[i % 8]
+        oracle.half_sweep(DIMS, BETA, SEED, 0, mu, p, U)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        mu, p = phases[(args.warmup + i) % 8]
+        oracle.half_sweep(DIMS, BETA, SEED, (args.warmup + i) // 8, mu, p, U)
+    dt = time.perf_counter() - t0
+    ups = 4 * 32 ** 4 / 8 * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": ups / PAPER_UPS, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "32^4 beta=5.7 hot start seed 7, FP64 checkerboard heatbath; reference step = "
+                                   "one half-sweep (V/2 link updates) of the FP64 CPU oracle",
+                       "lattice": list(DIMS), "beta": BETA},
+            "cpu_baseline": {"value": ups, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one checkerboard half-sweep of the 32^4 lattice per step, single thread"},
+            "e2e": {"value": ups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def variant_fp32(su3, stream, steps, warmup, world, hbm_peak, peak_kind):
+    import numpy as np
+    with su3.Lattice(DIMS, BETA, SEED, start=su3.SU3_HOT, precision=su3.SU3_FP32_MIXED,
+                     stream=stream.cuda_stream) as lat:
+        total_ms, sweep_ms, _ = time_sweeps(lat, stream, steps, warmup, SWEEPS_PER_STEP, world)
+        plaq = lat.plaquette()
+    V = int(np.prod(DIMS))
+    ups = 4 * V * SWEEPS_PER_STEP * steps / (total_ms * 1e-3)
+    kernel_ms = statistics.mean(sweep_ms) / 8
+    achieved = BYTES_PER_UPDATE["fp32_mixed"] * (V // 2) / (kernel_ms * 1e-3) / 1e9
+    return {"workload": "32^4 beta=5.7 hot start seed 7, FP32-mixed (12-real FP32 links, FP32 staple and "
+                        "heatbath, FP64 Gram-Schmidt), 2 sweeps/step",
+            "value": ups, "unit": UNIT, "ms_per_step": total_ms / steps, "dtype": "f32 (f64 reunitarisation)",
+            "plaquette_after": plaq,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": None,
+                         "bytes_per_launch": BYTES_PER_UPDATE["fp32_mixed"] * (V // 2),
+                         "kernel_ms": kernel_ms}}
+
+
+def run_profile_case(case):
+    import paper_0904_1179_gb300 as su3
+    prec = su3.SU3_FP64 if case == "fp64" else su3.SU3_FP32_MIXED
+    with su3.Lattice(DIMS, BETA, SEED, start=su3.SU3_HOT, precision=prec) as lat:
+        lat.sweep(3)
+        print(json.dumps({"profile_case": case, "lattice": list(DIMS), "sweeps": 3, "plaquette": lat.plaquette()}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--profile", choices=["fp64", "fp32_mixed"],
+                    help="small case for ncu: create the 32^4 lattice and run 3 graphed sweeps, nothing else")
+    args = ap.parse_args()
+    if args.profile:
+        return run_profile_case(args.profile)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import paper_0904_1179_gb300 as su3
+
+    rank, world, local = dist_setup()
+    device = torch.device("cuda", local)
+    hbm_peak, peak_kind = peaks()
+    stream = torch.cuda.Stream(device=device)
+    V = int(np.prod(DIMS))
+
+    with su3.Lattice(DIMS, BETA, SEED + rank, start=su3.SU3_HOT, precision=su3.SU3_FP64,
+                     stream=stream.cuda_stream) as lat:
+        sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+        total_ms, sweep_ms, clocks = time_sweeps(lat, stream, args.steps, args.warmup, SWEEPS_PER_STEP, world, sampler)
+        plaq = lat.plaquette()
+    units = 4.0 * V * SWEEPS_PER_STEP * args.steps
+    secs, all_units = reduce_max_sum(world, total_ms * 1e-3, units, device)
+    value = all_units / secs
+    kernel_ms = statistics.mean(sweep_ms) / 8
+    flop_per_launch = FP64_FLOP_PER_UPDATE * (V // 2)
+    achieved_tf = flop_per_launch / (kernel_ms * 1e-3) / 1e12
+
+    if rank != 0:
+        barrier(world)
+        return 0
+
+    variants = {}
+    if not args.no_variants:
+        variants["fp32_mixed"] = variant_fp32(su3, stream, args.steps, args.warmup, 1, hbm_peak, peak_kind)
+    e2e = time_e2e(su3, DIMS, su3.SU3_FP64, max(3, args.steps // 4), 3, SWEEPS_PER_STEP)
+    cpu = None if args.no_cpu_baseline else cpu_baseline_sample(False)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": value / PAPER_UPS, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "32^4 periodic lattice, beta=5.7, hot start (Haar, Philox seed 7), FP64 links, "
+                               "checkerboard Cabibbo-Marinari one-hit heatbath; step = 2 sweeps (paper Table 1 "
+                               "32^4 column)",
+                   "lattice": list(DIMS), "beta": BETA, "seed": SEED, "sweeps_per_step": SWEEPS_PER_STEP,
+                   "precision": "fp64", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "no flush: the 604 MB link store exceeds the 129 MB L2",
+                   "plaquette_after": plaq},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": args.steps * SWEEPS_PER_STEP * 9,
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_half_sweep_f64", "flop_per_launch": flop_per_launch, "kernel_ms": kernel_ms,
+                     "hbm_frac": BYTES_PER_UPDATE["fp64"] * (V // 2) / (kernel_ms * 1e-3) / 1e9 / hbm_peak,
+                     "hbm_peak": hbm_peak, "hbm_peak_kind": peak_kind},
+        "cpu_baseline": cpu,
+        "variants": variants,
+    }
+    print(json.dumps(line))
+    barrier(world)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
