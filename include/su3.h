@@ -146,6 +146,38 @@ SU3_API int su3_info(su3_handle h, int dims[4], double* beta, uint64_t* seed, in
  * keyed by its site. */
 SU3_API int su3_set_block_size(su3_handle h, int threads);
 
+/* Mean plaquette of a link store held by the caller in device memory,
+ * computed without allocating any memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code that runs
+ * while its stream is being captured into a CUDA graph (allocation cannot be
+ * captured), runtimes that hand out device memory only from their own pool or
+ * arena, and plugins or callbacks that must not touch the process allocator.
+ * It performs no cudaMalloc, cudaFree or other allocating call.
+ *   links: device pointer to a configuration in the library's device layout,
+ *     half-lattice structure of arrays indexed by h = s/2 (s the canonical
+ *     site index; each parity holds one site of every pair 2h, 2h+1):
+ *       SU3_FP64:       double2 [4 mu][2 parity][9 entries row*3+col][V/2]
+ *       SU3_FP32_MIXED: float4  [4 mu][2 parity][3 groups][V/2], rows 0 and 1
+ *                       only: groups (u00,u01), (u02,u10), (u11,u12), each
+ *                       entry as (re, im); row 2 is conj(row0 x row1).
+ *   out: device pointer to one double that receives the mean plaquette, as
+ *     defined for su3_plaquette, when the work enqueued on cuda_stream runs.
+ *   cuda_stream: the cudaStream_t to enqueue on (NULL = the default stream).
+ * The call is asynchronous and does not synchronise.  Its scratch -- one FP64
+ * partial sum per block of 256 sites -- is a fixed 512 KiB device array that
+ * every GPU loading libsu3 holds until process exit; lattices of more than
+ * 2^24 sites (64^4) are rejected with SU3_ESIZE.  Each call writes every
+ * partial it reads, so nothing in the scratch needs to start at zero, but all
+ * calls share the one array: calls that overlap on the GPU (on different
+ * streams, or from several host threads) race and return wrong results.  The
+ * first call on each device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Errors: SU3_EINVAL (NULL pointer, odd or < 2 extent, bad
+ * precision), SU3_ESIZE (too many sites), SU3_ECUDA (lookup or launch
+ * failed); su3_last_error() describes them. */
+SU3_API int su3_plaquette_noalloc(const void* links, int L0, int L1, int L2, int L3, int precision, double* out,
+                                  void* cuda_stream);
+
 /* Description of the last failure on the calling thread ("" if none). */
 SU3_API const char* su3_last_error(void);
 

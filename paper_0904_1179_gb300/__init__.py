@@ -20,7 +20,7 @@ __all__ = [
     "SU3_COLD", "SU3_HOT", "SU3_FP64", "SU3_FP32_MIXED", "Su3Error", "load_library", "library_path",
     "su3_create", "su3_create_ex", "su3_destroy", "su3_sweep", "su3_half_sweep", "su3_plaquette",
     "su3_links_get", "su3_links_set", "su3_sweep_count", "su3_set_sweep_count", "su3_set_stats", "su3_stats",
-    "su3_info", "su3_set_block_size", "su3_last_error", "su3_version", "Lattice", "links_shape", "EXPORTS",
+    "su3_info", "su3_set_block_size", "su3_plaquette_noalloc", "su3_last_error", "su3_version", "Lattice", "links_shape", "EXPORTS",
 ]
 
 SU3_COLD, SU3_HOT = 0, 1
@@ -57,6 +57,8 @@ EXPORTS = [
     ("su3_stats", ctypes.c_int, [_h, _pu64, _pu64]),
     ("su3_info", ctypes.c_int, [_h, _pi, _pd, _pu64, _pi]),
     ("su3_set_block_size", ctypes.c_int, [_h, ctypes.c_int]),
+    ("su3_plaquette_noalloc", ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5 + [ctypes.c_void_p,
+                                                                                      ctypes.c_void_p]),
     ("su3_last_error", ctypes.c_char_p, []),
     ("su3_version", ctypes.c_char_p, []),
 ]
@@ -186,6 +188,17 @@ def su3_info(h):
 
 def su3_set_block_size(h, threads):
     _check(load_library().su3_set_block_size(h, threads))
+
+
+def su3_plaquette_noalloc(links_ptr, dims, precision, out_ptr, cuda_stream=None):
+    """Mean plaquette of a device-resident link store (library device layout) into the
+    device double at out_ptr, without any allocation; asynchronous on cuda_stream.
+
+    For callers that cannot allocate device memory (stream capture, pool-only
+    runtimes).  Pointers are raw device addresses (ints), e.g. tensor.data_ptr()."""
+    L0, L1, L2, L3 = (int(x) for x in dims)
+    _check(load_library().su3_plaquette_noalloc(ctypes.c_void_p(links_ptr), L0, L1, L2, L3, int(precision),
+                                                ctypes.c_void_p(out_ptr), ctypes.c_void_p(cuda_stream or None)))
 
 
 def links_shape(L):

@@ -144,6 +144,8 @@ int sync(su3_lattice* h, const char* what) {
 
 }  // namespace
 
+int su3_internal_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+
 extern "C" {
 
 const char* su3_last_error(void) { return g_err; }

@@ -49,3 +49,6 @@ cudaError_t su3k_launch_init(const InitArgs& a, bool hot, cudaStream_t s);
 int su3k_plaquette_blocks(const su3dev::Geometry& g);
 cudaError_t su3k_launch_plaquette(const PlaqArgs& a, int precision, double* out, cudaStream_t s);
 cudaError_t su3k_launch_conv(const ConvArgs& a, bool to_store, cudaStream_t s);
+
+// Record a failure for su3_last_error() (thread-local); returns code.
+int su3_internal_fail(int code, const char* msg);

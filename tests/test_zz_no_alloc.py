@@ -1,0 +1,60 @@
+"""su3_plaquette_noalloc: the plaquette for callers that cannot allocate device
+memory (for example code running under CUDA stream capture, or runtimes that
+only hand out memory from their own pool).  The entry point keeps its scratch
+in a fixed device array instead of allocating; this test checks, through the C
+ABI, that it returns what the allocating su3_plaquette returns, on two calls in
+a row.  The file is named to be collected last."""
+import numpy as np
+import pytest
+
+import paper_0904_1179_gb300 as su3
+from paper_0904_1179_gb300 import build as su3_build
+
+pytestmark = pytest.mark.gpu
+
+
+def device_layout(U, L, precision):
+    """Canonical host links -> the library's device layout (index permutation only)."""
+    V = int(np.prod(L))
+    flat = U.reshape(V, 4, 3, 3, 2)
+    x = np.indices((L[3], L[2], L[1], L[0])).reshape(4, -1)
+    parity = (x.sum(axis=0) % 2).astype(bool)
+    if precision == su3.SU3_FP64:
+        soa = np.empty((4, 2, 9, V // 2, 2), dtype=np.float64)
+        for p in (0, 1):
+            sel = flat[parity == bool(p)].reshape(V // 2, 4, 9, 2)
+            soa[:, p] = sel.transpose(1, 2, 0, 3)
+    else:
+        soa = np.empty((4, 2, 3, V // 2, 4), dtype=np.float32)
+        for p in (0, 1):
+            sel = flat[parity == bool(p)][:, :, :2].reshape(V // 2, 4, 3, 4)
+            soa[:, p] = sel.transpose(1, 2, 0, 3).astype(np.float32)
+    return np.ascontiguousarray(soa)
+
+
+@pytest.mark.parametrize("precision,tol", [(su3.SU3_FP64, 1e-13), (su3.SU3_FP32_MIXED, 1e-12)])
+def test_noalloc_plaquette_matches_allocating_entry_point(precision, tol):
+    torch = pytest.importorskip("torch")
+    su3_build.build()
+    L = (8, 6, 4, 10)
+    stream = torch.cuda.current_stream()
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    expect = []
+    with su3.Lattice(L, 5.7, 12, start=su3.SU3_HOT, precision=precision) as lat:
+        for call in range(2):  # two calls in a row, on two different configurations
+            lat.sweep(2)
+            expect.append(lat.plaquette())
+            dev = torch.from_numpy(device_layout(lat.get_links(), L, precision)).cuda()
+            su3.su3_plaquette_noalloc(dev.data_ptr(), L, precision, out[call:].data_ptr(), stream.cuda_stream)
+            torch.cuda.synchronize()
+            assert abs(out[call].item() - expect[call]) < tol, (call, out[call].item(), expect[call])
+    assert expect[0] != expect[1]
+
+
+def test_noalloc_rejects_oversized_lattice():
+    torch = pytest.importorskip("torch")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    links = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(su3.Su3Error) as e:
+        su3.su3_plaquette_noalloc(links.data_ptr(), (66, 64, 64, 64), su3.SU3_FP64, out.data_ptr())
+    assert e.value.code == -5 and "64^4" in str(e.value)
