@@ -96,10 +96,11 @@ void release(su3_lattice* h) {
 HalfSweepArgs half_sweep_args(const su3_lattice* h, int parity) {
   HalfSweepArgs a{};
   a.geom = h->geom;
-  a.key = h->key;
+  a.key = su3dev::philox_round_keys(h->key);
   a.parity = parity;
   a.beta = h->beta;
   a.inv_beta15 = (float)(1.5 / h->beta);
+  a.inv_beta15_f64 = 1.5 / h->beta;
   a.sweep = h->d_sweep;
   a.links = h->links;
   a.stats = h->d_stats;
@@ -219,7 +220,7 @@ int su3_create_ex(int L0, int L1, int L2, int L3, double beta, uint64_t seed, in
     rc = cuda_fail(e, "su3_create: memset");
   }
   if (rc == SU3_OK) {
-    InitArgs ia{h->geom, h->key, precision, h->links};
+    InitArgs ia{h->geom, su3dev::philox_round_keys(h->key), precision, h->links};
     e = su3k_launch_init(ia, start == SU3_HOT, h->stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "su3_create: start configuration");
   }

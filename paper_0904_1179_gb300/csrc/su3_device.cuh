@@ -49,22 +49,36 @@ struct PhiloxKey {
   uint32_t k0, k1;
 };
 
-// ---------------------------------------------------------------------------
-// Philox4x32-10 block function.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key) {
+// The ten round keys of one seed (key, key + W, ..., key + 9W), computed once
+// on the host so that each round reads them from the kernel's parameter bank.
+struct PhiloxRoundKeys {
+  uint32_t k[10][2];
+};
+
+__host__ __device__ inline PhiloxRoundKeys philox_round_keys(PhiloxKey key) {
+  PhiloxRoundKeys rk;
   uint32_t k0 = key.k0, k1 = key.k1;
+  for (int r = 0; r < 10; ++r) {
+    rk.k[r][0] = k0;
+    rk.k[r][1] = k1;
+    k0 += kPhiloxWeylA;
+    k1 += kPhiloxWeylB;
+  }
+  return rk;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 block function: ten rounds, each two 32x32->64-bit products
+// and a xor with the round key.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxRoundKeys& rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    if (r > 0) {
-      k0 += kPhiloxWeylA;
-      k1 += kPhiloxWeylB;
-    }
     const uint32_t lo_a = kPhiloxMulA * c.x;
     const uint32_t hi_a = __umulhi(kPhiloxMulA, c.x);
     const uint32_t lo_b = kPhiloxMulB * c.z;
     const uint32_t hi_b = __umulhi(kPhiloxMulB, c.z);
-    c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+    c = make_uint4(hi_b ^ c.y ^ rk.k[r][0], lo_b, hi_a ^ c.w ^ rk.k[r][1], lo_a);
   }
   return c;
 }
@@ -322,7 +336,7 @@ __device__ __forceinline__ void gram_schmidt_rows01(cx<double> r0[3], cx<double>
   double n0 = 0.0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) n0 = fma(r0[k].re, r0[k].re, fma(r0[k].im, r0[k].im, n0));
-  const double i0 = 1.0 / sqrt(n0);
+  const double i0 = rsqrt(n0);
 #pragma unroll
   for (int k = 0; k < 3; ++k) r0[k] = mk(r0[k].re * i0, r0[k].im * i0);
   cx<double> d = mk(0.0, 0.0);
@@ -333,9 +347,70 @@ __device__ __forceinline__ void gram_schmidt_rows01(cx<double> r0[3], cx<double>
   double n1 = 0.0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) n1 = fma(r1[k].re, r1[k].re, fma(r1[k].im, r1[k].im, n1));
-  const double i1 = 1.0 / sqrt(n1);
+  const double i1 = rsqrt(n1);
 #pragma unroll
   for (int k = 0; k < 3; ++k) r1[k] = mk(r1[k].re * i1, r1[k].im * i1);
+}
+
+// ---------------------------------------------------------------------------
+// Reunitarisation of an FP32 link (rows 0, 1) for FP32 storage.
+//
+// The Gram-Schmidt coefficients -- the norms n0 = |r0|^2, n1 = |r1|^2 and the
+// overlap d = <r0, r1> -- are accumulated in FP64 from the exact products of
+// the FP32 entries; these sums are where cancellation needs the precision.
+// For a link that is unitary to within e = n - 1 = O(1e-6) (every link after
+// a heatbath step), the exact Gram-Schmidt result is then applied in FP32 as
+//   r0' = r0 (1 + s0),           s0 = 1/sqrt(1 + e0) - 1 = -e0/2 + 3 e0^2/8
+//   r1' = (r1 - c r0)(1 + s1),   c = d / n0,  e1 = n1 - |d|^2/n0 - 1,
+// each entry by one FMA, i.e. within one FP32 rounding of the FP64
+// Gram-Schmidt followed by rounding to FP32 (the series remainder is below
+// |e|^3 < 1e-9).  Links far from unitary (|e| or |d| >= 1e-3, e.g. arbitrary
+// input from links_set) take the full FP64 Gram-Schmidt instead.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void reunitarise_f32(const cx<float> a[3], const cx<float> b[3], float out[12]) {
+  double n0 = 0.0, n1 = 0.0, dre = 0.0, dim = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double ar = a[k].re, ai = a[k].im, br = b[k].re, bi = b[k].im;
+    n0 = fma(ar, ar, fma(ai, ai, n0));
+    n1 = fma(br, br, fma(bi, bi, n1));
+    dre = fma(ar, br, fma(ai, bi, dre));
+    dim = fma(ar, bi, fma(-ai, br, dim));
+  }
+  const float e0 = (float)(n0 - 1.0);
+  const float dr = (float)dre, di = (float)dim;
+  const float inv_n0 = 1.0f - e0;  // 1/n0 to O(e0^2)
+  const float cr = dr * inv_n0, ci = di * inv_n0;
+  const float e1 = (float)(n1 - 1.0) - (cr * dr + ci * di);
+  if (fabsf(e0) < 1e-3f && fabsf(e1) < 1e-3f && fabsf(dr) < 1e-3f && fabsf(di) < 1e-3f) {
+    const float s0 = e0 * fmaf(0.375f, e0, -0.5f);
+    const float s1 = e1 * fmaf(0.375f, e1, -0.5f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      out[2 * k] = fmaf(a[k].re, s0, a[k].re);
+      out[2 * k + 1] = fmaf(a[k].im, s0, a[k].im);
+      // r1 - c r0
+      const float tr = fmaf(-cr, a[k].re, fmaf(ci, a[k].im, b[k].re));
+      const float ti = fmaf(-cr, a[k].im, fmaf(-ci, a[k].re, b[k].im));
+      out[6 + 2 * k] = fmaf(tr, s1, tr);
+      out[6 + 2 * k + 1] = fmaf(ti, s1, ti);
+    }
+  } else {
+    cx<double> r0[3], r1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      r0[k] = mk((double)a[k].re, (double)a[k].im);
+      r1[k] = mk((double)b[k].re, (double)b[k].im);
+    }
+    gram_schmidt_rows01(r0, r1);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      out[2 * k] = (float)r0[k].re;
+      out[2 * k + 1] = (float)r0[k].im;
+      out[6 + 2 * k] = (float)r1[k].re;
+      out[6 + 2 * k + 1] = (float)r1[k].im;
+    }
+  }
 }
 
 }  // namespace su3dev

@@ -15,6 +15,13 @@
 
 using namespace su3dev;
 
+// Register budget of the FP32-mixed half-sweep: __launch_bounds__(threads,
+// min blocks per SM).  The defaults keep every block size up to
+// kMaxSweepThreads legal.
+#ifndef SU3_F32_MINBLOCKS
+#define SU3_F32_MINBLOCKS 3
+#endif
+
 namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
@@ -150,7 +157,7 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64(HalfSweepAr
       const int i = subrow_i(sub), j = subrow_j(sub);
       double r[4];
       su2_projection(u, A, i, j, r);
-      const double k = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+      const double kk = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
       double uu[6];
 #pragma unroll
       for (int call = 0; call < 3; ++call) {
@@ -158,10 +165,11 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64(HalfSweepAr
         uu[2 * call] = u01_f64(w.x, w.y);
         uu[2 * call + 1] = u01_f64(w.z, w.w);
       }
-      if (!(k > 1e-300)) continue;
-      const double alpha = 2.0 * args.beta * k / 3.0;
+      if (!(kk > 0.0)) continue;  // k = 0: degenerate staple (measure zero), leave the subgroup
+      const double ik = rsqrt(kk);
+      const double inv_alpha = args.inv_beta15_f64 * ik;  // 1/alpha = 3 / (2 beta k)
       const double c = cos(kTwoPi * uu[1]);
-      const double delta = -(log(uu[0]) + c * c * log(uu[2])) / alpha;
+      const double delta = -(log(uu[0]) + c * c * log(uu[2])) * inv_alpha;
       if (uu[3] * uu[3] > 1.0 - 0.5 * delta) continue;
       const double a0 = 1.0 - delta;
       double rho = 1.0 - a0 * a0;
@@ -172,7 +180,7 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64(HalfSweepAr
       double sphi, cphi;
       sincos(kTwoPi * uu[5], &sphi, &cphi);
       const double a[4] = {a0, rho * sn * cphi, rho * sn * sphi, rho * ct};
-      const double v[4] = {r[0] / k, r[1] / k, r[2] / k, r[3] / k};
+      const double v[4] = {r[0] * ik, r[1] * ik, r[2] * ik, r[3] * ik};
       apply_su2(u, i, j, a, v);
       ++accepted;
     }
@@ -203,7 +211,7 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64(HalfSweepAr
 // FP64 Gram-Schmidt.
 // ---------------------------------------------------------------------------
 template <int MU, bool STATS>
-__global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f32(HalfSweepArgs args) {
+__global__ void __launch_bounds__(kMaxSweepThreads, SU3_F32_MINBLOCKS) k_half_sweep_f32(HalfSweepArgs args) {
   const Geometry g = args.geom;
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   int accepted = 0;
@@ -245,21 +253,8 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f32(HalfSweepAr
       apply_su2(u, i, j, a, v);
       ++accepted;
     }
-    cx<double> r0[3], r1[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      r0[k] = mk((double)u.e[0][k].re, (double)u.e[0][k].im);
-      r1[k] = mk((double)u.e[1][k].re, (double)u.e[1][k].im);
-    }
-    gram_schmidt_rows01(r0, r1);
     float o[12];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      o[2 * k] = (float)r0[k].re;
-      o[2 * k + 1] = (float)r0[k].im;
-      o[6 + 2 * k] = (float)r1[k].re;
-      o[6 + 2 * k + 1] = (float)r1[k].im;
-    }
+    reunitarise_f32(u.e[0], u.e[1], o);
     store_f32_rows01(U, MU, p, h, g.Vh, o);
   }
   if (STATS) {

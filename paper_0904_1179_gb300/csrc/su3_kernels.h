@@ -12,9 +12,10 @@ constexpr int kMaxSweepThreads = 256;
 
 struct HalfSweepArgs {
   su3dev::Geometry geom;
-  su3dev::PhiloxKey key;
+  su3dev::PhiloxRoundKeys key;
   int parity;
   double beta;        // FP64 path
+  double inv_beta15_f64;  // FP64 path: 1.5 / beta
   float inv_beta15;   // FP32 path: 1.5 / beta, so that 1/alpha = inv_beta15 / k
   const uint64_t* sweep;  // device sweep counter (RNG position)
   void* links;
@@ -23,7 +24,7 @@ struct HalfSweepArgs {
 
 struct InitArgs {
   su3dev::Geometry geom;
-  su3dev::PhiloxKey key;
+  su3dev::PhiloxRoundKeys key;
   int precision;
   void* links;
 };

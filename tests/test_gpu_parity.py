@@ -89,7 +89,7 @@ def test_hot_start_matches_oracle(L):
     with su3.Lattice(L, BETA, 7, start=su3.SU3_HOT, precision=su3.SU3_FP64) as lat:
         G = lat.get_links()
     O = oracle.hot_start(L, 7)
-    assert np.abs(G - O).max() < 1e-14
+    assert np.abs(G - O).max() < 1e-13
     with su3.Lattice(L, BETA, 7, start=su3.SU3_HOT, precision=su3.SU3_FP32_MIXED) as lat:
         G = lat.get_links()
     O = oracle.hot_start(L, 7, f32=True)
@@ -297,8 +297,9 @@ def test_full_size_32x4_sampled(prec):
     rng = np.random.default_rng(1)
     with su3.Lattice(L, BETA, seed, start=su3.SU3_HOT, precision=prec) as lat:
         G0 = lat.get_links()
-        # GPU hot start = oracle hot start
-        assert np.abs(G0 - U0).max() < (2.5e-7 if f32 else 1e-14)
+        # GPU hot start = oracle hot start (Gram-Schmidt of Gaussian rows amplifies
+        # rounding by 1/|r1 - proj|, ~100 for the worst of 4.2M links)
+        assert np.abs(G0 - U0).max() < (2.5e-7 if f32 else 1e-13)
         lat.set_links(U0)
         for mu, p in ((0, 0), (3, 1)):
             lat.set_links(U0)
