@@ -146,6 +146,75 @@ SU3_API int su3_info(su3_handle h, int dims[4], double* beta, uint64_t* seed, in
  * keyed by its site. */
 SU3_API int su3_set_block_size(su3_handle h, int threads);
 
+/* ---------------------------------------------------------------------------
+ * Batches: n independent replicas, each with its own extents, beta and Philox
+ * seed (the same counter layout, keyed by the replica's seed), swept together
+ * by ONE persistent kernel launch per sweep, captured in a CUDA graph.  Each
+ * replica performs exactly the single-lattice sweep: replica r after k sweeps
+ * equals a lattice created alone with dims[r], betas[r], seeds[r] after k
+ * sweeps, bit for bit.
+ * ------------------------------------------------------------------------- */
+
+/* Create a batch.  dims[r] = {L0, L1, L2, L3} of replica r (even, >= 2),
+ * betas[r] > 0, seeds[r] its Philox key; start and precision as for
+ * su3_create_ex (one of each for all replicas); cuda_stream as for
+ * su3_create_ex.  The handle is a batch handle: use the su3_batch_* calls,
+ * su3_sweep_count/su3_set_sweep_count (one sweep index for all replicas),
+ * su3_status and su3_destroy.  Arrays are read during the call only.
+ * Errors: SU3_EINVAL (bad n, extent, beta, enum, NULL), SU3_ENOMEM, SU3_ECUDA.
+ * The tile and grid configuration comes from an earlier su3_batch_autotune of
+ * the same replica set in this process, if there was one. */
+SU3_API int su3_batch_create(int n, const int (*dims)[4], const double* betas, const uint64_t* seeds, int start,
+                             int precision, void* cuda_stream, su3_handle* out);
+
+/* nsweeps sweeps of every replica; asynchronous, one graph replay (memset of
+ * the arrival counters, the persistent sweep kernel, the sweep-counter
+ * increment) per sweep.  Inside the kernel, a tile of phase k of replica r
+ * waits for all tiles of phase k-1 of r; the wait is bounded in time and, if
+ * it runs out, the sweep stops and the next synchronising call returns
+ * SU3_ETIMEOUT (the configuration is then incomplete). */
+SU3_API int su3_batch_sweep(su3_handle b, int nsweeps);
+
+/* Mean plaquette of every replica (definition of su3_plaquette) into out_n[0..n-1].
+ * Synchronises; SU3_ETIMEOUT if an earlier batched sweep timed out. */
+SU3_API int su3_batch_plaquettes(su3_handle b, double* out_n);
+
+/* Copy replica `replica` to/from a host buffer in the canonical layout of
+ * su3_links_get/set (n_doubles = V_r * 72).  Synchronises. */
+SU3_API int su3_batch_links_get(su3_handle b, int replica, double* host, size_t n_doubles);
+SU3_API int su3_batch_links_set(su3_handle b, int replica, const double* host, size_t n_doubles);
+
+/* Number of replicas. */
+SU3_API int su3_batch_size(su3_handle b, int* n);
+
+/* Dispatch configuration: threads per block (= half-sites per tile, a multiple
+ * of 32 in [32, 256]; 0 = 128), persistent blocks per SM (0 = as many as fit),
+ * replicas per L2 window (0 = all: phase-major order over the whole batch).
+ * Results do not depend on it. */
+SU3_API int su3_batch_config(su3_handle b, int threads, int blocks_per_sm, int window);
+SU3_API int su3_batch_get_config(su3_handle b, int* threads, int* blocks_per_sm, int* window);
+
+/* Time every candidate configuration (threads 64/128/256, blocks per SM up to
+ * the occupancy limit, windows of n, n/2, n/4, ... replicas) on this batch,
+ * keep the fastest, and remember it for batches of the same replica extents
+ * and precision on the same GPU model in this process.  The links and the
+ * sweep index are saved before and restored after tuning, so the chain is
+ * unchanged.  Outputs (may be NULL) receive the chosen configuration.
+ * Allocates a temporary copy of the links. */
+SU3_API int su3_batch_autotune(su3_handle b, int* threads, int* blocks_per_sm, int* window);
+
+/* Fault-detection hook.  wait_limit_s (0 < limit <= 60) bounds each wait of
+ * the batched sweep (default 2 s); withhold_item >= 0 makes that work item
+ * (in dispatch order) never signal its completion, so that the waits on it
+ * run out -- the way to test SU3_ETIMEOUT without faulting the GPU.  -1
+ * disables withholding. */
+SU3_API int su3_batch_debug(su3_handle b, double wait_limit_s, int withhold_item);
+
+/* Synchronise the handle's stream and report asynchronous failures:
+ * SU3_ETIMEOUT if a batched sweep gave up waiting (the status is then cleared),
+ * SU3_ECUDA for a CUDA error, else SU3_OK. */
+SU3_API int su3_status(su3_handle h);
+
 /* Mean plaquette of a link store held by the caller in device memory,
  * computed without allocating any memory.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc -- code that runs

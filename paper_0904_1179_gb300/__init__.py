@@ -20,7 +20,9 @@ __all__ = [
     "SU3_COLD", "SU3_HOT", "SU3_FP64", "SU3_FP32_MIXED", "Su3Error", "load_library", "library_path",
     "su3_create", "su3_create_ex", "su3_destroy", "su3_sweep", "su3_half_sweep", "su3_plaquette",
     "su3_links_get", "su3_links_set", "su3_sweep_count", "su3_set_sweep_count", "su3_set_stats", "su3_stats",
-    "su3_info", "su3_set_block_size", "su3_plaquette_noalloc", "su3_last_error", "su3_version", "Lattice", "links_shape", "EXPORTS",
+    "su3_info", "su3_set_block_size", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
+    "su3_batch_links_get", "su3_batch_links_set", "su3_batch_size", "su3_batch_config", "su3_batch_get_config",
+    "su3_batch_autotune", "su3_batch_debug", "su3_status", "Batch", "su3_plaquette_noalloc", "su3_last_error", "su3_version", "Lattice", "links_shape", "EXPORTS",
 ]
 
 SU3_COLD, SU3_HOT = 0, 1
@@ -57,6 +59,18 @@ EXPORTS = [
     ("su3_stats", ctypes.c_int, [_h, _pu64, _pu64]),
     ("su3_info", ctypes.c_int, [_h, _pi, _pd, _pu64, _pi]),
     ("su3_set_block_size", ctypes.c_int, [_h, ctypes.c_int]),
+    ("su3_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _pd, _pu64, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(_h)]),
+    ("su3_batch_sweep", ctypes.c_int, [_h, ctypes.c_int]),
+    ("su3_batch_plaquettes", ctypes.c_int, [_h, _pd]),
+    ("su3_batch_links_get", ctypes.c_int, [_h, ctypes.c_int, _pd, ctypes.c_size_t]),
+    ("su3_batch_links_set", ctypes.c_int, [_h, ctypes.c_int, _pd, ctypes.c_size_t]),
+    ("su3_batch_size", ctypes.c_int, [_h, _pi]),
+    ("su3_batch_config", ctypes.c_int, [_h, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("su3_batch_get_config", ctypes.c_int, [_h, _pi, _pi, _pi]),
+    ("su3_batch_autotune", ctypes.c_int, [_h, _pi, _pi, _pi]),
+    ("su3_batch_debug", ctypes.c_int, [_h, ctypes.c_double, ctypes.c_int]),
+    ("su3_status", ctypes.c_int, [_h]),
     ("su3_plaquette_noalloc", ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5 + [ctypes.c_void_p,
                                                                                       ctypes.c_void_p]),
     ("su3_last_error", ctypes.c_char_p, []),
@@ -190,6 +204,72 @@ def su3_set_block_size(h, threads):
     _check(load_library().su3_set_block_size(h, threads))
 
 
+def su3_batch_create(dims, betas, seeds, start, precision, cuda_stream=None):
+    """dims: sequence of n (L0, L1, L2, L3); betas, seeds: length n."""
+    n = len(dims)
+    if len(betas) != n or len(seeds) != n:
+        raise ValueError("dims, betas and seeds must have the same length")
+    d = (ctypes.c_int * (4 * n))(*[int(x) for L in dims for x in L])
+    b = (ctypes.c_double * n)(*[float(x) for x in betas])
+    s = (ctypes.c_uint64 * n)(*[int(x) for x in seeds])
+    h = _h()
+    _check(load_library().su3_batch_create(n, d, b, s, int(start), int(precision), ctypes.c_void_p(cuda_stream or None),
+                                           ctypes.byref(h)))
+    return h
+
+
+def su3_batch_sweep(h, nsweeps):
+    _check(load_library().su3_batch_sweep(h, nsweeps))
+
+
+def su3_batch_plaquettes(h, n):
+    out = (ctypes.c_double * n)()
+    _check(load_library().su3_batch_plaquettes(h, out))
+    return list(out)
+
+
+def su3_batch_links_get(h, replica, out):
+    ptr, n = _host_buffer(out, True)
+    _check(load_library().su3_batch_links_get(h, int(replica), ptr, n))
+    return out
+
+
+def su3_batch_links_set(h, replica, links):
+    ptr, n = _host_buffer(links, False)
+    _check(load_library().su3_batch_links_set(h, int(replica), ptr, n))
+
+
+def su3_batch_size(h):
+    n = ctypes.c_int()
+    _check(load_library().su3_batch_size(h, ctypes.byref(n)))
+    return n.value
+
+
+def su3_batch_config(h, threads=0, blocks_per_sm=0, window=0):
+    _check(load_library().su3_batch_config(h, int(threads), int(blocks_per_sm), int(window)))
+
+
+def su3_batch_get_config(h):
+    t, b, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load_library().su3_batch_get_config(h, ctypes.byref(t), ctypes.byref(b), ctypes.byref(w)))
+    return t.value, b.value, w.value
+
+
+def su3_batch_autotune(h):
+    t, b, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load_library().su3_batch_autotune(h, ctypes.byref(t), ctypes.byref(b), ctypes.byref(w)))
+    return t.value, b.value, w.value
+
+
+def su3_batch_debug(h, wait_limit_s, withhold_item=-1):
+    _check(load_library().su3_batch_debug(h, float(wait_limit_s), int(withhold_item)))
+
+
+def su3_status(h):
+    """Synchronise; raises Su3Error (code SU3_ETIMEOUT or SU3_ECUDA) on an asynchronous failure."""
+    _check(load_library().su3_status(h))
+
+
 def su3_plaquette_noalloc(links_ptr, dims, precision, out_ptr, cuda_stream=None):
     """Mean plaquette of a device-resident link store (library device layout) into the
     device double at out_ptr, without any allocation; asynchronous on cuda_stream.
@@ -204,6 +284,74 @@ def su3_plaquette_noalloc(links_ptr, dims, precision, out_ptr, cuda_stream=None)
 def links_shape(L):
     """Canonical host layout of a configuration: U[L3][L2][L1][L0][mu][row][col][re/im]."""
     return (L[3], L[2], L[1], L[0], 4, 3, 3, 2)
+
+
+class Batch:
+    """Owning wrapper of a batch handle: n replicas swept by one launch per sweep."""
+
+    def __init__(self, dims, betas, seeds, start=SU3_HOT, precision=SU3_FP32_MIXED, stream=None):
+        self.dims = [tuple(int(x) for x in L) for L in dims]
+        self.n = len(self.dims)
+        self.handle = su3_batch_create(self.dims, betas, seeds, start, precision, stream)
+        self.precision = int(precision)
+
+    def close(self):
+        if self.handle is not None:
+            su3_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def updates_per_sweep(self):
+        return int(sum(4 * np.prod(L) for L in self.dims))
+
+    def sweep(self, n=1):
+        su3_batch_sweep(self.handle, n)
+
+    def plaquettes(self):
+        return su3_batch_plaquettes(self.handle, self.n)
+
+    def get_links(self, replica, out=None):
+        if out is None:
+            out = np.empty(links_shape(self.dims[replica]), dtype=np.float64)
+        return su3_batch_links_get(self.handle, replica, out)
+
+    def set_links(self, replica, links):
+        su3_batch_links_set(self.handle, replica, np.ascontiguousarray(links, dtype=np.float64))
+
+    @property
+    def sweep_count(self):
+        return su3_sweep_count(self.handle)
+
+    @sweep_count.setter
+    def sweep_count(self, n):
+        su3_set_sweep_count(self.handle, int(n))
+
+    def config(self, threads=0, blocks_per_sm=0, window=0):
+        su3_batch_config(self.handle, threads, blocks_per_sm, window)
+
+    def get_config(self):
+        return su3_batch_get_config(self.handle)
+
+    def autotune(self):
+        return su3_batch_autotune(self.handle)
+
+    def debug(self, wait_limit_s, withhold_item=-1):
+        su3_batch_debug(self.handle, wait_limit_s, withhold_item)
+
+    def status(self):
+        su3_status(self.handle)
 
 
 class Lattice:

@@ -11,14 +11,15 @@
 #include <cstring>
 #include <new>
 
-#include "su3.h"
-#include "su3_kernels.h"
+#include "su3_runtime.h"
 
 namespace {
 
 thread_local char g_err[512] = "";
 
-int fail(int code, const char* fmt, ...) {
+}  // namespace
+
+int su3_fail(int code, const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
   vsnprintf(g_err, sizeof g_err, fmt, ap);
@@ -26,46 +27,33 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
-int cuda_fail(cudaError_t e, const char* what) {
-  if (e == cudaErrorMemoryAllocation) return fail(SU3_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
-  return fail(SU3_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+int su3_cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return su3_fail(SU3_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return su3_fail(SU3_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define SU3_CUDA(call, what)                   \
-  do {                                         \
-    cudaError_t e_ = (call);                   \
-    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-  } while (0)
+int su3_sync(su3_lattice* h, const char* what) {
+  SU3_CUDA(cudaStreamSynchronize(h->stream), what);
+  SU3_CUDA(cudaGetLastError(), what);
+  return SU3_OK;
+}
 
-constexpr int kDefaultThreads = 128;
-constexpr long long kChunkSites = 1LL << 16;  // layout-conversion chunk (37.7 MB of FP64 links)
+namespace {
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  return su3_fail(code, "%s", buf);
+}
+
+int cuda_fail(cudaError_t e, const char* what) { return su3_cuda_fail(e, what); }
+
+constexpr int kDefaultThreads = kSu3DefaultThreads;
 
 }  // namespace
-
-struct su3_lattice {
-  int L[4] = {0, 0, 0, 0};
-  long long V = 0;
-  double beta = 0.0;
-  uint64_t seed = 0;
-  int precision = SU3_FP64;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  void* links = nullptr;
-  size_t link_bytes = 0;
-  uint64_t* d_sweep = nullptr;
-  uint64_t sweep_host = 0;
-  unsigned long long* d_stats = nullptr;
-  bool stats_on = false;
-  double* d_partials = nullptr;
-  double* d_plaq = nullptr;
-  double* h_plaq = nullptr;  // pinned
-  unsigned long long* h_stats = nullptr;  // pinned, 2 words
-  double* d_stage = nullptr;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // indexed by stats_on
-  int threads = kDefaultThreads;
-  su3dev::Geometry geom{};
-  su3dev::PhiloxKey key{};
-};
 
 namespace {
 
@@ -81,6 +69,7 @@ void release(su3_lattice* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graphs(h);
+  if (h->batch) su3_batch_release(h->batch);
   cudaFree(h->links);
   cudaFree(h->d_sweep);
   cudaFree(h->d_stats);
@@ -137,15 +126,16 @@ int ensure_graph(su3_lattice* h) {
   return SU3_OK;
 }
 
-int sync(su3_lattice* h, const char* what) {
-  SU3_CUDA(cudaStreamSynchronize(h->stream), what);
-  SU3_CUDA(cudaGetLastError(), what);
-  return SU3_OK;
-}
+int sync(su3_lattice* h, const char* what) { return su3_sync(h, what); }
+
+// Single-lattice calls reject batch handles and vice versa.
+bool is_batch(const su3_lattice* h) { return h && h->batch; }
 
 }  // namespace
 
-int su3_internal_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+void su3_release_handle(su3_lattice* h) { release(h); }
+
+int su3_internal_fail(int code, const char* msg) { return su3_fail(code, "%s", msg); }
 
 extern "C" {
 
@@ -244,6 +234,7 @@ int su3_destroy(su3_handle h) {
 
 int su3_sweep(su3_handle h, int nsweeps) {
   if (!h) return fail(SU3_EINVAL, "su3_sweep: NULL handle");
+  if (is_batch(h)) return fail(SU3_EINVAL, "su3_sweep: batch handle (use the su3_batch_* calls)");
   if (nsweeps < 0) return fail(SU3_EINVAL, "su3_sweep: nsweeps < 0");
   if (nsweeps == 0) return SU3_OK;
   int rc = ensure_graph(h);
@@ -256,6 +247,7 @@ int su3_sweep(su3_handle h, int nsweeps) {
 
 int su3_half_sweep(su3_handle h, int mu, int parity) {
   if (!h) return fail(SU3_EINVAL, "su3_half_sweep: NULL handle");
+  if (is_batch(h)) return fail(SU3_EINVAL, "su3_half_sweep: batch handle (use the su3_batch_* calls)");
   if (mu < 0 || mu > 3 || parity < 0 || parity > 1) return fail(SU3_EINVAL, "su3_half_sweep: bad mu/parity");
   SU3_CUDA(su3k_launch_half_sweep(half_sweep_args(h, parity), mu, h->precision, h->stats_on, h->threads, h->stream),
            "su3_half_sweep");
@@ -263,8 +255,8 @@ int su3_half_sweep(su3_handle h, int mu, int parity) {
 }
 
 double su3_plaquette(su3_handle h) {
-  if (!h) {
-    fail(SU3_EINVAL, "su3_plaquette: NULL handle");
+  if (!h || is_batch(h)) {
+    fail(SU3_EINVAL, h ? "su3_plaquette: batch handle (use su3_batch_plaquettes)" : "su3_plaquette: NULL handle");
     return NAN;
   }
   PlaqArgs a{h->geom, h->links, h->d_partials};
@@ -280,6 +272,7 @@ double su3_plaquette(su3_handle h) {
 
 int su3_links_get(su3_handle h, double* host, size_t n_doubles) {
   if (!h || !host) return fail(SU3_EINVAL, "su3_links_get: NULL argument");
+  if (is_batch(h)) return fail(SU3_EINVAL, "su3_links_get: batch handle (use the su3_batch_* calls)");
   if (n_doubles != (size_t)h->V * 72) return fail(SU3_ESIZE, "su3_links_get: n = %zu, expected %lld", n_doubles, h->V * 72);
   for (long long s0 = 0; s0 < h->V; s0 += kChunkSites) {
     const long long n = (h->V - s0) < kChunkSites ? (h->V - s0) : kChunkSites;
@@ -294,6 +287,7 @@ int su3_links_get(su3_handle h, double* host, size_t n_doubles) {
 
 int su3_links_set(su3_handle h, const double* host, size_t n_doubles) {
   if (!h || !host) return fail(SU3_EINVAL, "su3_links_set: NULL argument");
+  if (is_batch(h)) return fail(SU3_EINVAL, "su3_links_set: batch handle (use the su3_batch_* calls)");
   if (n_doubles != (size_t)h->V * 72) return fail(SU3_ESIZE, "su3_links_set: n = %zu, expected %lld", n_doubles, h->V * 72);
   for (long long s0 = 0; s0 < h->V; s0 += kChunkSites) {
     const long long n = (h->V - s0) < kChunkSites ? (h->V - s0) : kChunkSites;
@@ -321,6 +315,7 @@ int su3_set_sweep_count(su3_handle h, uint64_t n) {
 
 int su3_set_stats(su3_handle h, int enable) {
   if (!h) return fail(SU3_EINVAL, "su3_set_stats: NULL handle");
+  if (is_batch(h)) return fail(SU3_EINVAL, "su3_set_stats: batch handle (use the su3_batch_* calls)");
   h->stats_on = enable != 0;
   if (h->stats_on)
     SU3_CUDA(cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(unsigned long long), h->stream), "su3_set_stats");
@@ -350,6 +345,7 @@ int su3_info(su3_handle h, int dims[4], double* beta, uint64_t* seed, int* preci
 
 int su3_set_block_size(su3_handle h, int threads) {
   if (!h) return fail(SU3_EINVAL, "su3_set_block_size: NULL handle");
+  if (is_batch(h)) return fail(SU3_EINVAL, "su3_set_block_size: batch handle (use the su3_batch_* calls)");
   if (threads == 0) threads = kDefaultThreads;
   if (threads < 32 || threads > kMaxSweepThreads || (threads & 31))
     return fail(SU3_EINVAL, "su3_set_block_size: %d is not a multiple of 32 in [32, %d]", threads, kMaxSweepThreads);

@@ -1,0 +1,659 @@
+// su3_batch.cu -- many independent replicas (each with its own extents, beta and
+// seed) swept together: one persistent launch per sweep, captured in a CUDA
+// graph.
+//
+// Every replica runs the checkerboard sweep of Berg & Wu (arXiv:0904.1179,
+// Abstract and Sec. 1): eight dependent half-sweep phases (mu = 0..3, even then
+// odd sites).  Small replicas cannot fill a GB300 one phase at a time, so one
+// launch interleaves all replicas' phases:
+//   - the work of a sweep is a list of items (replica, phase, tile of `threads`
+//     consecutive half-sites), ordered window by window -- a window is a group of
+//     replicas small enough to stay resident in L2 across its eight phases --
+//     and within a window phase by phase;
+//   - persistent thread blocks (a whole number of blocks per SM) take items from
+//     a device counter in that order;
+//   - a tile of phase k of replica r starts once all tiles of phase k-1 of r
+//     have signalled completion (per-(replica, phase) arrival counters).  Every
+//     item a block waits for was taken earlier by a block that is running, so
+//     the order cannot deadlock; the wait is still bounded in time and, when the
+//     bound is hit, sets a status word and makes every block stop (no hang, no
+//     trap).
+// Links written by other blocks of the same launch are read through L2 only
+// (ld.global.cg); producers fence before their arrival, consumers acquire.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "su3_runtime.h"
+#include "su3_update.cuh"
+
+using namespace su3dev;
+
+namespace {
+
+constexpr int kBatchMaxThreads = 256;
+constexpr int kStatusTimeout = 1;
+constexpr long long kDefaultWaitNs = 2000000000LL;  // 2 s: a phase of any replica takes microseconds
+
+struct ReplicaDesc {
+  Geometry g;
+  PhiloxKey key;
+  long long offset;  // first element (double2 or float4) of the replica's link store
+  double inv_beta15_f64;
+  float inv_beta15;
+  int ntiles;  // work items per phase
+};
+
+struct BatchArgs {
+  const ReplicaDesc* reps;
+  const int4* schedule;  // (replica, phase, tile, 0) per work item, in dispatch order
+  int n_items;
+  unsigned int* queue;   // next work item
+  unsigned int* done;    // [replica * 8 + phase]: tiles completed in this sweep
+  int* status;           // 0 or kStatusTimeout
+  const uint64_t* sweep;
+  void* links;
+  long long wait_ns;
+  int withhold_item;  // fault-injection hook: this item never signals completion (-1: none)
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <typename T>
+__device__ __forceinline__ void update_item(int mu, const ReplicaDesc& rd, void* links, int h, int p, uint64_t t) {
+  const UpdateConsts uc{rd.inv_beta15_f64, rd.inv_beta15};
+  if constexpr (std::is_same<T, double>::value) {
+    double2* U = (double2*)links + rd.offset;
+    switch (mu) {
+      case 0: update_link_f64<0, true>(rd.g, U, h, p, t, rd.key, uc); break;
+      case 1: update_link_f64<1, true>(rd.g, U, h, p, t, rd.key, uc); break;
+      case 2: update_link_f64<2, true>(rd.g, U, h, p, t, rd.key, uc); break;
+      default: update_link_f64<3, true>(rd.g, U, h, p, t, rd.key, uc); break;
+    }
+  } else {
+    float4* U = (float4*)links + rd.offset;
+    switch (mu) {
+      case 0: update_link_f32<0, true>(rd.g, U, h, p, t, rd.key, uc); break;
+      case 1: update_link_f32<1, true>(rd.g, U, h, p, t, rd.key, uc); break;
+      case 2: update_link_f32<2, true>(rd.g, U, h, p, t, rd.key, uc); break;
+      default: update_link_f32<3, true>(rd.g, U, h, p, t, rd.key, uc); break;
+    }
+  }
+}
+
+// Register budget of the FP32-mixed instance: blocks of 256 threads per SM.
+#ifndef SU3_BATCH_F32_MINBLOCKS
+#define SU3_BATCH_F32_MINBLOCKS 2
+#endif
+
+template <typename T>
+__global__ void __launch_bounds__(kBatchMaxThreads, std::is_same<T, float>::value ? SU3_BATCH_F32_MINBLOCKS : 1)
+    k_batch_sweep(BatchArgs a) {
+  __shared__ int4 s_item;
+  __shared__ int s_stop;
+  const uint64_t t = *a.sweep;
+  for (;;) {
+    int idx = -1;
+    if (threadIdx.x == 0) {
+      int stop = 0;
+      int4 it = make_int4(0, 0, 0, 0);
+      idx = (int)atomicAdd(a.queue, 1u);
+      if (idx >= a.n_items || ld_relaxed_s32(a.status) != 0) {
+        stop = 1;
+      } else {
+        it = a.schedule[idx];
+        if (it.y > 0) {
+          // wait until every tile of phase it.y - 1 of this replica is done
+          const unsigned need = (unsigned)a.reps[it.x].ntiles;
+          const unsigned* cnt = a.done + it.x * 8 + it.y - 1;
+          if (ld_acquire_u32(cnt) < need) {
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_u32(cnt) < need) {
+              if (ld_relaxed_s32(a.status) != 0) {
+                stop = 1;
+                break;
+              }
+              if (global_ns() - t0 > (unsigned long long)a.wait_ns) {
+                atomicCAS(a.status, 0, kStatusTimeout);
+                stop = 1;
+                break;
+              }
+              __nanosleep(128);
+            }
+          }
+        }
+      }
+      s_item = it;
+      s_stop = stop;
+    }
+    __syncthreads();
+    const int4 it = s_item;
+    if (s_stop) return;
+    const ReplicaDesc rd = a.reps[it.x];
+    const int h = it.z * (int)blockDim.x + (int)threadIdx.x;
+    if (h < rd.g.Vh) update_item<T>(it.y >> 1, rd, a.links, h, it.y & 1, t);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (idx != a.withhold_item) atomicAdd(a.done + it.x * 8 + it.y, 1u);
+    }
+  }
+}
+
+cudaError_t launch_batch(const BatchArgs& a, int precision, int blocks, int threads, cudaStream_t s) {
+  if (precision == SU3_FP64)
+    k_batch_sweep<double><<<blocks, threads, 0, s>>>(a);
+  else
+    k_batch_sweep<float><<<blocks, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+int max_blocks_per_sm(int precision, int threads) {
+  int n = 0;
+  cudaError_t e = precision == SU3_FP64
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<double>, threads, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<float>, threads, 0);
+  return e == cudaSuccess ? n : 0;
+}
+
+std::mutex g_tune_mutex;
+std::map<std::string, std::vector<int>> g_tune_cache;  // key -> {threads, blocks per SM, window}
+
+}  // namespace
+
+struct su3_batch {
+  int n = 0;
+  std::vector<Geometry> geoms;
+  std::vector<double> betas;
+  std::vector<uint64_t> seeds;
+  std::vector<long long> offsets;  // element offsets (double2 or float4)
+  size_t elem_bytes = 0;
+  ReplicaDesc* d_reps = nullptr;
+  int4* d_schedule = nullptr;
+  int n_items = 0;
+  unsigned* d_sync = nullptr;  // [0] queue, [1 + 8r + k] arrival counters
+  int* d_status = nullptr;
+  int* h_status = nullptr;  // pinned
+  double* d_plaq_n = nullptr;
+  double* h_plaq_n = nullptr;  // pinned
+  int threads = 128;
+  int blocks_per_sm = 0;  // 0: as many as fit
+  int window = 0;         // replicas per window, 0: all
+  int num_sms = 0;
+  cudaGraphExec_t graph = nullptr;
+  long long wait_ns = kDefaultWaitNs;
+  int withhold_item = -1;
+  std::string tune_key;
+};
+
+void su3_batch_release(su3_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  cudaFree(b->d_reps);
+  cudaFree(b->d_schedule);
+  cudaFree(b->d_sync);
+  cudaFree(b->d_status);
+  cudaFree(b->d_plaq_n);
+  cudaFreeHost(b->h_status);
+  cudaFreeHost(b->h_plaq_n);
+  delete b;
+}
+
+namespace {
+
+su3_batch* batch_of(su3_handle h) { return h ? h->batch : nullptr; }
+
+int fail(int code, const char* what) { return su3_fail(code, "%s", what); }
+
+void drop_graph(su3_batch* b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+int tiles_of(const Geometry& g, int threads) { return (g.Vh + threads - 1) / threads; }
+
+// Upload the replica descriptors and the dispatch order for the current tile
+// size and window.
+int build_schedule(su3_lattice* h) {
+  su3_batch* b = h->batch;
+  std::vector<ReplicaDesc> reps(b->n);
+  for (int r = 0; r < b->n; ++r) {
+    ReplicaDesc d{};
+    d.g = b->geoms[r];
+    d.key.k0 = (uint32_t)b->seeds[r];
+    d.key.k1 = (uint32_t)(b->seeds[r] >> 32);
+    d.offset = b->offsets[r];
+    d.inv_beta15_f64 = 1.5 / b->betas[r];
+    d.inv_beta15 = (float)(1.5 / b->betas[r]);
+    d.ntiles = tiles_of(d.g, b->threads);
+    reps[r] = d;
+  }
+  std::vector<int4> items;
+  const int w = b->window > 0 ? b->window : b->n;
+  for (int r0 = 0; r0 < b->n; r0 += w) {
+    const int r1 = std::min(b->n, r0 + w);
+    for (int k = 0; k < 8; ++k)
+      for (int r = r0; r < r1; ++r)
+        for (int tl = 0; tl < reps[r].ntiles; ++tl) items.push_back(make_int4(r, k, tl, 0));
+  }
+  cudaFree(b->d_schedule);
+  b->d_schedule = nullptr;
+  SU3_CUDA(cudaMalloc(&b->d_schedule, items.size() * sizeof(int4)), "batch schedule");
+  SU3_CUDA(cudaMemcpy(b->d_schedule, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice), "batch schedule");
+  SU3_CUDA(cudaMemcpy(b->d_reps, reps.data(), reps.size() * sizeof(ReplicaDesc), cudaMemcpyHostToDevice),
+           "batch descriptors");
+  b->n_items = (int)items.size();
+  return SU3_OK;
+}
+
+int grid_blocks(su3_lattice* h) {
+  su3_batch* b = h->batch;
+  const int fit = max_blocks_per_sm(h->precision, b->threads);
+  int bps = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, fit) : fit;
+  if (bps < 1) bps = 1;
+  return bps * b->num_sms;
+}
+
+int enqueue_batch_sweep(su3_lattice* h, int blocks) {
+  su3_batch* b = h->batch;
+  SU3_CUDA(cudaMemsetAsync(b->d_sync, 0, (1 + 8 * (size_t)b->n) * sizeof(unsigned), h->stream), "batch counters");
+  BatchArgs a{};
+  a.reps = b->d_reps;
+  a.schedule = b->d_schedule;
+  a.n_items = b->n_items;
+  a.queue = b->d_sync;
+  a.done = b->d_sync + 1;
+  a.status = b->d_status;
+  a.sweep = h->d_sweep;
+  a.links = h->links;
+  a.wait_ns = b->wait_ns;
+  a.withhold_item = b->withhold_item;
+  SU3_CUDA(launch_batch(a, h->precision, blocks, b->threads, h->stream), "batch sweep launch");
+  SU3_CUDA(su3k_launch_increment(h->d_sweep, 1, h->stream), "sweep counter launch");
+  return SU3_OK;
+}
+
+int ensure_batch_graph(su3_lattice* h) {
+  su3_batch* b = h->batch;
+  if (b->graph) return SU3_OK;
+  cudaGraph_t graph = nullptr;
+  const int blocks = grid_blocks(h);  // occupancy query before capture starts
+  SU3_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "batch graph capture");
+  const int rc = enqueue_batch_sweep(h, blocks);
+  const cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  if (rc != SU3_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return su3_cuda_fail(e, "batch graph capture end");
+  const cudaError_t ei = cudaGraphInstantiate(&b->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    b->graph = nullptr;
+    return su3_cuda_fail(ei, "batch graph instantiate");
+  }
+  return SU3_OK;
+}
+
+int set_config(su3_lattice* h, int threads, int blocks_per_sm, int window) {
+  su3_batch* b = h->batch;
+  if (threads == 0) threads = 128;
+  if (threads < 32 || threads > kBatchMaxThreads || (threads & 31))
+    return su3_fail(SU3_EINVAL, "su3_batch_config: threads %d is not a multiple of 32 in [32, %d]", threads,
+                    kBatchMaxThreads);
+  if (blocks_per_sm < 0 || window < 0) return fail(SU3_EINVAL, "su3_batch_config: negative argument");
+  SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_batch_config");
+  const bool resched = threads != b->threads || window != b->window || !b->d_schedule;
+  b->threads = threads;
+  b->blocks_per_sm = blocks_per_sm;
+  b->window = window;
+  drop_graph(b);
+  return resched ? build_schedule(h) : SU3_OK;
+}
+
+int check_status(su3_lattice* h, const char* what) {
+  su3_batch* b = h->batch;
+  const int rc = su3_sync(h, what);
+  if (rc != SU3_OK) return rc;
+  SU3_CUDA(cudaMemcpy(b->h_status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost), what);
+  if (*b->h_status != 0) {
+    SU3_CUDA(cudaMemset(b->d_status, 0, sizeof(int)), what);
+    return su3_fail(SU3_ETIMEOUT,
+                    "%s: a batched sweep gave up waiting for a phase to complete (bounded wait of %.3f s); the "
+                    "configuration of that sweep is incomplete",
+                    what, (double)b->wait_ns * 1e-9);
+  }
+  return SU3_OK;
+}
+
+std::string tune_key_of(const su3_lattice* h) {
+  std::string k = h->precision == SU3_FP64 ? "f64" : "f32m";
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp p{};
+  cudaGetDeviceProperties(&p, dev);
+  k += "|sm" + std::to_string(p.major) + std::to_string(p.minor) + "x" + std::to_string(p.multiProcessorCount);
+  for (const Geometry& g : h->batch->geoms)
+    k += "|" + std::to_string(g.L0) + "," + std::to_string(g.L1) + "," + std::to_string(g.L2) + "," + std::to_string(g.L3);
+  return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+int su3_batch_create(int n, const int (*dims)[4], const double* betas, const uint64_t* seeds, int start, int precision,
+                     void* cuda_stream, su3_handle* out) {
+  if (!out) return fail(SU3_EINVAL, "su3_batch_create: out is NULL");
+  *out = nullptr;
+  if (n < 1 || !dims || !betas || !seeds) return fail(SU3_EINVAL, "su3_batch_create: need n >= 1 and non-NULL arrays");
+  if (start != SU3_COLD && start != SU3_HOT) return fail(SU3_EINVAL, "su3_batch_create: bad start");
+  if (precision != SU3_FP64 && precision != SU3_FP32_MIXED) return fail(SU3_EINVAL, "su3_batch_create: bad precision");
+  su3_batch* b = new (std::nothrow) su3_batch;
+  su3_lattice* h = b ? new (std::nothrow) su3_lattice : nullptr;
+  if (!b || !h) {
+    delete b;
+    return fail(SU3_ENOMEM, "su3_batch_create: host allocation failed");
+  }
+  h->batch = b;
+  h->precision = precision;
+  b->n = n;
+  b->elem_bytes = precision == SU3_FP64 ? sizeof(double2) : sizeof(float4);
+  const int ncomp = precision == SU3_FP64 ? kEntriesF64 : kGroupsF32;
+  long long total = 0, vmax = 0;
+  for (int r = 0; r < n; ++r) {
+    for (int mu = 0; mu < 4; ++mu)
+      if (dims[r][mu] < 2 || (dims[r][mu] & 1)) {
+        su3_release_handle(h);
+        return su3_fail(SU3_EINVAL, "su3_batch_create: replica %d extent L%d = %d must be even and >= 2", r, mu,
+                        dims[r][mu]);
+      }
+    const long long V = (long long)dims[r][0] * dims[r][1] * dims[r][2] * dims[r][3];
+    if (4 * V > 0x7fffffffLL) {
+      su3_release_handle(h);
+      return su3_fail(SU3_EINVAL, "su3_batch_create: replica %d: 4*V exceeds 2^31-1", r);
+    }
+    if (!(betas[r] > 0.0) || !std::isfinite(betas[r])) {
+      su3_release_handle(h);
+      return su3_fail(SU3_EINVAL, "su3_batch_create: replica %d: beta must be finite and > 0", r);
+    }
+    Geometry g{};
+    g.L0 = dims[r][0];
+    g.L1 = dims[r][1];
+    g.L2 = dims[r][2];
+    g.L3 = dims[r][3];
+    g.hL0 = g.L0 / 2;
+    g.Vh = (int)(V / 2);
+    g.s1 = g.L0;
+    g.s2 = g.L0 * g.L1;
+    g.s3 = g.L0 * g.L1 * g.L2;
+    b->geoms.push_back(g);
+    b->betas.push_back(betas[r]);
+    b->seeds.push_back(seeds[r]);
+    b->offsets.push_back(total);
+    total += 8LL * ncomp * g.Vh;
+    vmax = std::max(vmax, V);
+  }
+  h->V = vmax;
+  h->beta = betas[0];
+  h->seed = seeds[0];
+  h->link_bytes = (size_t)total * b->elem_bytes;
+  cudaError_t e;
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      su3_release_handle(h);
+      return su3_cuda_fail(e, "su3_batch_create: stream");
+    }
+    h->own_stream = true;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  Geometry gmax{};
+  gmax.Vh = (int)(vmax / 2);
+  const long long chunk = vmax < kChunkSites ? vmax : kChunkSites;
+  if ((e = cudaMalloc(&h->links, h->link_bytes)) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_sweep, sizeof(uint64_t))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_stats, 2 * sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_partials, (size_t)su3k_plaquette_blocks(gmax) * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_stage, (size_t)chunk * 72 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_reps, (size_t)n * sizeof(ReplicaDesc))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_sync, (1 + 8 * (size_t)n) * sizeof(unsigned))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_status, sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_plaq_n, (size_t)n * sizeof(double))) != cudaSuccess ||
+      (e = cudaMallocHost(&b->h_status, sizeof(int))) != cudaSuccess ||
+      (e = cudaMallocHost(&b->h_plaq_n, (size_t)n * sizeof(double))) != cudaSuccess) {
+    const int rc = su3_cuda_fail(e, "su3_batch_create: allocation");
+    cudaGetLastError();
+    su3_release_handle(h);
+    return rc;
+  }
+  int rc = SU3_OK;
+  if ((e = cudaMemsetAsync(h->d_sweep, 0, sizeof(uint64_t), h->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(b->d_status, 0, sizeof(int), h->stream)) != cudaSuccess)
+    rc = su3_cuda_fail(e, "su3_batch_create: memset");
+  for (int r = 0; r < n && rc == SU3_OK; ++r) {
+    PhiloxKey k{(uint32_t)seeds[r], (uint32_t)(seeds[r] >> 32)};
+    InitArgs ia{b->geoms[r], philox_round_keys(k), precision, (char*)h->links + b->offsets[r] * b->elem_bytes};
+    e = su3k_launch_init(ia, start == SU3_HOT, h->stream);
+    if (e != cudaSuccess) rc = su3_cuda_fail(e, "su3_batch_create: start configuration");
+  }
+  if (rc == SU3_OK) {
+    b->tune_key = tune_key_of(h);
+    std::vector<int> cfg;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      auto it = g_tune_cache.find(b->tune_key);
+      if (it != g_tune_cache.end()) cfg = it->second;
+    }
+    if (cfg.size() == 3) {
+      b->threads = cfg[0];
+      b->blocks_per_sm = cfg[1];
+      b->window = cfg[2];
+    }
+    rc = build_schedule(h);
+  }
+  if (rc == SU3_OK) rc = su3_sync(h, "su3_batch_create");
+  if (rc != SU3_OK) {
+    su3_release_handle(h);
+    return rc;
+  }
+  *out = h;
+  return SU3_OK;
+}
+
+int su3_batch_sweep(su3_handle h, int nsweeps) {
+  su3_batch* b = batch_of(h);
+  if (!b) return fail(SU3_EINVAL, "su3_batch_sweep: not a batch handle");
+  if (nsweeps < 0) return fail(SU3_EINVAL, "su3_batch_sweep: nsweeps < 0");
+  if (nsweeps == 0) return SU3_OK;
+  int rc = ensure_batch_graph(h);
+  if (rc != SU3_OK) return rc;
+  for (int i = 0; i < nsweeps; ++i) SU3_CUDA(cudaGraphLaunch(b->graph, h->stream), "su3_batch_sweep: graph launch");
+  h->sweep_host += (uint64_t)nsweeps;
+  return SU3_OK;
+}
+
+int su3_batch_plaquettes(su3_handle h, double* out_n) {
+  su3_batch* b = batch_of(h);
+  if (!b || !out_n) return fail(SU3_EINVAL, "su3_batch_plaquettes: not a batch handle or NULL output");
+  for (int r = 0; r < b->n; ++r) {
+    PlaqArgs a{b->geoms[r], (const char*)h->links + b->offsets[r] * b->elem_bytes, h->d_partials};
+    SU3_CUDA(su3k_launch_plaquette(a, h->precision, b->d_plaq_n + r, h->stream), "su3_batch_plaquettes");
+  }
+  SU3_CUDA(cudaMemcpyAsync(b->h_plaq_n, b->d_plaq_n, (size_t)b->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+           "su3_batch_plaquettes");
+  const int rc = check_status(h, "su3_batch_plaquettes");
+  if (rc != SU3_OK) return rc;
+  memcpy(out_n, b->h_plaq_n, (size_t)b->n * sizeof(double));
+  return SU3_OK;
+}
+
+static int batch_links(su3_handle h, int replica, double* host, size_t n_doubles, bool get) {
+  su3_batch* b = batch_of(h);
+  const char* what = get ? "su3_batch_links_get" : "su3_batch_links_set";
+  if (!b || !host) return su3_fail(SU3_EINVAL, "%s: not a batch handle or NULL buffer", what);
+  if (replica < 0 || replica >= b->n) return su3_fail(SU3_EINVAL, "%s: replica %d out of range", what, replica);
+  const Geometry& g = b->geoms[replica];
+  const long long V = 2LL * g.Vh;
+  if (n_doubles != (size_t)V * 72) return su3_fail(SU3_ESIZE, "%s: n = %zu, expected %lld", what, n_doubles, V * 72);
+  void* base = (char*)h->links + b->offsets[replica] * b->elem_bytes;
+  for (long long s0 = 0; s0 < V; s0 += kChunkSites) {
+    const long long n = (V - s0) < kChunkSites ? (V - s0) : kChunkSites;
+    ConvArgs a{g, h->precision, s0, n, h->d_stage, base};
+    if (get) {
+      SU3_CUDA(su3k_launch_conv(a, false, h->stream), what);
+      SU3_CUDA(cudaMemcpyAsync(host + s0 * 72, h->d_stage, (size_t)n * 72 * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream),
+               what);
+    } else {
+      SU3_CUDA(cudaMemcpyAsync(h->d_stage, host + s0 * 72, (size_t)n * 72 * sizeof(double), cudaMemcpyHostToDevice,
+                               h->stream),
+               what);
+      SU3_CUDA(su3k_launch_conv(a, true, h->stream), what);
+    }
+  }
+  return check_status(h, what);
+}
+
+int su3_batch_links_get(su3_handle h, int replica, double* host, size_t n_doubles) {
+  return batch_links(h, replica, host, n_doubles, true);
+}
+
+int su3_batch_links_set(su3_handle h, int replica, const double* host, size_t n_doubles) {
+  return batch_links(h, replica, const_cast<double*>(host), n_doubles, false);
+}
+
+int su3_batch_config(su3_handle h, int threads, int blocks_per_sm, int window) {
+  if (!batch_of(h)) return fail(SU3_EINVAL, "su3_batch_config: not a batch handle");
+  return set_config(h, threads, blocks_per_sm, window);
+}
+
+int su3_batch_get_config(su3_handle h, int* threads, int* blocks_per_sm, int* window) {
+  su3_batch* b = batch_of(h);
+  if (!b) return fail(SU3_EINVAL, "su3_batch_get_config: not a batch handle");
+  if (threads) *threads = b->threads;
+  if (blocks_per_sm) *blocks_per_sm = grid_blocks(h) / b->num_sms;
+  if (window) *window = b->window > 0 ? std::min(b->window, b->n) : b->n;
+  return SU3_OK;
+}
+
+int su3_batch_autotune(su3_handle h, int* threads, int* blocks_per_sm, int* window) {
+  su3_batch* b = batch_of(h);
+  if (!b) return fail(SU3_EINVAL, "su3_batch_autotune: not a batch handle");
+  // Tuning sweeps advance the chain: save the links and the sweep counter and
+  // restore them afterwards, so tuning leaves no trace in the results.
+  void* saved = nullptr;
+  SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_batch_autotune");
+  SU3_CUDA(cudaMalloc(&saved, h->link_bytes), "su3_batch_autotune: save buffer");
+  cudaError_t e = cudaMemcpyAsync(saved, h->links, h->link_bytes, cudaMemcpyDeviceToDevice, h->stream);
+  const uint64_t count = h->sweep_host;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  int best[3] = {b->threads, b->blocks_per_sm, b->window};
+  float best_ms = 1e30f;
+  int rc = e == cudaSuccess ? SU3_OK : su3_cuda_fail(e, "su3_batch_autotune");
+  std::vector<int> windows = {0};
+  for (int d = 2; d <= 16 && b->n / d >= 1; d *= 2) windows.push_back((b->n + d - 1) / d);
+  for (int thr : {64, 128, 256}) {
+    const int fit = max_blocks_per_sm(h->precision, thr);
+    for (int bps : {1, 2, 3, 4, 6, 8, 12, 16}) {
+      if (bps > fit || rc != SU3_OK) break;
+      for (int w : windows) {
+        if (rc != SU3_OK) break;
+        rc = set_config(h, thr, bps, w);
+        if (rc == SU3_OK) rc = ensure_batch_graph(h);
+        if (rc != SU3_OK) break;
+        if ((e = cudaGraphLaunch(b->graph, h->stream)) != cudaSuccess ||
+            (e = cudaEventRecord(e0, h->stream)) != cudaSuccess ||
+            (e = cudaGraphLaunch(b->graph, h->stream)) != cudaSuccess ||
+            (e = cudaGraphLaunch(b->graph, h->stream)) != cudaSuccess ||
+            (e = cudaEventRecord(e1, h->stream)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+          rc = su3_cuda_fail(e, "su3_batch_autotune: timing");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best[0] = thr;
+          best[1] = bps;
+          best[2] = w;
+        }
+      }
+    }
+  }
+  if (rc == SU3_OK) rc = check_status(h, "su3_batch_autotune");
+  if (rc == SU3_OK) rc = set_config(h, best[0], best[1], best[2]);
+  if (rc == SU3_OK) {
+    e = cudaMemcpyAsync(h->links, saved, h->link_bytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = su3k_launch_set_counter(h->d_sweep, count, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = su3_cuda_fail(e, "su3_batch_autotune: restore");
+    h->sweep_host = count;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(saved);
+  if (rc != SU3_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[b->tune_key] = {best[0], best[1], best[2]};
+  }
+  return su3_batch_get_config(h, threads, blocks_per_sm, window);
+}
+
+int su3_batch_debug(su3_handle h, double wait_limit_s, int withhold_item) {
+  su3_batch* b = batch_of(h);
+  if (!b) return fail(SU3_EINVAL, "su3_batch_debug: not a batch handle");
+  if (!(wait_limit_s > 0.0) || wait_limit_s > 60.0) return fail(SU3_EINVAL, "su3_batch_debug: wait limit not in (0, 60] s");
+  if (withhold_item < -1) return fail(SU3_EINVAL, "su3_batch_debug: bad item");
+  SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_batch_debug");
+  b->wait_ns = (long long)(wait_limit_s * 1e9);
+  b->withhold_item = withhold_item;
+  drop_graph(b);
+  return SU3_OK;
+}
+
+int su3_status(su3_handle h) {
+  if (!h) return fail(SU3_EINVAL, "su3_status: NULL handle");
+  if (!h->batch) return su3_sync(h, "su3_status");
+  return check_status(h, "su3_status");
+}
+
+int su3_batch_size(su3_handle h, int* n) {
+  su3_batch* b = batch_of(h);
+  if (!b || !n) return fail(SU3_EINVAL, "su3_batch_size: not a batch handle or NULL output");
+  *n = b->n;
+  return SU3_OK;
+}
+
+}  // extern "C"

@@ -83,6 +83,23 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxRoundKeys& r
   return c;
 }
 
+// Same block function with the round keys derived on the fly from the seed
+// (used where the key differs between work items, e.g. per replica).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key) {
+  uint32_t k0 = key.k0, k1 = key.k1;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo_a = kPhiloxMulA * c.x;
+    const uint32_t hi_a = __umulhi(kPhiloxMulA, c.x);
+    const uint32_t lo_b = kPhiloxMulB * c.z;
+    const uint32_t hi_b = __umulhi(kPhiloxMulB, c.z);
+    c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+    k0 += kPhiloxWeylA;
+    k1 += kPhiloxWeylB;
+  }
+  return c;
+}
+
 // Counter of draw `w1` (= mu | sub<<2 | call<<4) of site s at sweep t.
 __device__ __forceinline__ uint4 rng_counter(uint32_t site, uint32_t w1, uint64_t t, uint32_t tag) {
   return make_uint4(site, w1, (uint32_t)t, tag | ((uint32_t)(t >> 32) << 4));
@@ -284,12 +301,22 @@ __device__ __forceinline__ size_t link_base(int mu, int p, int Vh, int ncomp) {
   return ((size_t)(mu * 2 + p) * ncomp) * (size_t)Vh;
 }
 
+template <bool CG>
+__device__ __forceinline__ double2 ld_link(const double2* p) {
+  return CG ? __ldcg(p) : __ldg(p);
+}
+template <bool CG>
+__device__ __forceinline__ float4 ld_link(const float4* p) {
+  return CG ? __ldcg(p) : __ldg(p);
+}
+
+template <bool CG = false>
 __device__ __forceinline__ mat3<double> load_f64(const double2* __restrict__ U, int mu, int p, int h, int Vh) {
   mat3<double> m;
   const double2* b = U + link_base(mu, p, Vh, kEntriesF64) + h;
 #pragma unroll
   for (int c = 0; c < 9; ++c) {
-    const double2 v = __ldg(b + (size_t)c * Vh);
+    const double2 v = ld_link<CG>(b + (size_t)c * Vh);
     m.e[c / 3][c % 3] = mk(v.x, v.y);
   }
   return m;
@@ -302,10 +329,11 @@ __device__ __forceinline__ void store_f64(double2* U, int mu, int p, int h, int 
 }
 
 // Rows 0 and 1 only; the caller completes row 2 when it needs it.
+template <bool CG = false>
 __device__ __forceinline__ mat3<float> load_f32_rows01(const float4* __restrict__ U, int mu, int p, int h, int Vh) {
   mat3<float> m;
   const float4* b = U + link_base(mu, p, Vh, kGroupsF32) + h;
-  const float4 g0 = __ldg(b), g1 = __ldg(b + Vh), g2 = __ldg(b + 2 * (size_t)Vh);
+  const float4 g0 = ld_link<CG>(b), g1 = ld_link<CG>(b + Vh), g2 = ld_link<CG>(b + 2 * (size_t)Vh);
   m.e[0][0] = mk(g0.x, g0.y);
   m.e[0][1] = mk(g0.z, g0.w);
   m.e[0][2] = mk(g1.x, g1.y);
@@ -315,8 +343,9 @@ __device__ __forceinline__ mat3<float> load_f32_rows01(const float4* __restrict_
   return m;
 }
 
+template <bool CG = false>
 __device__ __forceinline__ mat3<float> load_f32(const float4* __restrict__ U, int mu, int p, int h, int Vh) {
-  mat3<float> m = load_f32_rows01(U, mu, p, h, Vh);
+  mat3<float> m = load_f32_rows01<CG>(U, mu, p, h, Vh);
   complete_row2(m);
   return m;
 }

@@ -12,6 +12,7 @@
 #include "su3_kernels.h"
 
 #include "su3_device.cuh"
+#include "su3_update.cuh"
 
 using namespace su3dev;
 
@@ -24,247 +25,43 @@ using namespace su3dev;
 
 namespace {
 
-constexpr double kTwoPi = 6.283185307179586476925286766559;
-
-template <typename T>
-__device__ __forceinline__ mat3<T> zero3() {
-  mat3<T> m;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) m.e[i][k] = mk(T(0), T(0));
-  return m;
-}
-
-// Link loader for the two storage forms.
-template <typename T>
-struct Store;
-
-template <>
-struct Store<double> {
-  __device__ __forceinline__ static mat3<double> load(const void* U, int mu, int p, int h, int Vh) {
-    return load_f64((const double2*)U, mu, p, h, Vh);
-  }
-};
-
-template <>
-struct Store<float> {
-  __device__ __forceinline__ static mat3<float> load(const void* U, int mu, int p, int h, int Vh) {
-    return load_f32((const float4*)U, mu, p, h, Vh);
-  }
-};
-
-// Six-staple sum A for U_mu(x), x = st of parity p:
-//   sum_{nu != mu} U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ + U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu).
-// Each three-link path is an SU(3) matrix, so only its rows 0 and 1 are
-// multiplied out and row 2 is completed as conj(row0 x row1).
-template <typename T, int MU>
-__device__ __forceinline__ mat3<T> staple(const Geometry& g, const void* U, const Site& st, int h, int p) {
-  const int q = p ^ 1;
-  mat3<T> A = zero3<T>();
-  const int h_pmu = nb_half(g, st, MU, +1);
-#pragma unroll
-  for (int nu = 0; nu < 4; ++nu) {
-    if (nu == MU) continue;
-    const int h_pnu = nb_half(g, st, nu, +1);
-    const int h_mnu = nb_half(g, st, nu, -1);
-    const int h_pmu_mnu = nb_half2(g, st, MU, nu);
-    {
-      const mat3<T> a = Store<T>::load(U, nu, q, h_pmu, g.Vh);  // U_nu(x+mu)
-      const mat3<T> b = Store<T>::load(U, MU, q, h_pnu, g.Vh);  // U_mu(x+nu)
-      mat3<T> t;
-      mul_nd_rows01(a, b, t);
-      const mat3<T> c = Store<T>::load(U, nu, p, h, g.Vh);  // U_nu(x)
-      mat3<T> f;
-      mul_nd_rows01(t, c, f);
-      complete_row2(f);
-      acc_full(A, f);
-    }
-    {
-      const mat3<T> d = Store<T>::load(U, nu, p, h_pmu_mnu, g.Vh);  // U_nu(x+mu-nu)
-      const mat3<T> e = Store<T>::load(U, MU, q, h_mnu, g.Vh);      // U_mu(x-nu)
-      mat3<T> hm;
-      mul_nn_rows01(e, d, hm);
-      complete_row2(hm);
-      const mat3<T> f = Store<T>::load(U, nu, q, h_mnu, g.Vh);  // U_nu(x-nu)
-      mat3<T> b;
-      mul_dn_rows01(hm, f, b);
-      complete_row2(b);
-      acc_full(A, b);
+// ---------------------------------------------------------------------------
+// Single-lattice half-sweeps: one thread per link of (mu, parity).
+// ---------------------------------------------------------------------------
+template <bool STATS>
+__device__ __forceinline__ void count_stats(int accepted, bool active, unsigned long long* stats) {
+  if (STATS) {
+    const unsigned m = __ballot_sync(0xffffffffu, active);
+    const int acc = __reduce_add_sync(0xffffffffu, accepted);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&stats[0], (unsigned long long)acc);
+      atomicAdd(&stats[1], 3ull * (unsigned long long)__popc(m));
     }
   }
-  return A;
 }
 
-// 2x2 block of W = U A in rows/columns (i, j), projected on the SU(2) direction:
-// r = (Re(W_ii+W_jj), Im(W_ij+W_ji), Re(W_ij-W_ji), Im(W_ii-W_jj)) / 2.
-template <typename T>
-__device__ __forceinline__ void su2_projection(const mat3<T>& u, const mat3<T>& A, int i, int j, T r[4]) {
-  cx<T> wii = mk(T(0), T(0)), wij = wii, wji = wii, wjj = wii;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    wii = mac(wii, u.e[i][c], A.e[c][i]);
-    wij = mac(wij, u.e[i][c], A.e[c][j]);
-    wji = mac(wji, u.e[j][c], A.e[c][i]);
-    wjj = mac(wjj, u.e[j][c], A.e[c][j]);
-  }
-  r[0] = T(0.5) * (wii.re + wjj.re);
-  r[1] = T(0.5) * (wij.im + wji.im);
-  r[2] = T(0.5) * (wij.re - wji.re);
-  r[3] = T(0.5) * (wii.im - wjj.im);
-}
-
-// rows (i, j) of u <- R rows (i, j), R = Y V^+ with Y = m(a), V = m(v),
-// m(q) = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]].
-template <typename T>
-__device__ __forceinline__ void apply_su2(mat3<T>& u, int i, int j, const T a[4], const T v[4]) {
-  const cx<T> y00 = mk(a[0], a[3]), y01 = mk(a[2], a[1]), y10 = mk(-a[2], a[1]), y11 = mk(a[0], -a[3]);
-  const cx<T> v00 = mk(v[0], v[3]), v01 = mk(v[2], v[1]), v10 = mk(-v[2], v[1]), v11 = mk(v[0], -v[3]);
-  // (V^+)_{pq} = conj(V_{qp})
-  cx<T> R00 = mac_cb(mac_cb(mk(T(0), T(0)), y00, v00), y01, v01);
-  cx<T> R01 = mac_cb(mac_cb(mk(T(0), T(0)), y00, v10), y01, v11);
-  cx<T> R10 = mac_cb(mac_cb(mk(T(0), T(0)), y10, v00), y11, v01);
-  cx<T> R11 = mac_cb(mac_cb(mk(T(0), T(0)), y10, v10), y11, v11);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const cx<T> ui = u.e[i][c], uj = u.e[j][c];
-    u.e[i][c] = mac(mul(R00, ui), R01, uj);
-    u.e[j][c] = mac(mul(R10, ui), R11, uj);
-  }
-}
-
-__device__ __forceinline__ int subrow_i(int sub) { return sub == 2 ? 1 : 0; }
-__device__ __forceinline__ int subrow_j(int sub) { return sub == 0 ? 1 : 2; }
-
-// ---------------------------------------------------------------------------
-// FP64 half-sweep.
-// ---------------------------------------------------------------------------
 template <int MU, bool STATS>
 __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64(HalfSweepArgs args) {
-  const Geometry g = args.geom;
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = h < args.geom.Vh;
   int accepted = 0;
-  if (h < g.Vh) {
-    const int p = args.parity;
-    const Site st = site_of(g, h, p);
-    const uint32_t s = (uint32_t)canon(g, st);
-    const uint64_t t = *args.sweep;
-    double2* U = (double2*)args.links;
-    const mat3<double> A = staple<double, MU>(g, U, st, h, p);
-    mat3<double> u = load_f64(U, MU, p, h, g.Vh);
-#pragma unroll
-    for (int sub = 0; sub < 3; ++sub) {
-      const int i = subrow_i(sub), j = subrow_j(sub);
-      double r[4];
-      su2_projection(u, A, i, j, r);
-      const double kk = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
-      double uu[6];
-#pragma unroll
-      for (int call = 0; call < 3; ++call) {
-        const uint4 w = philox4x32_10(rng_counter(s, (uint32_t)(MU | (sub << 2) | (call << 4)), t, kTagUpdate), args.key);
-        uu[2 * call] = u01_f64(w.x, w.y);
-        uu[2 * call + 1] = u01_f64(w.z, w.w);
-      }
-      if (!(kk > 0.0)) continue;  // k = 0: degenerate staple (measure zero), leave the subgroup
-      const double ik = rsqrt(kk);
-      const double inv_alpha = args.inv_beta15_f64 * ik;  // 1/alpha = 3 / (2 beta k)
-      const double c = cos(kTwoPi * uu[1]);
-      const double delta = -(log(uu[0]) + c * c * log(uu[2])) * inv_alpha;
-      if (uu[3] * uu[3] > 1.0 - 0.5 * delta) continue;
-      const double a0 = 1.0 - delta;
-      double rho = 1.0 - a0 * a0;
-      rho = rho > 0.0 ? sqrt(rho) : 0.0;
-      const double ct = 1.0 - 2.0 * uu[4];
-      double sn = 1.0 - ct * ct;
-      sn = sn > 0.0 ? sqrt(sn) : 0.0;
-      double sphi, cphi;
-      sincos(kTwoPi * uu[5], &sphi, &cphi);
-      const double a[4] = {a0, rho * sn * cphi, rho * sn * sphi, rho * ct};
-      const double v[4] = {r[0] * ik, r[1] * ik, r[2] * ik, r[3] * ik};
-      apply_su2(u, i, j, a, v);
-      ++accepted;
-    }
-    cx<double> r0[3] = {u.e[0][0], u.e[0][1], u.e[0][2]};
-    cx<double> r1[3] = {u.e[1][0], u.e[1][1], u.e[1][2]};
-    gram_schmidt_rows01(r0, r1);
-    mat3<double> out;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      out.e[0][k] = r0[k];
-      out.e[1][k] = r1[k];
-    }
-    complete_row2(out);
-    store_f64(U, MU, p, h, g.Vh, out);
+  if (active) {
+    const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15};
+    accepted = update_link_f64<MU, false>(args.geom, (double2*)args.links, h, args.parity, *args.sweep, args.key, uc);
   }
-  if (STATS) {
-    const unsigned m = __ballot_sync(0xffffffffu, h < g.Vh);
-    const int acc = __reduce_add_sync(0xffffffffu, accepted);
-    if ((threadIdx.x & 31) == 0) {
-      atomicAdd(&args.stats[0], (unsigned long long)acc);
-      atomicAdd(&args.stats[1], 3ull * (unsigned long long)__popc(m));
-    }
-  }
+  count_stats<STATS>(accepted, active, args.stats);
 }
 
-// ---------------------------------------------------------------------------
-// FP32-mixed half-sweep: FP32 storage (rows 0,1), FP32 staple and heatbath,
-// FP64 Gram-Schmidt.
-// ---------------------------------------------------------------------------
 template <int MU, bool STATS>
 __global__ void __launch_bounds__(kMaxSweepThreads, SU3_F32_MINBLOCKS) k_half_sweep_f32(HalfSweepArgs args) {
-  const Geometry g = args.geom;
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = h < args.geom.Vh;
   int accepted = 0;
-  if (h < g.Vh) {
-    const int p = args.parity;
-    const Site st = site_of(g, h, p);
-    const uint32_t s = (uint32_t)canon(g, st);
-    const uint64_t t = *args.sweep;
-    float4* U = (float4*)args.links;
-    const mat3<float> A = staple<float, MU>(g, U, st, h, p);
-    mat3<float> u = load_f32(U, MU, p, h, g.Vh);
-    const float inv_beta15 = args.inv_beta15;
-#pragma unroll
-    for (int sub = 0; sub < 3; ++sub) {
-      const int i = subrow_i(sub), j = subrow_j(sub);
-      float r[4];
-      su2_projection(u, A, i, j, r);
-      const float kk = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
-      const uint4 w0 = philox4x32_10(rng_counter(s, (uint32_t)(MU | (sub << 2)), t, kTagUpdate), args.key);
-      const uint4 w1 = philox4x32_10(rng_counter(s, (uint32_t)(MU | (sub << 2) | (1 << 4)), t, kTagUpdate), args.key);
-      if (!(kk > 1e-30f)) continue;  // degenerate staple (measure zero): leave the subgroup
-      const float ik = rsqrtf(kk);
-      // 1/alpha = 3 / (2 beta k)
-      const float ia = inv_beta15 * ik;
-      const float u0 = u01_f32(w0.x), u1 = u01_f32(w0.y), u2 = u01_f32(w0.z), u3 = u01_f32(w0.w);
-      const float cc = __cosf(fmaf(6.2831853f, u1, -3.14159265f));  // -cos(2 pi u1); only its square is used
-      const float delta = -(__logf(u0) + cc * cc * __logf(u2)) * ia;
-      if (u3 * u3 > 1.0f - 0.5f * delta) continue;
-      const float u4 = u01_f32(w1.x), u5 = u01_f32(w1.y);
-      const float a0 = 1.0f - delta;
-      const float rho = sqrtf(fmaxf(0.0f, delta * (2.0f - delta)));  // sqrt(1 - a0^2)
-      const float ct = 1.0f - 2.0f * u4;
-      const float sn = 2.0f * sqrtf(u4 * (1.0f - u4));  // sqrt(1 - ct^2)
-      float sphi, cphi;
-      __sincosf(fmaf(6.2831853f, u5, -3.14159265f), &sphi, &cphi);  // angle 2 pi u5 - pi
-      const float rs = -rho * sn;                                     // undo the shift by pi
-      const float a[4] = {a0, rs * cphi, rs * sphi, rho * ct};
-      const float v[4] = {r[0] * ik, r[1] * ik, r[2] * ik, r[3] * ik};
-      apply_su2(u, i, j, a, v);
-      ++accepted;
-    }
-    float o[12];
-    reunitarise_f32(u.e[0], u.e[1], o);
-    store_f32_rows01(U, MU, p, h, g.Vh, o);
+  if (active) {
+    const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15};
+    accepted = update_link_f32<MU, false>(args.geom, (float4*)args.links, h, args.parity, *args.sweep, args.key, uc);
   }
-  if (STATS) {
-    const unsigned m = __ballot_sync(0xffffffffu, h < g.Vh);
-    const int acc = __reduce_add_sync(0xffffffffu, accepted);
-    if ((threadIdx.x & 31) == 0) {
-      atomicAdd(&args.stats[0], (unsigned long long)acc);
-      atomicAdd(&args.stats[1], 3ull * (unsigned long long)__popc(m));
-    }
-  }
+  count_stats<STATS>(accepted, active, args.stats);
 }
 
 __global__ void k_increment(uint64_t* counter, uint64_t n) { *counter += n; }
@@ -518,6 +315,12 @@ __global__ void k_store_to_canon(ConvArgs args) {
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
+template <int MU, bool STATS>
+static cudaError_t launch_f32(const HalfSweepArgs& a, int blocks, int threads, cudaStream_t s) {
+  k_half_sweep_f32<MU, STATS><<<blocks, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int MU>
 static cudaError_t launch_half_sweep_mu(const HalfSweepArgs& a, int precision, bool stats, int threads, cudaStream_t s) {
   const int blocks = (a.geom.Vh + threads - 1) / threads;
@@ -526,13 +329,9 @@ static cudaError_t launch_half_sweep_mu(const HalfSweepArgs& a, int precision, b
       k_half_sweep_f64<MU, true><<<blocks, threads, 0, s>>>(a);
     else
       k_half_sweep_f64<MU, false><<<blocks, threads, 0, s>>>(a);
-  } else {
-    if (stats)
-      k_half_sweep_f32<MU, true><<<blocks, threads, 0, s>>>(a);
-    else
-      k_half_sweep_f32<MU, false><<<blocks, threads, 0, s>>>(a);
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
+  return stats ? launch_f32<MU, true>(a, blocks, threads, s) : launch_f32<MU, false>(a, blocks, threads, s);
 }
 
 cudaError_t su3k_launch_half_sweep(const HalfSweepArgs& a, int mu, int precision, bool stats, int threads, cudaStream_t s) {

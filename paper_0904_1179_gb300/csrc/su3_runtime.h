@@ -1,0 +1,57 @@
+// su3_runtime.h -- host-side state shared by the libsu3 runtime files
+// (su3_api.cu: single lattices; su3_batch.cu: batches of replicas).  Internal.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "su3.h"
+#include "su3_kernels.h"
+
+// Threads per block of the half-sweep kernels unless set otherwise.
+constexpr int kSu3DefaultThreads = 128;
+// Sites per chunk of the canonical-layout staging buffer (37.7 MB of FP64 links).
+constexpr long long kChunkSites = 1LL << 16;
+
+struct su3_batch;
+
+struct su3_lattice {
+  int L[4] = {0, 0, 0, 0};
+  long long V = 0;
+  double beta = 0.0;
+  uint64_t seed = 0;
+  int precision = SU3_FP64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* links = nullptr;
+  size_t link_bytes = 0;
+  uint64_t* d_sweep = nullptr;
+  uint64_t sweep_host = 0;
+  unsigned long long* d_stats = nullptr;
+  bool stats_on = false;
+  double* d_partials = nullptr;
+  double* d_plaq = nullptr;
+  double* h_plaq = nullptr;               // pinned
+  unsigned long long* h_stats = nullptr;  // pinned, 2 words
+  double* d_stage = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // indexed by stats_on
+  int threads = kSu3DefaultThreads;
+  su3dev::Geometry geom{};
+  su3dev::PhiloxKey key{};
+  su3_batch* batch = nullptr;  // non-null for a batch of replicas
+};
+
+// Record a failure for su3_last_error(); returns code.
+int su3_fail(int code, const char* fmt, ...);
+int su3_cuda_fail(cudaError_t e, const char* what);
+int su3_sync(su3_lattice* h, const char* what);
+// Free a handle and everything it owns (batch part included).
+void su3_release_handle(su3_lattice* h);
+// Free the batch part of a handle (defined in su3_batch.cu).
+void su3_batch_release(su3_batch* b);
+
+#define SU3_CUDA(call, what)                               \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return su3_cuda_fail(e_, what); \
+  } while (0)

@@ -1,0 +1,248 @@
+// su3_update.cuh -- one checkerboard link update on sm_103a CUDA cores, shared
+// by the single-lattice half-sweep kernels (one launch per (mu, parity)) and
+// the persistent batched sweep.
+//
+// A link U_mu(x) gathers its six-staple sum from the 18 neighbouring links,
+// runs the one-hit Kennedy-Pendleton heatbath in the SU(2) subgroups (0,1),
+// (0,2), (1,2) (Cabibbo-Marinari), is reunitarised and stored.  Links of one
+// (mu, parity) never enter each other's staples (checkerboard updating,
+// Abstract and Sec. 1 of Berg & Wu, arXiv:0904.1179); every update draws its
+// random numbers from Philox counters keyed by its site, so the result does
+// not depend on which thread, block or launch performs it.  The work is a 4D
+// stencil of 3x3 complex products, not a dense contraction: CUDA cores, no
+// tensor cores.
+#pragma once
+
+#include "su3_device.cuh"
+
+namespace su3dev {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+template <typename T>
+__device__ __forceinline__ mat3<T> zero3() {
+  mat3<T> m;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) m.e[i][k] = mk(T(0), T(0));
+  return m;
+}
+
+// Link loader for the two storage forms.  CG = true reads through L2 only
+// (ld.global.cg): required where other thread blocks of the same launch have
+// written the links (the persistent batched sweep); otherwise the read-only
+// path (ld.global.nc) is used.
+template <typename T, bool CG>
+struct Store;
+
+template <bool CG>
+struct Store<double, CG> {
+  __device__ __forceinline__ static mat3<double> load(const void* U, int mu, int p, int h, int Vh) {
+    return load_f64<CG>((const double2*)U, mu, p, h, Vh);
+  }
+};
+
+template <bool CG>
+struct Store<float, CG> {
+  __device__ __forceinline__ static mat3<float> load(const void* U, int mu, int p, int h, int Vh) {
+    return load_f32<CG>((const float4*)U, mu, p, h, Vh);
+  }
+};
+
+// Six-staple sum A for U_mu(x), x = st of parity p:
+//   sum_{nu != mu} U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ + U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu).
+// Each three-link path is an SU(3) matrix, so only its rows 0 and 1 are
+// multiplied out and row 2 is completed as conj(row0 x row1).
+template <typename T, int MU, bool CG>
+__device__ __forceinline__ mat3<T> staple(const Geometry& g, const void* U, const Site& st, int h, int p) {
+  const int q = p ^ 1;
+  mat3<T> A = zero3<T>();
+  const int h_pmu = nb_half(g, st, MU, +1);
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == MU) continue;
+    const int h_pnu = nb_half(g, st, nu, +1);
+    const int h_mnu = nb_half(g, st, nu, -1);
+    const int h_pmu_mnu = nb_half2(g, st, MU, nu);
+    {
+      const mat3<T> a = Store<T, CG>::load(U, nu, q, h_pmu, g.Vh);  // U_nu(x+mu)
+      const mat3<T> b = Store<T, CG>::load(U, MU, q, h_pnu, g.Vh);  // U_mu(x+nu)
+      mat3<T> t;
+      mul_nd_rows01(a, b, t);
+      const mat3<T> c = Store<T, CG>::load(U, nu, p, h, g.Vh);  // U_nu(x)
+      mat3<T> f;
+      mul_nd_rows01(t, c, f);
+      complete_row2(f);
+      acc_full(A, f);
+    }
+    {
+      const mat3<T> d = Store<T, CG>::load(U, nu, p, h_pmu_mnu, g.Vh);  // U_nu(x+mu-nu)
+      const mat3<T> e = Store<T, CG>::load(U, MU, q, h_mnu, g.Vh);      // U_mu(x-nu)
+      mat3<T> hm;
+      mul_nn_rows01(e, d, hm);
+      complete_row2(hm);
+      const mat3<T> f = Store<T, CG>::load(U, nu, q, h_mnu, g.Vh);  // U_nu(x-nu)
+      mat3<T> b;
+      mul_dn_rows01(hm, f, b);
+      complete_row2(b);
+      acc_full(A, b);
+    }
+  }
+  return A;
+}
+
+
+// 2x2 block of W = U A in rows/columns (i, j), projected on the SU(2) direction:
+// r = (Re(W_ii+W_jj), Im(W_ij+W_ji), Re(W_ij-W_ji), Im(W_ii-W_jj)) / 2.
+template <typename T>
+__device__ __forceinline__ void su2_projection(const mat3<T>& u, const mat3<T>& A, int i, int j, T r[4]) {
+  cx<T> wii = mk(T(0), T(0)), wij = wii, wji = wii, wjj = wii;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    wii = mac(wii, u.e[i][c], A.e[c][i]);
+    wij = mac(wij, u.e[i][c], A.e[c][j]);
+    wji = mac(wji, u.e[j][c], A.e[c][i]);
+    wjj = mac(wjj, u.e[j][c], A.e[c][j]);
+  }
+  r[0] = T(0.5) * (wii.re + wjj.re);
+  r[1] = T(0.5) * (wij.im + wji.im);
+  r[2] = T(0.5) * (wij.re - wji.re);
+  r[3] = T(0.5) * (wii.im - wjj.im);
+}
+
+// rows (i, j) of u <- R rows (i, j), R = Y V^+ with Y = m(a), V = m(v),
+// m(q) = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]].
+template <typename T>
+__device__ __forceinline__ void apply_su2(mat3<T>& u, int i, int j, const T a[4], const T v[4]) {
+  const cx<T> y00 = mk(a[0], a[3]), y01 = mk(a[2], a[1]), y10 = mk(-a[2], a[1]), y11 = mk(a[0], -a[3]);
+  const cx<T> v00 = mk(v[0], v[3]), v01 = mk(v[2], v[1]), v10 = mk(-v[2], v[1]), v11 = mk(v[0], -v[3]);
+  // (V^+)_{pq} = conj(V_{qp})
+  cx<T> R00 = mac_cb(mac_cb(mk(T(0), T(0)), y00, v00), y01, v01);
+  cx<T> R01 = mac_cb(mac_cb(mk(T(0), T(0)), y00, v10), y01, v11);
+  cx<T> R10 = mac_cb(mac_cb(mk(T(0), T(0)), y10, v00), y11, v01);
+  cx<T> R11 = mac_cb(mac_cb(mk(T(0), T(0)), y10, v10), y11, v11);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cx<T> ui = u.e[i][c], uj = u.e[j][c];
+    u.e[i][c] = mac(mul(R00, ui), R01, uj);
+    u.e[j][c] = mac(mul(R10, ui), R11, uj);
+  }
+}
+
+__device__ __forceinline__ int subrow_i(int sub) { return sub == 2 ? 1 : 0; }
+__device__ __forceinline__ int subrow_j(int sub) { return sub == 0 ? 1 : 2; }
+
+
+// Parameters of one link update that do not vary across the links of a lattice.
+struct UpdateConsts {
+  double inv_beta15_f64;  // 1.5 / beta: 1/alpha = 3/(2 beta k) = inv_beta15 / k
+  float inv_beta15;
+};
+
+// ---------------------------------------------------------------------------
+// One FP64 link update: staple, three one-hit SU(2) heatbath steps, FP64
+// Gram-Schmidt, store.  Returns the number of accepted SU(2) proposals.
+// ---------------------------------------------------------------------------
+template <int MU, bool CG, typename KEY>
+__device__ __forceinline__ int update_link_f64(const Geometry& g, double2* U, int h, int p, uint64_t t, const KEY& key,
+                                               const UpdateConsts& uc) {
+  int accepted = 0;
+  const Site st = site_of(g, h, p);
+  const uint32_t s = (uint32_t)canon(g, st);
+  const mat3<double> A = staple<double, MU, CG>(g, U, st, h, p);
+  mat3<double> u = load_f64<CG>(U, MU, p, h, g.Vh);
+#pragma unroll
+  for (int sub = 0; sub < 3; ++sub) {
+    const int i = subrow_i(sub), j = subrow_j(sub);
+    double r[4];
+    su2_projection(u, A, i, j, r);
+    const double kk = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
+    double uu[6];
+#pragma unroll
+    for (int call = 0; call < 3; ++call) {
+      const uint4 w = philox4x32_10(rng_counter(s, (uint32_t)(MU | (sub << 2) | (call << 4)), t, kTagUpdate), key);
+      uu[2 * call] = u01_f64(w.x, w.y);
+      uu[2 * call + 1] = u01_f64(w.z, w.w);
+    }
+    if (!(kk > 0.0)) continue;  // k = 0: degenerate staple (measure zero), leave the subgroup
+    const double ik = rsqrt(kk);
+    const double inv_alpha = uc.inv_beta15_f64 * ik;  // 1/alpha = 3 / (2 beta k)
+    const double c = cos(kTwoPi * uu[1]);
+    const double delta = -(log(uu[0]) + c * c * log(uu[2])) * inv_alpha;
+    if (uu[3] * uu[3] > 1.0 - 0.5 * delta) continue;
+    const double a0 = 1.0 - delta;
+    double rho = 1.0 - a0 * a0;
+    rho = rho > 0.0 ? sqrt(rho) : 0.0;
+    const double ct = 1.0 - 2.0 * uu[4];
+    double sn = 1.0 - ct * ct;
+    sn = sn > 0.0 ? sqrt(sn) : 0.0;
+    double sphi, cphi;
+    sincos(kTwoPi * uu[5], &sphi, &cphi);
+    const double a[4] = {a0, rho * sn * cphi, rho * sn * sphi, rho * ct};
+    const double v[4] = {r[0] * ik, r[1] * ik, r[2] * ik, r[3] * ik};
+    apply_su2(u, i, j, a, v);
+    ++accepted;
+  }
+  cx<double> r0[3] = {u.e[0][0], u.e[0][1], u.e[0][2]};
+  cx<double> r1[3] = {u.e[1][0], u.e[1][1], u.e[1][2]};
+  gram_schmidt_rows01(r0, r1);
+  mat3<double> out;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    out.e[0][k] = r0[k];
+    out.e[1][k] = r1[k];
+  }
+  complete_row2(out);
+  store_f64(U, MU, p, h, g.Vh, out);
+  return accepted;
+}
+
+// ---------------------------------------------------------------------------
+// One FP32-mixed link update: FP32 storage (rows 0,1), FP32 staple and
+// heatbath, Gram-Schmidt coefficients in FP64.
+// ---------------------------------------------------------------------------
+template <int MU, bool CG, typename KEY>
+__device__ __forceinline__ int update_link_f32(const Geometry& g, float4* U, int h, int p, uint64_t t, const KEY& key,
+                                               const UpdateConsts& uc) {
+  int accepted = 0;
+  const Site st = site_of(g, h, p);
+  const uint32_t s = (uint32_t)canon(g, st);
+  const mat3<float> A = staple<float, MU, CG>(g, U, st, h, p);
+  mat3<float> u = load_f32<CG>(U, MU, p, h, g.Vh);
+  const float inv_beta15 = uc.inv_beta15;
+#pragma unroll
+  for (int sub = 0; sub < 3; ++sub) {
+    const int i = subrow_i(sub), j = subrow_j(sub);
+    float r[4];
+    su2_projection(u, A, i, j, r);
+    const float kk = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
+    const uint4 w0 = philox4x32_10(rng_counter(s, (uint32_t)(MU | (sub << 2)), t, kTagUpdate), key);
+    const uint4 w1 = philox4x32_10(rng_counter(s, (uint32_t)(MU | (sub << 2) | (1 << 4)), t, kTagUpdate), key);
+    if (!(kk > 1e-30f)) continue;  // degenerate staple (measure zero): leave the subgroup
+    const float ik = rsqrtf(kk);
+    const float ia = inv_beta15 * ik;  // 1/alpha = 3 / (2 beta k)
+    const float u0 = u01_f32(w0.x), u1 = u01_f32(w0.y), u2 = u01_f32(w0.z), u3 = u01_f32(w0.w);
+    const float cc = __cosf(fmaf(6.2831853f, u1, -3.14159265f));  // -cos(2 pi u1); only its square is used
+    const float delta = -(__logf(u0) + cc * cc * __logf(u2)) * ia;
+    if (u3 * u3 > 1.0f - 0.5f * delta) continue;
+    const float u4 = u01_f32(w1.x), u5 = u01_f32(w1.y);
+    const float a0 = 1.0f - delta;
+    const float rho = sqrtf(fmaxf(0.0f, delta * (2.0f - delta)));  // sqrt(1 - a0^2)
+    const float ct = 1.0f - 2.0f * u4;
+    const float sn = 2.0f * sqrtf(u4 * (1.0f - u4));  // sqrt(1 - ct^2)
+    float sphi, cphi;
+    __sincosf(fmaf(6.2831853f, u5, -3.14159265f), &sphi, &cphi);  // angle 2 pi u5 - pi
+    const float rs = -rho * sn;                                     // undo the shift by pi
+    const float a[4] = {a0, rs * cphi, rs * sphi, rho * ct};
+    const float v[4] = {r[0] * ik, r[1] * ik, r[2] * ik, r[3] * ik};
+    apply_su2(u, i, j, a, v);
+    ++accepted;
+  }
+  float o[12];
+  reunitarise_f32(u.e[0], u.e[1], o);
+  store_f32_rows01(U, MU, p, h, g.Vh, o);
+  return accepted;
+}
+
+}  // namespace su3dev
