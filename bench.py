@@ -263,9 +263,12 @@ def run_reference(args):
     return 0
 
 
-def variant_fp32(su3, stream, steps, warmup, world, hbm_peak, peak_kind):
+def variant_fp32(su3, stream, steps, warmup, world, hbm_peak, peak_kind, precision=None):
     import numpy as np
-    with su3.Lattice(DIMS, BETA, SEED, start=su3.SU3_HOT, precision=su3.SU3_FP32_MIXED,
+    if precision is None:
+        precision = su3.SU3_FP32_MIXED
+    eft = precision == su3.SU3_FP32_EFT
+    with su3.Lattice(DIMS, BETA, SEED, start=su3.SU3_HOT, precision=precision,
                      stream=stream.cuda_stream) as lat:
         total_ms, sweep_ms, _ = time_sweeps(lat, stream, steps, warmup, SWEEPS_PER_STEP, world)
         plaq = lat.plaquette()
@@ -273,9 +276,12 @@ def variant_fp32(su3, stream, steps, warmup, world, hbm_peak, peak_kind):
     ups = 4 * V * SWEEPS_PER_STEP * steps / (total_ms * 1e-3)
     kernel_ms = statistics.mean(sweep_ms) / 8
     achieved = BYTES_PER_UPDATE["fp32_mixed"] * (V // 2) / (kernel_ms * 1e-3) / 1e9
+    gs = ("Gram-Schmidt coefficients as compensated FP32 sums (error-free transformations, ~2^-47)" if eft
+          else "FP64 Gram-Schmidt coefficients")
     return {"workload": "32^4 beta=5.7 hot start seed 7, FP32-mixed (12-real FP32 links, FP32 staple and "
-                        "heatbath, FP64 Gram-Schmidt), 2 sweeps/step",
-            "value": ups, "unit": UNIT, "ms_per_step": total_ms / steps, "dtype": "f32 (f64 reunitarisation)",
+                        "heatbath, %s), 2 sweeps/step" % gs,
+            "value": ups, "unit": UNIT, "ms_per_step": total_ms / steps,
+            "dtype": "f32 (compensated-f32 reunitarisation)" if eft else "f32 (f64 reunitarisation)",
             "plaquette_after": plaq,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": None,
@@ -393,6 +399,8 @@ def main():
     variants = {}
     if not args.no_variants:
         variants["fp32_mixed"] = variant_fp32(su3, stream, args.steps, args.warmup, 1, hbm_peak, peak_kind)
+        variants["fp32_eft"] = variant_fp32(su3, stream, args.steps, args.warmup, 1, hbm_peak, peak_kind,
+                                            su3.SU3_FP32_EFT)
         variants["batched"] = variant_batched(su3, stream, args.steps, args.warmup, hbm_peak, peak_kind)
     e2e = time_e2e(su3, DIMS, su3.SU3_FP64, max(3, args.steps // 4), 3, SWEEPS_PER_STEP)
     cpu = None if args.no_cpu_baseline else cpu_baseline_sample(False)

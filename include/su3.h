@@ -69,7 +69,7 @@ extern "C" {
 typedef struct su3_lattice* su3_handle;
 
 enum { SU3_COLD = 0, SU3_HOT = 1 };
-enum { SU3_FP64 = 0, SU3_FP32_MIXED = 1 };
+enum { SU3_FP64 = 0, SU3_FP32_MIXED = 1, SU3_FP32_EFT = 2 };
 enum {
   SU3_OK = 0,
   SU3_EINVAL = -1,   /* bad argument: NULL handle/pointer, odd or too large extent, beta <= 0, bad enum */
@@ -91,6 +91,12 @@ SU3_API int su3_create(int L0, int L1, int L2, int L3, double beta, uint64_t see
  *   2 = conj(row0 x row1) is rebuilt on every read), staple and SU(2)
  *   heatbath in FP32, Gram-Schmidt of every updated link in FP64, plaquette
  *   sums in FP64.  Uniforms use 23-bit FP32 draws (one Philox word each).
+ * precision SU3_FP32_EFT: as SU3_FP32_MIXED, except that the Gram-Schmidt
+ *   coefficients (|row0|^2, |row1|^2, <row0,row1>) are accumulated as
+ *   compensated FP32 sums (error-free transformations: TwoProd by FMA,
+ *   TwoSum), accurate to about 2^-47 relative, instead of on GB300's FP64
+ *   units (1/64 of the FP32 rate).  Same storage, same random numbers; links
+ *   agree with SU3_FP32_MIXED to within one FP32 rounding per update.
  * cuda_stream: a cudaStream_t to enqueue all work on (for example PyTorch's
  *   current stream); NULL lets the library create and own a stream.  A
  *   caller-supplied stream must outlive the handle. */
@@ -226,9 +232,9 @@ SU3_API int su3_status(su3_handle h);
  *     half-lattice structure of arrays indexed by h = s/2 (s the canonical
  *     site index; each parity holds one site of every pair 2h, 2h+1):
  *       SU3_FP64:       double2 [4 mu][2 parity][9 entries row*3+col][V/2]
- *       SU3_FP32_MIXED: float4  [4 mu][2 parity][3 groups][V/2], rows 0 and 1
- *                       only: groups (u00,u01), (u02,u10), (u11,u12), each
- *                       entry as (re, im); row 2 is conj(row0 x row1).
+ *       SU3_FP32_MIXED: float4  [4 mu][2 parity][3 columns k][V/2], rows 0
+ *                       and 1 only: column k = (re u0k, re u1k, im u0k,
+ *                       im u1k); row 2 is conj(row0 x row1).
  *   out: device pointer to one double that receives the mean plaquette, as
  *     defined for su3_plaquette, when the work enqueued on cuda_stream runs.
  *   cuda_stream: the cudaStream_t to enqueue on (NULL = the default stream).

@@ -17,7 +17,7 @@ import threading
 import numpy as np
 
 __all__ = [
-    "SU3_COLD", "SU3_HOT", "SU3_FP64", "SU3_FP32_MIXED", "Su3Error", "load_library", "library_path",
+    "SU3_COLD", "SU3_HOT", "SU3_FP64", "SU3_FP32_MIXED", "SU3_FP32_EFT", "Su3Error", "load_library", "library_path",
     "su3_create", "su3_create_ex", "su3_destroy", "su3_sweep", "su3_half_sweep", "su3_plaquette",
     "su3_links_get", "su3_links_set", "su3_sweep_count", "su3_set_sweep_count", "su3_set_stats", "su3_stats",
     "su3_info", "su3_set_block_size", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
@@ -26,7 +26,7 @@ __all__ = [
 ]
 
 SU3_COLD, SU3_HOT = 0, 1
-SU3_FP64, SU3_FP32_MIXED = 0, 1
+SU3_FP64, SU3_FP32_MIXED, SU3_FP32_EFT = 0, 1, 2
 SU3_OK, SU3_EINVAL, SU3_ENOMEM, SU3_ECUDA, SU3_ETIMEOUT, SU3_ESIZE = 0, -1, -2, -3, -4, -5
 _CODES = {SU3_EINVAL: "SU3_EINVAL", SU3_ENOMEM: "SU3_ENOMEM", SU3_ECUDA: "SU3_ECUDA",
           SU3_ETIMEOUT: "SU3_ETIMEOUT", SU3_ESIZE: "SU3_ESIZE"}

@@ -155,7 +155,7 @@ int su3_create_ex(int L0, int L1, int L2, int L3, double beta, uint64_t seed, in
   if (4 * V > 0x7fffffffLL) return fail(SU3_EINVAL, "su3_create: 4*V = %lld exceeds 2^31-1", 4 * V);
   if (!(beta > 0.0) || !std::isfinite(beta)) return fail(SU3_EINVAL, "su3_create: beta must be finite and > 0");
   if (start != SU3_COLD && start != SU3_HOT) return fail(SU3_EINVAL, "su3_create: bad start %d", start);
-  if (precision != SU3_FP64 && precision != SU3_FP32_MIXED)
+  if (precision != SU3_FP64 && precision != SU3_FP32_MIXED && precision != SU3_FP32_EFT)
     return fail(SU3_EINVAL, "su3_create: bad precision %d", precision);
 
   su3_lattice* h = new (std::nothrow) su3_lattice;

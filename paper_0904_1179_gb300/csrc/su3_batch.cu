@@ -81,7 +81,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-template <typename T>
+template <typename T, bool EFT>
 __device__ __forceinline__ void update_item(int mu, const ReplicaDesc& rd, void* links, int h, int p, uint64_t t) {
   const UpdateConsts uc{rd.inv_beta15_f64, rd.inv_beta15};
   if constexpr (std::is_same<T, double>::value) {
@@ -95,10 +95,10 @@ __device__ __forceinline__ void update_item(int mu, const ReplicaDesc& rd, void*
   } else {
     float4* U = (float4*)links + rd.offset;
     switch (mu) {
-      case 0: update_link_f32<0, true>(rd.g, U, h, p, t, rd.key, uc); break;
-      case 1: update_link_f32<1, true>(rd.g, U, h, p, t, rd.key, uc); break;
-      case 2: update_link_f32<2, true>(rd.g, U, h, p, t, rd.key, uc); break;
-      default: update_link_f32<3, true>(rd.g, U, h, p, t, rd.key, uc); break;
+      case 0: update_link_f32<0, true, EFT>(rd.g, U, h, p, t, rd.key, uc); break;
+      case 1: update_link_f32<1, true, EFT>(rd.g, U, h, p, t, rd.key, uc); break;
+      case 2: update_link_f32<2, true, EFT>(rd.g, U, h, p, t, rd.key, uc); break;
+      default: update_link_f32<3, true, EFT>(rd.g, U, h, p, t, rd.key, uc); break;
     }
   }
 }
@@ -108,7 +108,7 @@ __device__ __forceinline__ void update_item(int mu, const ReplicaDesc& rd, void*
 #define SU3_BATCH_F32_MINBLOCKS 2
 #endif
 
-template <typename T>
+template <typename T, bool EFT>
 __global__ void __launch_bounds__(kBatchMaxThreads, std::is_same<T, float>::value ? SU3_BATCH_F32_MINBLOCKS : 1)
     k_batch_sweep(BatchArgs a) {
   __shared__ int4 s_item;
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, std::is_same<T, float>::valu
     if (s_stop) return;
     const ReplicaDesc rd = a.reps[it.x];
     const int h = it.z * (int)blockDim.x + (int)threadIdx.x;
-    if (h < rd.g.Vh) update_item<T>(it.y >> 1, rd, a.links, h, it.y & 1, t);
+    if (h < rd.g.Vh) update_item<T, EFT>(it.y >> 1, rd, a.links, h, it.y & 1, t);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -164,17 +164,22 @@ __global__ void __launch_bounds__(kBatchMaxThreads, std::is_same<T, float>::valu
 
 cudaError_t launch_batch(const BatchArgs& a, int precision, int blocks, int threads, cudaStream_t s) {
   if (precision == SU3_FP64)
-    k_batch_sweep<double><<<blocks, threads, 0, s>>>(a);
+    k_batch_sweep<double, false><<<blocks, threads, 0, s>>>(a);
+  else if (precision == SU3_FP32_EFT)
+    k_batch_sweep<float, true><<<blocks, threads, 0, s>>>(a);
   else
-    k_batch_sweep<float><<<blocks, threads, 0, s>>>(a);
+    k_batch_sweep<float, false><<<blocks, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 int max_blocks_per_sm(int precision, int threads) {
   int n = 0;
-  cudaError_t e = precision == SU3_FP64
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<double>, threads, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<float>, threads, 0);
+  cudaError_t e =
+      precision == SU3_FP64
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<double, false>, threads, 0)
+          : precision == SU3_FP32_EFT
+                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<float, true>, threads, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<float, false>, threads, 0);
   return e == cudaSuccess ? n : 0;
 }
 
@@ -351,7 +356,7 @@ int check_status(su3_lattice* h, const char* what) {
 }
 
 std::string tune_key_of(const su3_lattice* h) {
-  std::string k = h->precision == SU3_FP64 ? "f64" : "f32m";
+  std::string k = h->precision == SU3_FP64 ? "f64" : (h->precision == SU3_FP32_EFT ? "f32e" : "f32m");
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceProp p{};
@@ -372,7 +377,8 @@ int su3_batch_create(int n, const int (*dims)[4], const double* betas, const uin
   *out = nullptr;
   if (n < 1 || !dims || !betas || !seeds) return fail(SU3_EINVAL, "su3_batch_create: need n >= 1 and non-NULL arrays");
   if (start != SU3_COLD && start != SU3_HOT) return fail(SU3_EINVAL, "su3_batch_create: bad start");
-  if (precision != SU3_FP64 && precision != SU3_FP32_MIXED) return fail(SU3_EINVAL, "su3_batch_create: bad precision");
+  if (precision != SU3_FP64 && precision != SU3_FP32_MIXED && precision != SU3_FP32_EFT)
+    return fail(SU3_EINVAL, "su3_batch_create: bad precision");
   su3_batch* b = new (std::nothrow) su3_batch;
   su3_lattice* h = b ? new (std::nothrow) su3_lattice : nullptr;
   if (!b || !h) {

@@ -22,8 +22,10 @@ namespace su3dev {
 // s = x0 + L0*(x1 + L1*(x2 + L2*x3)) and L0 is even, so each parity holds
 // exactly one site of every pair (2h, 2h+1).
 //   FP64:       double2 [4 mu][2 parity][9 entries (row*3+col)][Vh]
-//   FP32-mixed: float4  [4 mu][2 parity][3 groups][Vh], rows 0 and 1 only:
-//               g0 = (u00, u01), g1 = (u02, u10), g2 = (u11, u12) as re,im pairs.
+//   FP32-mixed: float4  [4 mu][2 parity][3 columns][Vh], rows 0 and 1 only:
+//               column k holds (re u0k, re u1k, im u0k, im u1k), so one load
+//               gives the row pairs (u0k, u1k) of real and of imaginary parts
+//               that the paired FP32 arithmetic (fma.rn.f32x2) works on.
 // ---------------------------------------------------------------------------
 constexpr int kEntriesF64 = 9;
 constexpr int kGroupsF32 = 3;
@@ -333,13 +335,12 @@ template <bool CG = false>
 __device__ __forceinline__ mat3<float> load_f32_rows01(const float4* __restrict__ U, int mu, int p, int h, int Vh) {
   mat3<float> m;
   const float4* b = U + link_base(mu, p, Vh, kGroupsF32) + h;
-  const float4 g0 = ld_link<CG>(b), g1 = ld_link<CG>(b + Vh), g2 = ld_link<CG>(b + 2 * (size_t)Vh);
-  m.e[0][0] = mk(g0.x, g0.y);
-  m.e[0][1] = mk(g0.z, g0.w);
-  m.e[0][2] = mk(g1.x, g1.y);
-  m.e[1][0] = mk(g1.z, g1.w);
-  m.e[1][1] = mk(g2.x, g2.y);
-  m.e[1][2] = mk(g2.z, g2.w);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4 c = ld_link<CG>(b + (size_t)k * Vh);
+    m.e[0][k] = mk(c.x, c.z);
+    m.e[1][k] = mk(c.y, c.w);
+  }
   return m;
 }
 
@@ -350,11 +351,11 @@ __device__ __forceinline__ mat3<float> load_f32(const float4* __restrict__ U, in
   return m;
 }
 
-__device__ __forceinline__ void store_f32_rows01(float4* U, int mu, int p, int h, int Vh, float r[12]) {
+// r = row 0 (re, im) x 3 columns, then row 1 (re, im) x 3 columns.
+__device__ __forceinline__ void store_f32_rows01(float4* U, int mu, int p, int h, int Vh, const float r[12]) {
   float4* b = U + link_base(mu, p, Vh, kGroupsF32) + h;
-  b[0] = make_float4(r[0], r[1], r[2], r[3]);
-  b[Vh] = make_float4(r[4], r[5], r[6], r[7]);
-  b[2 * (size_t)Vh] = make_float4(r[8], r[9], r[10], r[11]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) b[(size_t)k * Vh] = make_float4(r[2 * k], r[6 + 2 * k], r[2 * k + 1], r[6 + 2 * k + 1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -396,21 +397,76 @@ __device__ __forceinline__ void gram_schmidt_rows01(cx<double> r0[3], cx<double>
 // |e|^3 < 1e-9).  Links far from unitary (|e| or |d| >= 1e-3, e.g. arbitrary
 // input from links_set) take the full FP64 Gram-Schmidt instead.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void reunitarise_f32(const cx<float> a[3], const cx<float> b[3], float out[12]) {
-  double n0 = 0.0, n1 = 0.0, dre = 0.0, dim = 0.0;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const double ar = a[k].re, ai = a[k].im, br = b[k].re, bi = b[k].im;
-    n0 = fma(ar, ar, fma(ai, ai, n0));
-    n1 = fma(br, br, fma(bi, bi, n1));
-    dre = fma(ar, br, fma(ai, bi, dre));
-    dim = fma(ar, bi, fma(-ai, br, dim));
+// Error-free transformations (Knuth TwoSum; TwoProd by FMA): a*b = p + e and
+// a + b = s + e exactly in FP32.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// sum_k x_k y_k as hi + lo to about 2^-47 relative (compensated dot product).
+__device__ __forceinline__ void dot2(const float* x, const float* y, int n, float& hi, float& lo) {
+  hi = x[0] * y[0];
+  lo = fmaf(x[0], y[0], -hi);
+  for (int k = 1; k < n; ++k) {
+    const float p = x[k] * y[k];
+    const float pe = fmaf(x[k], y[k], -p);
+    float s, se;
+    two_sum(hi, p, s, se);
+    hi = s;
+    lo += pe + se;
   }
-  const float e0 = (float)(n0 - 1.0);
-  const float dr = (float)dre, di = (float)dim;
-  const float inv_n0 = 1.0f - e0;  // 1/n0 to O(e0^2)
-  const float cr = dr * inv_n0, ci = di * inv_n0;
-  const float e1 = (float)(n1 - 1.0) - (cr * dr + ci * di);
+}
+
+// EFT = false: the coefficients n0, n1, d are FP64 sums of the exact FP32
+// products (FP64 pipe).  EFT = true: the same sums as compensated FP32 dot
+// products (TwoProd by FMA, TwoSum), about 2^-47 relative -- FP64-class
+// accuracy on the FP32 pipe, which GB300 runs 64x faster than FP64.
+template <bool EFT>
+__device__ __forceinline__ void reunitarise_f32(const cx<float> a[3], const cx<float> b[3], float out[12]) {
+  float e0, dr, di, cr, ci, e1;
+  if (EFT) {
+    float ar[6], br[6], bx[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      ar[2 * k] = a[k].re;
+      ar[2 * k + 1] = a[k].im;
+      br[2 * k] = b[k].re;
+      br[2 * k + 1] = b[k].im;
+      bx[2 * k] = b[k].im;  // Im <a, b> = sum a.re b.im - a.im b.re
+      bx[2 * k + 1] = -b[k].re;
+    }
+    float h0, l0, h1, l1, hr, lr, hi_, li;
+    dot2(ar, ar, 6, h0, l0);
+    dot2(br, br, 6, h1, l1);
+    dot2(ar, br, 6, hr, lr);
+    dot2(ar, bx, 6, hi_, li);
+    e0 = (h0 - 1.0f) + l0;  // h0 - 1 is exact (Sterbenz)
+    dr = hr + lr;
+    di = hi_ + li;
+    const float inv_n0 = 1.0f - e0;  // 1/n0 to O(e0^2)
+    cr = dr * inv_n0;
+    ci = di * inv_n0;
+    e1 = ((h1 - 1.0f) + l1) - (cr * dr + ci * di);
+  } else {
+    double n0 = 0.0, n1 = 0.0, dre = 0.0, dim = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double ar = a[k].re, ai = a[k].im, br = b[k].re, bi = b[k].im;
+      n0 = fma(ar, ar, fma(ai, ai, n0));
+      n1 = fma(br, br, fma(bi, bi, n1));
+      dre = fma(ar, br, fma(ai, bi, dre));
+      dim = fma(ar, bi, fma(-ai, br, dim));
+    }
+    e0 = (float)(n0 - 1.0);
+    dr = (float)dre;
+    di = (float)dim;
+    const float inv_n0 = 1.0f - e0;  // 1/n0 to O(e0^2)
+    cr = dr * inv_n0;
+    ci = di * inv_n0;
+    e1 = (float)(n1 - 1.0) - (cr * dr + ci * di);
+  }
   if (fabsf(e0) < 1e-3f && fabsf(e1) < 1e-3f && fabsf(dr) < 1e-3f && fabsf(di) < 1e-3f) {
     const float s0 = e0 * fmaf(0.375f, e0, -0.5f);
     const float s1 = e1 * fmaf(0.375f, e1, -0.5f);

@@ -52,14 +52,14 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64(HalfSweepAr
   count_stats<STATS>(accepted, active, args.stats);
 }
 
-template <int MU, bool STATS>
+template <int MU, bool STATS, bool EFT>
 __global__ void __launch_bounds__(kMaxSweepThreads, SU3_F32_MINBLOCKS) k_half_sweep_f32(HalfSweepArgs args) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = h < args.geom.Vh;
   int accepted = 0;
   if (active) {
     const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15};
-    accepted = update_link_f32<MU, false>(args.geom, (float4*)args.links, h, args.parity, *args.sweep, args.key, uc);
+    accepted = update_link_f32<MU, false, EFT>(args.geom, (float4*)args.links, h, args.parity, *args.sweep, args.key, uc);
   }
   count_stats<STATS>(accepted, active, args.stats);
 }
@@ -315,9 +315,9 @@ __global__ void k_store_to_canon(ConvArgs args) {
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
-template <int MU, bool STATS>
+template <int MU, bool STATS, bool EFT>
 static cudaError_t launch_f32(const HalfSweepArgs& a, int blocks, int threads, cudaStream_t s) {
-  k_half_sweep_f32<MU, STATS><<<blocks, threads, 0, s>>>(a);
+  k_half_sweep_f32<MU, STATS, EFT><<<blocks, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -331,7 +331,9 @@ static cudaError_t launch_half_sweep_mu(const HalfSweepArgs& a, int precision, b
       k_half_sweep_f64<MU, false><<<blocks, threads, 0, s>>>(a);
     return cudaGetLastError();
   }
-  return stats ? launch_f32<MU, true>(a, blocks, threads, s) : launch_f32<MU, false>(a, blocks, threads, s);
+  if (precision == 2)
+    return stats ? launch_f32<MU, true, true>(a, blocks, threads, s) : launch_f32<MU, false, true>(a, blocks, threads, s);
+  return stats ? launch_f32<MU, true, false>(a, blocks, threads, s) : launch_f32<MU, false, false>(a, blocks, threads, s);
 }
 
 cudaError_t su3k_launch_half_sweep(const HalfSweepArgs& a, int mu, int precision, bool stats, int threads, cudaStream_t s) {

@@ -14,6 +14,7 @@
 #pragma once
 
 #include "su3_device.cuh"
+#include "su3_pair.cuh"
 
 namespace su3dev {
 
@@ -199,23 +200,108 @@ __device__ __forceinline__ int update_link_f64(const Geometry& g, double2* U, in
 }
 
 // ---------------------------------------------------------------------------
-// One FP32-mixed link update: FP32 storage (rows 0,1), FP32 staple and
-// heatbath, Gram-Schmidt coefficients in FP64.
+// FP32-mixed staple on row pairs (su3_pair.cuh): every three-link path is an
+// SU(3) matrix, so rows 0,1 are multiplied out two rows at a time and row 2
+// is completed.
 // ---------------------------------------------------------------------------
-template <int MU, bool CG, typename KEY>
+template <int MU, bool CG>
+__device__ __forceinline__ pm3 staple_p(const Geometry& g, const float4* U, const Site& st, int h, int p) {
+  const int q = p ^ 1;
+  pm3 A = zero_p();
+  const int h_pmu = nb_half(g, st, MU, +1);
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == MU) continue;
+    const int h_pnu = nb_half(g, st, nu, +1);
+    const int h_mnu = nb_half(g, st, nu, -1);
+    const int h_pmu_mnu = nb_half2(g, st, MU, nu);
+    {
+      const pm3 a = load_pm3<CG>(U, nu, q, h_pmu, g.Vh);  // U_nu(x+mu)
+      pm3 b = load_pm3<CG>(U, MU, q, h_pnu, g.Vh);        // U_mu(x+nu)
+      complete_row2_p(b);
+      pm3 t;
+      mul_nd_p(a, b, t);
+      pm3 c = load_pm3<CG>(U, nu, p, h, g.Vh);  // U_nu(x)
+      complete_row2_p(c);
+      pm3 f;
+      mul_nd_p(t, c, f);
+      complete_row2_p(f);
+      acc_p(A, f);
+    }
+    {
+      pm3 d = load_pm3<CG>(U, nu, p, h_pmu_mnu, g.Vh);  // U_nu(x+mu-nu)
+      complete_row2_p(d);
+      const pm3 e = load_pm3<CG>(U, MU, q, h_mnu, g.Vh);  // U_mu(x-nu)
+      pm3 hm;
+      mul_nn_p(e, d, hm);
+      complete_row2_p(hm);
+      pm3 f = load_pm3<CG>(U, nu, q, h_mnu, g.Vh);  // U_nu(x-nu)
+      complete_row2_p(f);
+      pm3 b;
+      mul_dn_p(hm, f, b);
+      complete_row2_p(b);
+      acc_p(A, b);
+    }
+  }
+  return A;
+}
+
+// ---------------------------------------------------------------------------
+// One FP32-mixed link update: FP32 storage (rows 0,1), FP32 staple and
+// heatbath, Gram-Schmidt coefficients in FP64 (EFT = false) or as
+// compensated FP32 sums of FP64-class accuracy (EFT = true).
+// ---------------------------------------------------------------------------
+template <int MU, bool CG, bool EFT, typename KEY>
 __device__ __forceinline__ int update_link_f32(const Geometry& g, float4* U, int h, int p, uint64_t t, const KEY& key,
                                                const UpdateConsts& uc) {
   int accepted = 0;
   const Site st = site_of(g, h, p);
   const uint32_t s = (uint32_t)canon(g, st);
-  const mat3<float> A = staple<float, MU, CG>(g, U, st, h, p);
-  mat3<float> u = load_f32<CG>(U, MU, p, h, g.Vh);
+  const pm3 A = staple_p<MU, CG>(g, U, st, h, p);
+  pm3 u = load_pm3<CG>(U, MU, p, h, g.Vh);
+  complete_row2_p(u);
   const float inv_beta15 = uc.inv_beta15;
 #pragma unroll
   for (int sub = 0; sub < 3; ++sub) {
     const int i = subrow_i(sub), j = subrow_j(sub);
-    float r[4];
-    su2_projection(u, A, i, j, r);
+    // 2x2 block (i, j) of W = U A
+    cx<float> wii, wij, wji, wjj;
+    if (sub == 0) {
+      // rows 0 and 1 as one pair: (W_0b, W_1b) = sum_c (U_0c, U_1c) A_cb
+      float2 wr[2], wi[2];
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        float2 zr = make_float2(0.f, 0.f), zi = zr;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float ar = pre(A, c, b), ai = pim(A, c, b);
+          zr = fma2(u.re[c], bc2(ar), zr);
+          zr = fma2(u.im[c], bc2(-ai), zr);
+          zi = fma2(u.re[c], bc2(ai), zi);
+          zi = fma2(u.im[c], bc2(ar), zi);
+        }
+        wr[b] = zr;
+        wi[b] = zi;
+      }
+      wii = mk(wr[0].x, wi[0].x);
+      wji = mk(wr[0].y, wi[0].y);
+      wij = mk(wr[1].x, wi[1].x);
+      wjj = mk(wr[1].y, wi[1].y);
+    } else {
+      wii = mk(0.f, 0.f);
+      wij = wii;
+      wji = wii;
+      wjj = wii;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        wii = mac(wii, pget(u, i, c), pget(A, c, i));
+        wij = mac(wij, pget(u, i, c), pget(A, c, j));
+        wji = mac(wji, pget(u, j, c), pget(A, c, i));
+        wjj = mac(wjj, pget(u, j, c), pget(A, c, j));
+      }
+    }
+    const float r[4] = {0.5f * (wii.re + wjj.re), 0.5f * (wij.im + wji.im), 0.5f * (wij.re - wji.re),
+                        0.5f * (wii.im - wjj.im)};
     const float kk = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
     const uint4 w0 = philox4x32_10(rng_counter(s, (uint32_t)(MU | (sub << 2)), t, kTagUpdate), key);
     const uint4 w1 = philox4x32_10(rng_counter(s, (uint32_t)(MU | (sub << 2) | (1 << 4)), t, kTagUpdate), key);
@@ -236,11 +322,33 @@ __device__ __forceinline__ int update_link_f32(const Geometry& g, float4* U, int
     const float rs = -rho * sn;                                     // undo the shift by pi
     const float a[4] = {a0, rs * cphi, rs * sphi, rho * ct};
     const float v[4] = {r[0] * ik, r[1] * ik, r[2] * ik, r[3] * ik};
-    apply_su2(u, i, j, a, v);
+    // R = Y V^+ with Y = m(a), V = m(v), m(q) = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]]
+    const cx<float> y00 = mk(a[0], a[3]), y01 = mk(a[2], a[1]), y10 = mk(-a[2], a[1]), y11 = mk(a[0], -a[3]);
+    const cx<float> v00 = mk(v[0], v[3]), v01 = mk(v[2], v[1]), v10 = mk(-v[2], v[1]), v11 = mk(v[0], -v[3]);
+    const cx<float> R00 = mac_cb(mac_cb(mk(0.f, 0.f), y00, v00), y01, v01);
+    const cx<float> R01 = mac_cb(mac_cb(mk(0.f, 0.f), y00, v10), y01, v11);
+    const cx<float> R10 = mac_cb(mac_cb(mk(0.f, 0.f), y10, v00), y11, v01);
+    const cx<float> R11 = mac_cb(mac_cb(mk(0.f, 0.f), y10, v10), y11, v11);
+    if (sub == 0) {
+      rotate01_p(u, R00, R01, R10, R11);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const cx<float> ui = pget(u, i, c), uj = pget(u, j, c);
+        pset(u, i, c, mac(mul(R00, ui), R01, uj));
+        pset(u, j, c, mac(mul(R10, ui), R11, uj));
+      }
+    }
     ++accepted;
   }
+  cx<float> r0[3], r1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    r0[k] = pget(u, 0, k);
+    r1[k] = pget(u, 1, k);
+  }
   float o[12];
-  reunitarise_f32(u.e[0], u.e[1], o);
+  reunitarise_f32<EFT>(r0, r1, o);
   store_f32_rows01(U, MU, p, h, g.Vh, o);
   return accepted;
 }

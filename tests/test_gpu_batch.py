@@ -37,7 +37,7 @@ def config_batch():
     return batch_96()
 
 
-@pytest.mark.parametrize("prec", [su3.SU3_FP64, su3.SU3_FP32_MIXED])
+@pytest.mark.parametrize("prec", [su3.SU3_FP64, su3.SU3_FP32_MIXED, su3.SU3_FP32_EFT])
 def test_replicas_equal_single_lattices(prec):
     with su3.Batch(MIX, BETAS, SEEDS, start=su3.SU3_HOT, precision=prec) as b:
         b.sweep(3)

@@ -193,7 +193,7 @@ def test_fp64_cold_start_chain_config0():
 
 def test_graph_replay_equals_eager_half_sweeps():
     L = (8, 8, 8, 16)
-    for prec in (su3.SU3_FP64, su3.SU3_FP32_MIXED):
+    for prec in (su3.SU3_FP64, su3.SU3_FP32_MIXED, su3.SU3_FP32_EFT):
         with su3.Lattice(L, BETA, 4, start=su3.SU3_HOT, precision=prec) as a, \
                 su3.Lattice(L, BETA, 4, start=su3.SU3_HOT, precision=prec) as b:
             a.sweep(3)
@@ -205,7 +205,7 @@ def test_graph_replay_equals_eager_half_sweeps():
             assert np.array_equal(a.get_links(), b.get_links())
 
 
-@pytest.mark.parametrize("prec", [su3.SU3_FP64, su3.SU3_FP32_MIXED])
+@pytest.mark.parametrize("prec", [su3.SU3_FP64, su3.SU3_FP32_MIXED, su3.SU3_FP32_EFT])
 def test_block_size_does_not_change_results(prec):
     L = (6, 4, 10, 8)
     ref = None
@@ -240,8 +240,9 @@ def test_resume_from_checkpoint(prec):
 # the FP32-mixed sweep
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("prec", [su3.SU3_FP32_MIXED, su3.SU3_FP32_EFT])
 @pytest.mark.parametrize("L", [(4, 4, 4, 4), (8, 8, 8, 8), (6, 4, 10, 8)])
-def test_fp32_half_sweeps_match_oracle_reading(L):
+def test_fp32_half_sweeps_match_oracle_reading(L, prec):
     seed, t = 29, 5
     U0 = oracle.hot_start(L, 7, f32=True)
     oracle.sweep(L, BETA, 2, 0, 2, U0, f32=True)
@@ -249,7 +250,7 @@ def test_fp32_half_sweeps_match_oracle_reading(L):
     flips = 0
     total = 0
     worst = 0.0
-    with su3.Lattice(L, BETA, seed, start=su3.SU3_COLD, precision=su3.SU3_FP32_MIXED) as lat:
+    with su3.Lattice(L, BETA, seed, start=su3.SU3_COLD, precision=prec) as lat:
         for mu in range(4):
             for p in range(2):
                 lat.set_links(U0)
@@ -270,7 +271,7 @@ def test_fp32_half_sweeps_match_oracle_reading(L):
                 other[pm == bool(p), mu] = False
                 assert np.array_equal(lat.get_links()[other], U0[other])
     assert flips <= max(2, total // 2000), (flips, total)
-    print("fp32 half-sweeps %s: worst |dU| %.2e, flips %d of %d" % (L, worst, flips, total))
+    print("fp32 (precision %d) half-sweeps %s: worst |dU| %.2e, flips %d of %d" % (prec, L, worst, flips, total))
 
 
 def test_fp32_links_stay_su3_and_float():
@@ -288,10 +289,10 @@ def test_fp32_links_stay_su3_and_float():
 # full-size lattice (32^4, the benchmark's workload), sampled against the oracle
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("prec", [su3.SU3_FP64, su3.SU3_FP32_MIXED])
+@pytest.mark.parametrize("prec", [su3.SU3_FP64, su3.SU3_FP32_MIXED, su3.SU3_FP32_EFT])
 def test_full_size_32x4_sampled(prec):
     L = (32, 32, 32, 32)
-    f32 = prec == su3.SU3_FP32_MIXED
+    f32 = prec != su3.SU3_FP64
     seed = 7
     U0 = oracle.hot_start(L, seed, f32=f32)
     rng = np.random.default_rng(1)
@@ -361,7 +362,7 @@ def test_fp64_chain_agrees_with_oracle_chain():
 def test_fp32_chain_agrees_with_fp64_chain():
     L = (8, 8, 8, 8)
     res = {}
-    for prec in (su3.SU3_FP64, su3.SU3_FP32_MIXED):
+    for prec in (su3.SU3_FP64, su3.SU3_FP32_MIXED, su3.SU3_FP32_EFT):
         with su3.Lattice(L, BETA, 300 + prec, start=su3.SU3_HOT, precision=prec) as lat:
             lat.sweep(200)
             p = []
@@ -369,9 +370,11 @@ def test_fp32_chain_agrees_with_fp64_chain():
                 lat.sweep(1)
                 p.append(lat.plaquette())
         res[prec] = binned(p)
-    (m64, e64), (m32, e32) = res[su3.SU3_FP64], res[su3.SU3_FP32_MIXED]
+    (m64, e64), (m32, e32), (me, ee) = res[su3.SU3_FP64], res[su3.SU3_FP32_MIXED], res[su3.SU3_FP32_EFT]
     assert abs(m64 - m32) < 3 * math.hypot(e64, e32), res
-    print("plaquette 8^4 beta 5.7: FP64 %.6f(%d)  FP32-mixed %.6f(%d)" % (m64, round(e64 * 1e6), m32, round(e32 * 1e6)))
+    assert abs(m64 - me) < 3 * math.hypot(e64, ee), res
+    print("plaquette 8^4 beta 5.7: FP64 %.6f(%d)  FP32-mixed %.6f(%d)  FP32-EFT %.6f(%d)"
+          % (m64, round(e64 * 1e6), m32, round(e32 * 1e6), me, round(ee * 1e6)))
 
 
 def test_acceptance_rate_reported():

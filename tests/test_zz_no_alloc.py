@@ -27,8 +27,9 @@ def device_layout(U, L, precision):
     else:
         soa = np.empty((4, 2, 3, V // 2, 4), dtype=np.float32)
         for p in (0, 1):
-            sel = flat[parity == bool(p)][:, :, :2].reshape(V // 2, 4, 3, 4)
-            soa[:, p] = sel.transpose(1, 2, 0, 3).astype(np.float32)
+            rows01 = flat[parity == bool(p)][:, :, :2]  # (h, mu, row, col, re/im)
+            # column k -> (re u0k, re u1k, im u0k, im u1k)
+            soa[:, p] = rows01.transpose(1, 3, 0, 4, 2).reshape(4, 3, V // 2, 4).astype(np.float32)
     return np.ascontiguousarray(soa)
 
 
