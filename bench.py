@@ -65,6 +65,10 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of each kernel as of commit 5c3fa88 (profiles/*.md).
+NCU_TRAFFIC = {"fp64": 687.6e6, "fp32_mixed": 222.0e6, "fp32_eft": 222.4e6, "batched": 3.407e9}
+
 # Peak FP64 FMA rate of GB300: 1.006 TFLOP/s measured by an FMA loop at the
 # 2070 MHz maximum SM clock (the nominal figure is 1.25 TFLOP/s).
 FP64_PEAK_TFLOPS = 1.006
@@ -284,17 +288,30 @@ def variant_fp32(su3, stream, steps, warmup, world, hbm_peak, peak_kind, precisi
             "dtype": "f32 (compensated-f32 reunitarisation)" if eft else "f32 (f64 reunitarisation)",
             "plaquette_after": plaq,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": None,
+                         "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                         "traffic": NCU_TRAFFIC["fp32_eft" if eft else "fp32_mixed"],
                          "bytes_per_launch": BYTES_PER_UPDATE["fp32_mixed"] * (V // 2),
                          "kernel_ms": kernel_ms}}
 
 
 def run_profile_case(case):
     import paper_0904_1179_gb300 as su3
-    prec = su3.SU3_FP64 if case == "fp64" else su3.SU3_FP32_MIXED
-    with su3.Lattice(DIMS, BETA, SEED, start=su3.SU3_HOT, precision=prec) as lat:
+    if case == "batched":
+        from paper_0904_1179_gb300.workloads import batch_96
+        dims, betas, seeds = batch_96()
+        with su3.Batch(dims, betas, seeds, start=su3.SU3_HOT, precision=su3.SU3_FP32_MIXED) as b:
+            b.config(64, 8, 0)
+            b.sweep(3)
+            p = b.plaquettes()
+        print(json.dumps({"profile_case": case, "replicas": len(dims), "sweeps": 3, "plaquette_0": p[0]}))
+        return 0
+    dims, beta = (DIMS, BETA)
+    if case.endswith("_64"):
+        dims, beta, case = (64, 64, 64, 64), 6.0, case[:-3]
+    prec = {"fp64": su3.SU3_FP64, "fp32_mixed": su3.SU3_FP32_MIXED, "fp32_eft": su3.SU3_FP32_EFT}[case]
+    with su3.Lattice(dims, beta, SEED, start=su3.SU3_HOT, precision=prec) as lat:
         lat.sweep(3)
-        print(json.dumps({"profile_case": case, "lattice": list(DIMS), "sweeps": 3, "plaquette": lat.plaquette()}))
+        print(json.dumps({"profile_case": case, "lattice": list(dims), "sweeps": 3, "plaquette": lat.plaquette()}))
     return 0
 
 
@@ -347,9 +364,74 @@ def variant_batched(su3, stream, steps, warmup, hbm_peak, peak_kind):
             "updates_per_step": ups, "autotuned": {"threads": cfg[0], "blocks_per_sm": cfg[1], "window": cfg[2]},
             "one_by_one": {"value": one_by_one, "unit": UNIT, "speedup": value / one_by_one},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": None,
+                         "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": NCU_TRAFFIC["batched"],
                          "bytes_per_launch": BYTES_PER_UPDATE["fp32_mixed"] * ups, "kernel_ms": sweep_ms,
                          "note": "one launch = one sweep of all replicas; duration includes the counter reset"}}
+
+
+def binned_mean(x, nbins=20):
+    import numpy as np
+    x = np.asarray(x, dtype=np.float64)
+    b = x[: (x.size // nbins) * nbins].reshape(nbins, -1).mean(axis=1)
+    return float(b.mean()), float(b.std(ddof=1) / np.sqrt(nbins))
+
+
+def run_chains(args):
+    """Plaquette chains of the precision study: 32^4 and 48^4 at beta 5.7 and 6.0, hot start,
+    200 thermalisation + 1000 measured sweeps with the plaquette after every sweep, in FP64,
+    FP32-mixed and FP32-EFT from the same Philox seed; prints one JSON line per (lattice, beta)
+    with binned means, errors and the deviations of the FP32 chains from the FP64 chain."""
+    import paper_0904_1179_gb300 as su3
+    cases = [((32, 32, 32, 32), 5.7), ((32, 32, 32, 32), 6.0), ((48, 48, 48, 48), 5.7), ((48, 48, 48, 48), 6.0)]
+    if args.chains_small:
+        cases = [((8, 8, 8, 8), 5.7)]
+    ntherm, nmeas = args.chains_therm, args.chains_meas
+    precs = [("fp64", su3.SU3_FP64), ("fp32_mixed", su3.SU3_FP32_MIXED), ("fp32_eft", su3.SU3_FP32_EFT)]
+    for L, beta in cases:
+        res = {}
+        for name, prec in precs:
+            t0 = time.perf_counter()
+            with su3.Lattice(L, beta, 11, start=su3.SU3_HOT, precision=prec) as lat:
+                lat.sweep(ntherm)
+                plaq = []
+                for _ in range(nmeas):
+                    lat.sweep(1)
+                    plaq.append(lat.plaquette())
+                lat.set_stats(True)
+                lat.sweep(10)
+                acc, prop = lat.stats()
+            m, e = binned_mean(plaq)
+            res[name] = {"mean": m, "err": e, "acceptance": acc / prop, "seconds": time.perf_counter() - t0}
+        out = {"chains": True, "lattice": list(L), "beta": beta, "therm": ntherm, "measured": nmeas, "seed": 11,
+               "start": "hot", "bins": 20, **res}
+        for name in ("fp32_mixed", "fp32_eft"):
+            d = res[name]["mean"] - res["fp64"]["mean"]
+            sig = (res[name]["err"] ** 2 + res["fp64"]["err"] ** 2) ** 0.5
+            out["delta_" + name] = {"value": d, "sigma": sig, "n_sigma": d / sig}
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_large(args):
+    """64^4 at beta 6.0, hot start seed 7, 100 sweeps: FP64 against FP32-mixed side by side."""
+    import numpy as np
+    import torch
+    import paper_0904_1179_gb300 as su3
+    L = (64, 64, 64, 64)
+    V = int(np.prod(L))
+    nsw = args.large_sweeps
+    out = {"large": True, "lattice": list(L), "beta": 6.0, "sweeps": nsw}
+    for name, prec in (("fp32_mixed", su3.SU3_FP32_MIXED), ("fp32_eft", su3.SU3_FP32_EFT), ("fp64", su3.SU3_FP64)):
+        stream = torch.cuda.Stream()
+        with su3.Lattice(L, 6.0, 7, start=su3.SU3_HOT, precision=prec, stream=stream.cuda_stream) as lat:
+            total_ms, sweep_ms, _ = time_sweeps(lat, stream, nsw, 3, 1, 1)
+            p = lat.plaquette()
+        ups = 4 * V * nsw / (total_ms * 1e-3)
+        bpu = BYTES_PER_UPDATE["fp64" if prec == su3.SU3_FP64 else "fp32_mixed"]
+        out[name] = {"value": ups, "unit": UNIT, "ms_per_sweep": total_ms / nsw, "plaquette_after": p,
+                     "algorithmic_GBps": bpu * ups / 1e9}
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def main():
@@ -360,11 +442,22 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--profile", choices=["fp64", "fp32_mixed"],
-                    help="small case for ncu: create the 32^4 lattice and run 3 graphed sweeps, nothing else")
+    ap.add_argument("--chains", action="store_true", help="precision study: FP64 vs FP32 plaquette chains")
+    ap.add_argument("--chains-small", action="store_true", help="one small chain (8^4) instead of 32^4/48^4")
+    ap.add_argument("--chains-therm", type=int, default=200)
+    ap.add_argument("--chains-meas", type=int, default=1000)
+    ap.add_argument("--large", action="store_true", help="64^4 beta 6.0, FP64 vs FP32-mixed")
+    ap.add_argument("--large-sweeps", type=int, default=100)
+    ap.add_argument("--profile", choices=["fp64", "fp32_mixed", "fp32_eft", "batched", "fp64_64", "fp32_mixed_64"],
+                    help="small case for ncu: create the 32^4 lattice (or the 96-replica batch) and run 3 graphed "
+                         "sweeps, nothing else")
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args.profile)
+    if args.chains:
+        return run_chains(args)
+    if args.large:
+        return run_large(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -420,7 +513,7 @@ def main():
         "gpu_launches": args.steps * SWEEPS_PER_STEP * 9,
         "gpu_launches_note": "headline timed region: per sweep 8 half-sweep kernels + 1 sweep-counter kernel",
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC["fp64"],
                      "kernel": "k_half_sweep_f64", "flop_per_launch": flop_per_launch, "kernel_ms": kernel_ms,
                      "hbm_frac": BYTES_PER_UPDATE["fp64"] * (V // 2) / (kernel_ms * 1e-3) / 1e9 / hbm_peak,
                      "hbm_peak": hbm_peak, "hbm_peak_kind": peak_kind},
