@@ -103,16 +103,20 @@ __device__ __forceinline__ void update_item(int mu, const ReplicaDesc& rd, void*
   }
 }
 
-// Register budget of the FP32-mixed instance: blocks of 256 threads per SM.
+// Register budget of the FP32 instances: __launch_bounds__(threads, blocks per SM).
+#ifndef SU3_BATCH_LB_THREADS
+#define SU3_BATCH_LB_THREADS kBatchMaxThreads
+#endif
 #ifndef SU3_BATCH_F32_MINBLOCKS
-#define SU3_BATCH_F32_MINBLOCKS 2
+#define SU3_BATCH_F32_MINBLOCKS 3
 #endif
 
 template <typename T, bool EFT>
-__global__ void __launch_bounds__(kBatchMaxThreads, std::is_same<T, float>::value ? SU3_BATCH_F32_MINBLOCKS : 1)
+__global__ void __launch_bounds__(SU3_BATCH_LB_THREADS, std::is_same<T, float>::value ? SU3_BATCH_F32_MINBLOCKS : 1)
     k_batch_sweep(BatchArgs a) {
   __shared__ int4 s_item;
   __shared__ int s_stop;
+  __shared__ ReplicaDesc s_rep;  // descriptor of the current item's replica (block-uniform)
   const uint64_t t = *a.sweep;
   for (;;) {
     int idx = -1;
@@ -147,13 +151,13 @@ __global__ void __launch_bounds__(kBatchMaxThreads, std::is_same<T, float>::valu
       }
       s_item = it;
       s_stop = stop;
+      if (!stop) s_rep = a.reps[it.x];
     }
     __syncthreads();
     const int4 it = s_item;
     if (s_stop) return;
-    const ReplicaDesc rd = a.reps[it.x];
     const int h = it.z * (int)blockDim.x + (int)threadIdx.x;
-    if (h < rd.g.Vh) update_item<T, EFT>(it.y >> 1, rd, a.links, h, it.y & 1, t);
+    if (h < s_rep.g.Vh) update_item<T, EFT>(it.y >> 1, s_rep, a.links, h, it.y & 1, t);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -327,9 +331,9 @@ int ensure_batch_graph(su3_lattice* h) {
 int set_config(su3_lattice* h, int threads, int blocks_per_sm, int window) {
   su3_batch* b = h->batch;
   if (threads == 0) threads = 128;
-  if (threads < 32 || threads > kBatchMaxThreads || (threads & 31))
+  if (threads < 32 || threads > SU3_BATCH_LB_THREADS || (threads & 31))
     return su3_fail(SU3_EINVAL, "su3_batch_config: threads %d is not a multiple of 32 in [32, %d]", threads,
-                    kBatchMaxThreads);
+                    (int)SU3_BATCH_LB_THREADS);
   if (blocks_per_sm < 0 || window < 0) return fail(SU3_EINVAL, "su3_batch_config: negative argument");
   SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_batch_config");
   const bool resched = threads != b->threads || window != b->window || !b->d_schedule;
@@ -590,6 +594,7 @@ int su3_batch_autotune(su3_handle h, int* threads, int* blocks_per_sm, int* wind
   std::vector<int> windows = {0};
   for (int d = 2; d <= 16 && b->n / d >= 1; d *= 2) windows.push_back((b->n + d - 1) / d);
   for (int thr : {64, 128, 256}) {
+    if (thr > SU3_BATCH_LB_THREADS) continue;
     const int fit = max_blocks_per_sm(h->precision, thr);
     for (int bps : {1, 2, 3, 4, 6, 8, 12, 16}) {
       if (bps > fit || rc != SU3_OK) break;

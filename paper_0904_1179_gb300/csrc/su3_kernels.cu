@@ -19,8 +19,11 @@ using namespace su3dev;
 // Register budget of the FP32-mixed half-sweep: __launch_bounds__(threads,
 // min blocks per SM).  The defaults keep every block size up to
 // kMaxSweepThreads legal.
+#ifndef SU3_F32_LB_THREADS
+#define SU3_F32_LB_THREADS kMaxSweepThreads
+#endif
 #ifndef SU3_F32_MINBLOCKS
-#define SU3_F32_MINBLOCKS 3
+#define SU3_F32_MINBLOCKS 4
 #endif
 
 namespace {
@@ -53,7 +56,7 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64(HalfSweepAr
 }
 
 template <int MU, bool STATS, bool EFT>
-__global__ void __launch_bounds__(kMaxSweepThreads, SU3_F32_MINBLOCKS) k_half_sweep_f32(HalfSweepArgs args) {
+__global__ void __launch_bounds__(SU3_F32_LB_THREADS, SU3_F32_MINBLOCKS) k_half_sweep_f32(HalfSweepArgs args) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = h < args.geom.Vh;
   int accepted = 0;
