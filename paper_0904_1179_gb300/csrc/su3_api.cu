@@ -76,6 +76,12 @@ void release(su3_lattice* h) {
   cudaFree(h->d_partials);
   cudaFree(h->d_plaq);
   cudaFree(h->d_stage);
+  cudaFree(h->d_stage2);
+  for (int b = 0; b < 2; ++b) {
+    if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);
+    if (h->ev_conv[b]) cudaEventDestroy(h->ev_conv[b]);
+  }
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   cudaFreeHost(h->h_plaq);
   cudaFreeHost(h->h_stats);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -136,6 +142,57 @@ bool is_batch(const su3_lattice* h) { return h && h->batch; }
 void su3_release_handle(su3_lattice* h) { release(h); }
 
 int su3_internal_fail(int code, const char* msg) { return su3_fail(code, "%s", msg); }
+
+namespace {
+
+// Second staging buffer, copy stream and events of the transfer pipeline,
+// created on first use.
+int ensure_transfer(su3_lattice* h, const char* what) {
+  if (h->copy_stream) return SU3_OK;
+  const long long chunk = h->V < kChunkSites ? h->V : kChunkSites;
+  SU3_CUDA(cudaMalloc(&h->d_stage2, (size_t)chunk * 72 * sizeof(double)), what);
+  for (int b = 0; b < 2; ++b) {
+    SU3_CUDA(cudaEventCreateWithFlags(&h->ev_copied[b], cudaEventDisableTiming), what);
+    SU3_CUDA(cudaEventCreateWithFlags(&h->ev_conv[b], cudaEventDisableTiming), what);
+  }
+  SU3_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), what);
+  return SU3_OK;
+}
+
+}  // namespace
+
+int su3_transfer(su3_lattice* h, const su3dev::Geometry& g, void* links, double* host, bool get, const char* what) {
+  int rc = ensure_transfer(h, what);
+  if (rc != SU3_OK) return rc;
+  const long long V = 2LL * g.Vh;
+  double* stage[2] = {h->d_stage, h->d_stage2};
+  int i = 0;
+  for (long long s0 = 0; s0 < V; s0 += kChunkSites, ++i) {
+    const long long n = (V - s0) < kChunkSites ? (V - s0) : kChunkSites;
+    const int b = i & 1;
+    const size_t bytes = (size_t)n * 72 * sizeof(double);
+    ConvArgs a{g, h->precision, s0, n, stage[b], links};
+    if (get) {
+      // stage[b] is free once the copy-out of chunk i-2 has finished
+      if (i >= 2) SU3_CUDA(cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0), what);
+      SU3_CUDA(su3k_launch_conv(a, false, h->stream), what);
+      SU3_CUDA(cudaEventRecord(h->ev_conv[b], h->stream), what);
+      SU3_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_conv[b], 0), what);
+      SU3_CUDA(cudaMemcpyAsync(host + s0 * 72, stage[b], bytes, cudaMemcpyDeviceToHost, h->copy_stream), what);
+      SU3_CUDA(cudaEventRecord(h->ev_copied[b], h->copy_stream), what);
+    } else {
+      // stage[b] is free once the conversion of chunk i-2 has read it
+      if (i >= 2) SU3_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_conv[b], 0), what);
+      SU3_CUDA(cudaMemcpyAsync(stage[b], host + s0 * 72, bytes, cudaMemcpyHostToDevice, h->copy_stream), what);
+      SU3_CUDA(cudaEventRecord(h->ev_copied[b], h->copy_stream), what);
+      SU3_CUDA(cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0), what);
+      SU3_CUDA(su3k_launch_conv(a, true, h->stream), what);
+      SU3_CUDA(cudaEventRecord(h->ev_conv[b], h->stream), what);
+    }
+  }
+  SU3_CUDA(cudaStreamSynchronize(h->copy_stream), what);
+  return su3_sync(h, what);
+}
 
 extern "C" {
 
@@ -274,30 +331,14 @@ int su3_links_get(su3_handle h, double* host, size_t n_doubles) {
   if (!h || !host) return fail(SU3_EINVAL, "su3_links_get: NULL argument");
   if (is_batch(h)) return fail(SU3_EINVAL, "su3_links_get: batch handle (use the su3_batch_* calls)");
   if (n_doubles != (size_t)h->V * 72) return fail(SU3_ESIZE, "su3_links_get: n = %zu, expected %lld", n_doubles, h->V * 72);
-  for (long long s0 = 0; s0 < h->V; s0 += kChunkSites) {
-    const long long n = (h->V - s0) < kChunkSites ? (h->V - s0) : kChunkSites;
-    ConvArgs a{h->geom, h->precision, s0, n, h->d_stage, h->links};
-    SU3_CUDA(su3k_launch_conv(a, false, h->stream), "su3_links_get: convert");
-    SU3_CUDA(cudaMemcpyAsync(host + s0 * 72, h->d_stage, (size_t)n * 72 * sizeof(double), cudaMemcpyDeviceToHost,
-                             h->stream),
-             "su3_links_get: copy");
-  }
-  return sync(h, "su3_links_get");
+  return su3_transfer(h, h->geom, h->links, host, true, "su3_links_get");
 }
 
 int su3_links_set(su3_handle h, const double* host, size_t n_doubles) {
   if (!h || !host) return fail(SU3_EINVAL, "su3_links_set: NULL argument");
   if (is_batch(h)) return fail(SU3_EINVAL, "su3_links_set: batch handle (use the su3_batch_* calls)");
   if (n_doubles != (size_t)h->V * 72) return fail(SU3_ESIZE, "su3_links_set: n = %zu, expected %lld", n_doubles, h->V * 72);
-  for (long long s0 = 0; s0 < h->V; s0 += kChunkSites) {
-    const long long n = (h->V - s0) < kChunkSites ? (h->V - s0) : kChunkSites;
-    SU3_CUDA(cudaMemcpyAsync(h->d_stage, host + s0 * 72, (size_t)n * 72 * sizeof(double), cudaMemcpyHostToDevice,
-                             h->stream),
-             "su3_links_set: copy");
-    ConvArgs a{h->geom, h->precision, s0, n, h->d_stage, h->links};
-    SU3_CUDA(su3k_launch_conv(a, true, h->stream), "su3_links_set: convert");
-  }
-  return sync(h, "su3_links_set");
+  return su3_transfer(h, h->geom, h->links, const_cast<double*>(host), false, "su3_links_set");
 }
 
 int su3_sweep_count(su3_handle h, uint64_t* out) {

@@ -535,21 +535,8 @@ static int batch_links(su3_handle h, int replica, double* host, size_t n_doubles
   const long long V = 2LL * g.Vh;
   if (n_doubles != (size_t)V * 72) return su3_fail(SU3_ESIZE, "%s: n = %zu, expected %lld", what, n_doubles, V * 72);
   void* base = (char*)h->links + b->offsets[replica] * b->elem_bytes;
-  for (long long s0 = 0; s0 < V; s0 += kChunkSites) {
-    const long long n = (V - s0) < kChunkSites ? (V - s0) : kChunkSites;
-    ConvArgs a{g, h->precision, s0, n, h->d_stage, base};
-    if (get) {
-      SU3_CUDA(su3k_launch_conv(a, false, h->stream), what);
-      SU3_CUDA(cudaMemcpyAsync(host + s0 * 72, h->d_stage, (size_t)n * 72 * sizeof(double), cudaMemcpyDeviceToHost,
-                               h->stream),
-               what);
-    } else {
-      SU3_CUDA(cudaMemcpyAsync(h->d_stage, host + s0 * 72, (size_t)n * 72 * sizeof(double), cudaMemcpyHostToDevice,
-                               h->stream),
-               what);
-      SU3_CUDA(su3k_launch_conv(a, true, h->stream), what);
-    }
-  }
+  const int rc = su3_transfer(h, g, base, host, get, what);
+  if (rc != SU3_OK) return rc;
   return check_status(h, what);
 }
 

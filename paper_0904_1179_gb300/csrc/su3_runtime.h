@@ -33,7 +33,11 @@ struct su3_lattice {
   double* d_plaq = nullptr;
   double* h_plaq = nullptr;               // pinned
   unsigned long long* h_stats = nullptr;  // pinned, 2 words
-  double* d_stage = nullptr;
+  double* d_stage = nullptr;   // canonical-layout staging buffers (two, for the
+  double* d_stage2 = nullptr;  // copy/convert pipeline of links_get/set)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_conv[2] = {nullptr, nullptr};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // indexed by stats_on
   int threads = kSu3DefaultThreads;
   su3dev::Geometry geom{};
@@ -45,6 +49,11 @@ struct su3_lattice {
 int su3_fail(int code, const char* fmt, ...);
 int su3_cuda_fail(cudaError_t e, const char* what);
 int su3_sync(su3_lattice* h, const char* what);
+// Copy a configuration (geometry g, device store at `links`) to or from a host
+// buffer in the canonical layout, chunk by chunk: host<->device copies on a
+// second stream overlap the layout conversions on the handle's stream.
+// Synchronises.
+int su3_transfer(su3_lattice* h, const su3dev::Geometry& g, void* links, double* host, bool get, const char* what);
 // Free a handle and everything it owns (batch part included).
 void su3_release_handle(su3_lattice* h);
 // Free the batch part of a handle (defined in su3_batch.cu).

@@ -116,13 +116,14 @@ __device__ __forceinline__ void su2_projection(const mat3<T>& u, const mat3<T>& 
 // m(q) = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]].
 template <typename T>
 __device__ __forceinline__ void apply_su2(mat3<T>& u, int i, int j, const T a[4], const T v[4]) {
-  const cx<T> y00 = mk(a[0], a[3]), y01 = mk(a[2], a[1]), y10 = mk(-a[2], a[1]), y11 = mk(a[0], -a[3]);
+  const cx<T> y00 = mk(a[0], a[3]), y01 = mk(a[2], a[1]);
   const cx<T> v00 = mk(v[0], v[3]), v01 = mk(v[2], v[1]), v10 = mk(-v[2], v[1]), v11 = mk(v[0], -v[3]);
-  // (V^+)_{pq} = conj(V_{qp})
-  cx<T> R00 = mac_cb(mac_cb(mk(T(0), T(0)), y00, v00), y01, v01);
-  cx<T> R01 = mac_cb(mac_cb(mk(T(0), T(0)), y00, v10), y01, v11);
-  cx<T> R10 = mac_cb(mac_cb(mk(T(0), T(0)), y10, v00), y11, v01);
-  cx<T> R11 = mac_cb(mac_cb(mk(T(0), T(0)), y10, v10), y11, v11);
+  // (V^+)_{pq} = conj(V_{qp}); a product of two matrices of this SU(2) form
+  // has the form again, so R10 = -conj(R01) and R11 = conj(R00).
+  const cx<T> R00 = mac_cb(mac_cb(mk(T(0), T(0)), y00, v00), y01, v01);
+  const cx<T> R01 = mac_cb(mac_cb(mk(T(0), T(0)), y00, v10), y01, v11);
+  const cx<T> R10 = mk(-R01.re, R01.im);
+  const cx<T> R11 = mk(R00.re, -R00.im);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const cx<T> ui = u.e[i][c], uj = u.e[j][c];
@@ -169,7 +170,7 @@ __device__ __forceinline__ int update_link_f64(const Geometry& g, double2* U, in
     if (!(kk > 0.0)) continue;  // k = 0: degenerate staple (measure zero), leave the subgroup
     const double ik = rsqrt(kk);
     const double inv_alpha = uc.inv_beta15_f64 * ik;  // 1/alpha = 3 / (2 beta k)
-    const double c = cos(kTwoPi * uu[1]);
+    const double c = cospi(2.0 * uu[1]);  // cos(2 pi u1)
     const double delta = -(log(uu[0]) + c * c * log(uu[2])) * inv_alpha;
     if (uu[3] * uu[3] > 1.0 - 0.5 * delta) continue;
     const double a0 = 1.0 - delta;
@@ -179,7 +180,7 @@ __device__ __forceinline__ int update_link_f64(const Geometry& g, double2* U, in
     double sn = 1.0 - ct * ct;
     sn = sn > 0.0 ? sqrt(sn) : 0.0;
     double sphi, cphi;
-    sincos(kTwoPi * uu[5], &sphi, &cphi);
+    sincospi(2.0 * uu[5], &sphi, &cphi);  // angle 2 pi u5
     const double a[4] = {a0, rho * sn * cphi, rho * sn * sphi, rho * ct};
     const double v[4] = {r[0] * ik, r[1] * ik, r[2] * ik, r[3] * ik};
     apply_su2(u, i, j, a, v);
@@ -323,12 +324,12 @@ __device__ __forceinline__ int update_link_f32(const Geometry& g, float4* U, int
     const float a[4] = {a0, rs * cphi, rs * sphi, rho * ct};
     const float v[4] = {r[0] * ik, r[1] * ik, r[2] * ik, r[3] * ik};
     // R = Y V^+ with Y = m(a), V = m(v), m(q) = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]]
-    const cx<float> y00 = mk(a[0], a[3]), y01 = mk(a[2], a[1]), y10 = mk(-a[2], a[1]), y11 = mk(a[0], -a[3]);
+    const cx<float> y00 = mk(a[0], a[3]), y01 = mk(a[2], a[1]);
     const cx<float> v00 = mk(v[0], v[3]), v01 = mk(v[2], v[1]), v10 = mk(-v[2], v[1]), v11 = mk(v[0], -v[3]);
     const cx<float> R00 = mac_cb(mac_cb(mk(0.f, 0.f), y00, v00), y01, v01);
     const cx<float> R01 = mac_cb(mac_cb(mk(0.f, 0.f), y00, v10), y01, v11);
-    const cx<float> R10 = mac_cb(mac_cb(mk(0.f, 0.f), y10, v00), y11, v01);
-    const cx<float> R11 = mac_cb(mac_cb(mk(0.f, 0.f), y10, v10), y11, v11);
+    const cx<float> R10 = mk(-R01.re, R01.im);  // R keeps the SU(2) form
+    const cx<float> R11 = mk(R00.re, -R00.im);
     if (sub == 0) {
       rotate01_p(u, R00, R01, R10, R11);
     } else {
