@@ -136,12 +136,21 @@ SU3_API int su3_links_set(su3_handle h, const double* host, size_t n_doubles);
 SU3_API int su3_sweep_count(su3_handle h, uint64_t* out);
 SU3_API int su3_set_sweep_count(su3_handle h, uint64_t n);
 
-/* Acceptance statistics of the one-hit SU(2) proposals.  Counting is off by
+/* Acceptance statistics of the SU(2) proposals (accepted, drawn).  Counting is off by
  * default (it costs a warp reduction and an atomic per warp); enabling resets
  * the counters.  su3_stats synchronises and returns the totals since the last
  * enable or reset. */
 SU3_API int su3_set_stats(su3_handle h, int enable);
 SU3_API int su3_stats(su3_handle h, uint64_t* accepted, uint64_t* proposed);
+
+/* SU(2) heatbath variant.  max_tries = 1 (the default) is the one-hit
+ * heatbath of the paper's MPI code (Sec. 2.1 remark: one proposal, 97.2%
+ * accepted at beta = 5.7; a rejected proposal leaves the subgroup unchanged).
+ * max_tries > 1 is the repeat-until-accepted heatbath of its non-MPI program:
+ * up to max_tries Kennedy-Pendleton proposals per subgroup, proposal n drawn
+ * from counter word mu | sub<<2 | call<<4 | n<<6 (proposal 0 is the one-hit
+ * draw).  1 <= max_tries <= 2^20.  Valid for single lattices and batches. */
+SU3_API int su3_set_heatbath(su3_handle h, int max_tries);
 
 /* Lattice properties of a handle. */
 SU3_API int su3_info(su3_handle h, int dims[4], double* beta, uint64_t* seed, int* precision);

@@ -67,15 +67,17 @@ def _load():
         lib.oracle_plaquette.restype = ctypes.c_double
         lib.oracle_staple.argtypes = [_i32p, _f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _f64p]
         lib.oracle_half_sweep.argtypes = [_i32p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
-                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, _f64p, _u64p]
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, _f64p, _u64p, ctypes.c_int]
         lib.oracle_sweep.argtypes = [_i32p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
-                                     ctypes.c_int, _f64p, _u64p, _f64p]
+                                     ctypes.c_int, _f64p, _u64p, _f64p, ctypes.c_int]
         lib.oracle_update_links.argtypes = [_i32p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
-                                            _i64p, ctypes.c_int64, ctypes.c_int, _f64p, _u64p]
+                                            _i64p, ctypes.c_int64, ctypes.c_int, _f64p, _u64p, ctypes.c_int]
         lib.oracle_updated_links.argtypes = [_i32p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
-                                             ctypes.c_int, _i64p, ctypes.c_int64, ctypes.c_int, _f64p, _f64p, _f64p]
+                                             ctypes.c_int, _i64p, ctypes.c_int64, ctypes.c_int, _f64p, _f64p, _f64p,
+                                             ctypes.c_int]
         lib.oracle_gauge_transform.argtypes = [_i32p, ctypes.c_uint64, _f64p]
-        lib.oracle_kp_draws.argtypes = [ctypes.c_double, ctypes.c_uint64, ctypes.c_int64, _f64p, _u8p]
+        lib.oracle_kp_draws.argtypes = [ctypes.c_double, ctypes.c_uint64, ctypes.c_int64, _f64p, _u8p, ctypes.c_int,
+                                         _i64p]
         lib.oracle_kp_draws.restype = ctypes.c_int64
         _lib = lib
         return lib
@@ -154,38 +156,40 @@ def staple(L, U, site, mu, f32=False):
     return out.reshape(3, 3, 2)
 
 
-def half_sweep(L, beta, seed, t, mu, parity, U, f32=False, reverse=False):
-    """One checkerboard half-sweep in place; returns (accepted, proposed) SU(2) hits."""
+def half_sweep(L, beta, seed, t, mu, parity, U, f32=False, reverse=False, max_tries=1):
+    """One checkerboard half-sweep in place; returns (accepted, proposed) SU(2) proposals.
+
+    max_tries = 1: one-hit heatbath; > 1: repeat until accepted, at most max_tries proposals."""
     _check_links(L, U)
     st = np.zeros(2, dtype=np.uint64)
     _rc(_load().oracle_half_sweep(_dims(L), float(beta), ctypes.c_uint64(seed), ctypes.c_uint64(t), int(mu),
                                   int(parity), int(bool(f32)), int(bool(reverse)), _ptr(U, ctypes.c_double),
-                                  _ptr(st, ctypes.c_uint64)))
+                                  _ptr(st, ctypes.c_uint64), int(max_tries)))
     return int(st[0]), int(st[1])
 
 
-def sweep(L, beta, seed, t0, nsweeps, U, f32=False):
+def sweep(L, beta, seed, t0, nsweeps, U, f32=False, max_tries=1):
     """nsweeps sweeps in place from sweep index t0; returns ((accepted, proposed), plaquette per sweep)."""
     _check_links(L, U)
     st = np.zeros(2, dtype=np.uint64)
     plaq = np.zeros(max(int(nsweeps), 1), dtype=np.float64)
     _rc(_load().oracle_sweep(_dims(L), float(beta), ctypes.c_uint64(seed), ctypes.c_uint64(t0), int(nsweeps),
                              int(bool(f32)), _ptr(U, ctypes.c_double), _ptr(st, ctypes.c_uint64),
-                             _ptr(plaq, ctypes.c_double)))
+                             _ptr(plaq, ctypes.c_double), int(max_tries)))
     return (int(st[0]), int(st[1])), plaq[: int(nsweeps)]
 
 
-def update_links(L, beta, seed, t, mu, sites, U, f32=False):
+def update_links(L, beta, seed, t, mu, sites, U, f32=False, max_tries=1):
     _check_links(L, U)
     s = np.ascontiguousarray(np.asarray(sites, dtype=np.int64))
     st = np.zeros(2, dtype=np.uint64)
     _rc(_load().oracle_update_links(_dims(L), float(beta), ctypes.c_uint64(seed), ctypes.c_uint64(t), int(mu),
                                     _ptr(s, ctypes.c_int64), s.size, int(bool(f32)), _ptr(U, ctypes.c_double),
-                                    _ptr(st, ctypes.c_uint64)))
+                                    _ptr(st, ctypes.c_uint64), int(max_tries)))
     return int(st[0]), int(st[1])
 
 
-def updated_links(L, beta, seed, t, mu, sites, U, f32=False, with_margins=False):
+def updated_links(L, beta, seed, t, mu, sites, U, f32=False, with_margins=False, max_tries=1):
     """Updated values of the listed links of direction mu, each from the unchanged U; shape (n, 3, 3, 2).
 
     With with_margins, also returns (n, 3) accept margins u3^2 - (1 - delta/2) per subgroup
@@ -196,7 +200,7 @@ def updated_links(L, beta, seed, t, mu, sites, U, f32=False, with_margins=False)
     marg = np.empty((s.size, 3), dtype=np.float64)
     _rc(_load().oracle_updated_links(_dims(L), float(beta), ctypes.c_uint64(seed), ctypes.c_uint64(t), int(mu),
                                      _ptr(s, ctypes.c_int64), s.size, int(bool(f32)), _ptr(U, ctypes.c_double),
-                                     _ptr(out, ctypes.c_double), _ptr(marg, ctypes.c_double)))
+                                     _ptr(out, ctypes.c_double), _ptr(marg, ctypes.c_double), int(max_tries)))
     return (out, marg) if with_margins else out
 
 
@@ -205,12 +209,16 @@ def gauge_transform(L, seed, U):
     _rc(_load().oracle_gauge_transform(_dims(L), ctypes.c_uint64(seed), _ptr(U, ctypes.c_double)))
 
 
-def kp_draws(alpha, seed, n):
-    """n one-hit Kennedy-Pendleton draws at fixed alpha; returns (quaternions (n,4), accepted (n,) bool)."""
+def kp_draws(alpha, seed, n, max_tries=1, with_tries=False):
+    """n Kennedy-Pendleton draws at fixed alpha with up to max_tries proposals each;
+    returns (quaternions (n,4), accepted (n,) bool[, proposals drawn])."""
     out = np.zeros((int(n), 4), dtype=np.float64)
     acc = np.zeros(int(n), dtype=np.uint8)
+    tries = ctypes.c_int64(0)
     _load().oracle_kp_draws(float(alpha), ctypes.c_uint64(seed), int(n), _ptr(out, ctypes.c_double),
-                            _ptr(acc, ctypes.c_uint8))
+                            _ptr(acc, ctypes.c_uint8), int(max_tries), ctypes.byref(tries))
+    if with_tries:
+        return out, acc.astype(bool), tries.value
     return out, acc.astype(bool)
 
 

@@ -357,24 +357,26 @@ static int kp_one_hit(double alpha, const double u[6], double a[4])
     return 1;
 }
 
-/* Six uniforms of subgroup `sub` of the update of link (s, mu) at sweep t. */
-static void subgroup_uniforms(uint64_t seed, int64_t s, int mu, int sub, uint64_t t, int f32, double u[6])
+/* Six uniforms of proposal `tr` (0 for the one-hit heatbath) of subgroup
+ * `sub` of the update of link (s, mu) at sweep t. */
+static void subgroup_uniforms(uint64_t seed, int64_t s, int mu, int sub, int tr, uint64_t t, int f32, double u[6])
 {
     uint32_t w[4];
+    const uint32_t base = (uint32_t)(mu | (sub << 2)) | ((uint32_t)tr << 6);
     if (!f32) {
         int call;
         for (call = 0; call < 3; call++) {
-            draw_words(seed, (uint32_t)s, (uint32_t)(mu | (sub << 2) | (call << 4)), t, 0u, w);
+            draw_words(seed, (uint32_t)s, base | (uint32_t)(call << 4), t, 0u, w);
             u[2 * call] = oracle_u01_f64(w[0], w[1]);
             u[2 * call + 1] = oracle_u01_f64(w[2], w[3]);
         }
     } else {
-        draw_words(seed, (uint32_t)s, (uint32_t)(mu | (sub << 2)), t, 0u, w);
+        draw_words(seed, (uint32_t)s, base, t, 0u, w);
         u[0] = oracle_u01_f32(w[0]);
         u[1] = oracle_u01_f32(w[1]);
         u[2] = oracle_u01_f32(w[2]);
         u[3] = oracle_u01_f32(w[3]);
-        draw_words(seed, (uint32_t)s, (uint32_t)(mu | (sub << 2) | (1 << 4)), t, 0u, w);
+        draw_words(seed, (uint32_t)s, base | (1u << 4), t, 0u, w);
         u[4] = oracle_u01_f32(w[0]);
         u[5] = oracle_u01_f32(w[1]);
     }
@@ -390,9 +392,14 @@ static void su2_from_quaternion(const double a[4], cplx m[2][2])
 }
 
 /* One Cabibbo-Marinari update of link (s, mu): three SU(2) subgroups, each
- * with a one-hit KP heatbath in the field of the staple A, then GS. */
+ * a Kennedy-Pendleton heatbath in the field of the staple A, then GS.
+ * max_tries = 1 is the one-hit heatbath of the MPI code; max_tries > 1
+ * repeats the proposal until it is accepted, at most max_tries times (the
+ * non-MPI program's repeat-until-accepted heatbath, Sec. 2.1 remark).
+ * stats[0] counts accepted proposals, stats[1] proposals drawn (a degenerate
+ * subgroup counts as one). */
 static mat3 update_link(const geom* g, const double* U, double beta, uint64_t seed, uint64_t t, int64_t s, int mu,
-                        int f32, uint64_t* stats, double* margins)
+                        int f32, int max_tries, uint64_t* stats, double* margins)
 {
     static const int sub_rows[3][2] = {{0, 1}, {0, 2}, {1, 2}};
     mat3 A = staple(g, U, s, mu, f32);
@@ -402,38 +409,45 @@ static mat3 update_link(const geom* g, const double* U, double beta, uint64_t se
         int i = sub_rows[sub][0], j = sub_rows[sub][1];
         mat3 W = m_mul(&u, &A);
         double r[4], k, uu[6], a[4];
+        int tr;
         r[0] = 0.5 * (W.e[i][i].re + W.e[j][j].re);
         r[1] = 0.5 * (W.e[i][j].im + W.e[j][i].im);
         r[2] = 0.5 * (W.e[i][j].re - W.e[j][i].re);
         r[3] = 0.5 * (W.e[i][i].im - W.e[j][j].im);
         k = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
-        subgroup_uniforms(seed, s, mu, sub, t, f32, uu);
-        if (stats) stats[1]++;
         if (margins) margins[sub] = NAN;
-        if (!(k > 1e-300)) continue; /* degenerate staple: measure zero, leave the subgroup */
-        if (margins) {
-            /* distance of the one-hit accept test from its threshold */
-            double c = cos(2.0 * ORACLE_PI * uu[1]);
-            double delta = -(log(uu[0]) + c * c * log(uu[2])) / (2.0 * beta * k / 3.0);
-            margins[sub] = uu[3] * uu[3] - (1.0 - 0.5 * delta);
+        if (!(k > 1e-300)) { /* degenerate staple: measure zero, leave the subgroup */
+            if (stats) stats[1]++;
+            continue;
         }
-        if (kp_one_hit(2.0 * beta * k / 3.0, uu, a)) {
-            cplx y[2][2], v[2][2], vd[2][2], R[2][2];
-            double rn[4];
-            int p, q, col;
-            rn[0] = r[0] / k; rn[1] = r[1] / k; rn[2] = r[2] / k; rn[3] = r[3] / k;
-            su2_from_quaternion(a, y);
-            su2_from_quaternion(rn, v);
-            for (p = 0; p < 2; p++)
-                for (q = 0; q < 2; q++) vd[p][q] = c_conj(v[q][p]);
-            for (p = 0; p < 2; p++)
-                for (q = 0; q < 2; q++) R[p][q] = c_add(c_mul(y[p][0], vd[0][q]), c_mul(y[p][1], vd[1][q]));
-            for (col = 0; col < 3; col++) {
-                cplx ui = u.e[i][col], uj = u.e[j][col];
-                u.e[i][col] = c_add(c_mul(R[0][0], ui), c_mul(R[0][1], uj));
-                u.e[j][col] = c_add(c_mul(R[1][0], ui), c_mul(R[1][1], uj));
+        for (tr = 0; tr < max_tries; tr++) {
+            subgroup_uniforms(seed, s, mu, sub, tr, t, f32, uu);
+            if (stats) stats[1]++;
+            if (margins && tr == 0) {
+                /* distance of the first proposal's accept test from its threshold */
+                double c = cos(2.0 * ORACLE_PI * uu[1]);
+                double delta = -(log(uu[0]) + c * c * log(uu[2])) / (2.0 * beta * k / 3.0);
+                margins[sub] = uu[3] * uu[3] - (1.0 - 0.5 * delta);
             }
-            if (stats) stats[0]++;
+            if (kp_one_hit(2.0 * beta * k / 3.0, uu, a)) {
+                cplx y[2][2], v[2][2], vd[2][2], R[2][2];
+                double rn[4];
+                int p, q, col;
+                rn[0] = r[0] / k; rn[1] = r[1] / k; rn[2] = r[2] / k; rn[3] = r[3] / k;
+                su2_from_quaternion(a, y);
+                su2_from_quaternion(rn, v);
+                for (p = 0; p < 2; p++)
+                    for (q = 0; q < 2; q++) vd[p][q] = c_conj(v[q][p]);
+                for (p = 0; p < 2; p++)
+                    for (q = 0; q < 2; q++) R[p][q] = c_add(c_mul(y[p][0], vd[0][q]), c_mul(y[p][1], vd[1][q]));
+                for (col = 0; col < 3; col++) {
+                    cplx ui = u.e[i][col], uj = u.e[j][col];
+                    u.e[i][col] = c_add(c_mul(R[0][0], ui), c_mul(R[0][1], uj));
+                    u.e[j][col] = c_add(c_mul(R[1][0], ui), c_mul(R[1][1], uj));
+                }
+                if (stats) stats[0]++;
+                break;
+            }
         }
     }
     reunitarise(&u);
@@ -549,16 +563,17 @@ int oracle_staple(const int L[4], const double* U, int64_t site, int mu, int f32
  * result must not depend on it).  stats[0] += accepted, stats[1] += proposed
  * SU(2) hits (stats may be NULL). */
 int oracle_half_sweep(const int L[4], double beta, uint64_t seed, uint64_t t, int mu, int parity, int f32, int reverse,
-                      double* U, uint64_t* stats)
+                      double* U, uint64_t* stats, int max_tries)
 {
     geom g;
     int64_t i;
     if (check_dims(L) || mu < 0 || mu > 3 || parity < 0 || parity > 1 || !(beta > 0.0) || !isfinite(beta)) return -1;
+    if (max_tries < 1) return -1;
     if (geom_init(&g, L)) return -2;
     for (i = 0; i < g.V; i++) {
         int64_t s = reverse ? g.V - 1 - i : i;
         if (site_parity(L, s) != parity) continue;
-        store_link(U, s, mu, update_link(&g, U, beta, seed, t, s, mu, f32, stats, NULL), f32);
+        store_link(U, s, mu, update_link(&g, U, beta, seed, t, s, mu, f32, max_tries, stats, NULL), f32);
     }
     geom_free(&g);
     return 0;
@@ -568,13 +583,13 @@ int oracle_half_sweep(const int L[4], double beta, uint64_t seed, uint64_t t, in
  * for each mu the even then the odd sites.  plaq (may be NULL) receives the
  * mean plaquette after each sweep. */
 int oracle_sweep(const int L[4], double beta, uint64_t seed, uint64_t t0, int nsweeps, int f32, double* U, uint64_t* stats,
-                 double* plaq)
+                 double* plaq, int max_tries)
 {
     int n, mu, p, rc;
     for (n = 0; n < nsweeps; n++) {
         for (mu = 0; mu < 4; mu++)
             for (p = 0; p < 2; p++) {
-                rc = oracle_half_sweep(L, beta, seed, t0 + (uint64_t)n, mu, p, f32, 0, U, stats);
+                rc = oracle_half_sweep(L, beta, seed, t0 + (uint64_t)n, mu, p, f32, 0, U, stats, max_tries);
                 if (rc) return rc;
             }
         if (plaq) plaq[n] = oracle_plaquette(L, U, f32);
@@ -586,16 +601,17 @@ int oracle_sweep(const int L[4], double beta, uint64_t seed, uint64_t t0, int ns
  * list order, in place.  Used for sampled checks on large lattices and for the
  * single-link equilibrium test. */
 int oracle_update_links(const int L[4], double beta, uint64_t seed, uint64_t t, int mu, const int64_t* sites, int64_t n,
-                        int f32, double* U, uint64_t* stats)
+                        int f32, double* U, uint64_t* stats, int max_tries)
 {
     geom g;
     int64_t i;
-    if (check_dims(L) || mu < 0 || mu > 3 || !(beta > 0.0)) return -1;
+    if (check_dims(L) || mu < 0 || mu > 3 || !(beta > 0.0) || max_tries < 1) return -1;
     if (geom_init(&g, L)) return -2;
     for (i = 0; i < n; i++) {
         if (sites[i] < 0 || sites[i] >= g.V) { geom_free(&g); return -1; }
     }
-    for (i = 0; i < n; i++) store_link(U, sites[i], mu, update_link(&g, U, beta, seed, t, sites[i], mu, f32, stats, NULL), f32);
+    for (i = 0; i < n; i++)
+        store_link(U, sites[i], mu, update_link(&g, U, beta, seed, t, sites[i], mu, f32, max_tries, stats, NULL), f32);
     geom_free(&g);
     return 0;
 }
@@ -606,17 +622,17 @@ int oracle_update_links(const int L[4], double beta, uint64_t seed, uint64_t t, 
  * the one-hit proposal is accepted iff it is <= 0 (NaN for a skipped
  * degenerate subgroup). */
 int oracle_updated_links(const int L[4], double beta, uint64_t seed, uint64_t t, int mu, const int64_t* sites, int64_t n,
-                         int f32, const double* U, double* out, double* margins)
+                         int f32, const double* U, double* out, double* margins, int max_tries)
 {
     geom g;
     int64_t i;
-    if (check_dims(L) || mu < 0 || mu > 3 || !(beta > 0.0)) return -1;
+    if (check_dims(L) || mu < 0 || mu > 3 || !(beta > 0.0) || max_tries < 1) return -1;
     if (geom_init(&g, L)) return -2;
     for (i = 0; i < n; i++) {
         mat3 m;
         int r, c;
         if (sites[i] < 0 || sites[i] >= g.V) { geom_free(&g); return -1; }
-        m = update_link(&g, U, beta, seed, t, sites[i], mu, f32, NULL, margins ? margins + 3 * i : NULL);
+        m = update_link(&g, U, beta, seed, t, sites[i], mu, f32, max_tries, NULL, margins ? margins + 3 * i : NULL);
         if (f32) {
             for (r = 0; r < 2; r++)
                 for (c = 0; c < 3; c++) {
@@ -661,25 +677,31 @@ int oracle_gauge_transform(const int L[4], uint64_t seed, double* U)
     return 0;
 }
 
-/* n independent one-hit KP draws at fixed alpha (Philox tag 3, counter
- * (i, 0, 0)); out[4*i..4*i+3] = quaternion if accepted[i], else zeros.
- * Returns the number accepted. */
-int64_t oracle_kp_draws(double alpha, uint64_t seed, int64_t n, double* out, uint8_t* accepted)
+/* n independent KP draws at fixed alpha (Philox tag 3, counter
+ * (i, call<<4 | try<<6, 0)), each with up to max_tries proposals;
+ * out[4*i..4*i+3] = quaternion if accepted[i], else zeros.  tries (may be
+ * NULL) receives the number of proposals drawn.  Returns the number accepted. */
+int64_t oracle_kp_draws(double alpha, uint64_t seed, int64_t n, double* out, uint8_t* accepted, int max_tries,
+                        int64_t* tries)
 {
-    int64_t i, nacc = 0;
+    int64_t i, nacc = 0, ntry = 0;
     for (i = 0; i < n; i++) {
         uint32_t w[4];
         double u[6], a[4] = {0.0, 0.0, 0.0, 0.0};
-        int call, ok;
-        for (call = 0; call < 3; call++) {
-            draw_words(seed, (uint32_t)i, (uint32_t)(call << 4), (uint64_t)(i >> 32), 3u, w);
-            u[2 * call] = oracle_u01_f64(w[0], w[1]);
-            u[2 * call + 1] = oracle_u01_f64(w[2], w[3]);
+        int call, ok = 0, tr;
+        for (tr = 0; tr < max_tries && !ok; tr++) {
+            for (call = 0; call < 3; call++) {
+                draw_words(seed, (uint32_t)i, (uint32_t)((call << 4) | (tr << 6)), (uint64_t)(i >> 32), 3u, w);
+                u[2 * call] = oracle_u01_f64(w[0], w[1]);
+                u[2 * call + 1] = oracle_u01_f64(w[2], w[3]);
+            }
+            ok = kp_one_hit(alpha, u, a);
+            ntry++;
         }
-        ok = kp_one_hit(alpha, u, a);
         out[4 * i] = a[0]; out[4 * i + 1] = a[1]; out[4 * i + 2] = a[2]; out[4 * i + 3] = a[3];
         accepted[i] = (uint8_t)ok;
         nacc += ok;
     }
+    if (tries) *tries = ntry;
     return nacc;
 }

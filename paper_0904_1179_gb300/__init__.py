@@ -20,7 +20,7 @@ __all__ = [
     "SU3_COLD", "SU3_HOT", "SU3_FP64", "SU3_FP32_MIXED", "SU3_FP32_EFT", "Su3Error", "load_library", "library_path",
     "su3_create", "su3_create_ex", "su3_destroy", "su3_sweep", "su3_half_sweep", "su3_plaquette",
     "su3_links_get", "su3_links_set", "su3_sweep_count", "su3_set_sweep_count", "su3_set_stats", "su3_stats",
-    "su3_info", "su3_set_block_size", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
+    "su3_info", "su3_set_block_size", "su3_set_heatbath", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
     "su3_batch_links_get", "su3_batch_links_set", "su3_batch_size", "su3_batch_config", "su3_batch_get_config",
     "su3_batch_autotune", "su3_batch_debug", "su3_status", "Batch", "su3_plaquette_noalloc", "su3_last_error", "su3_version", "Lattice", "links_shape", "EXPORTS",
 ]
@@ -59,6 +59,7 @@ EXPORTS = [
     ("su3_stats", ctypes.c_int, [_h, _pu64, _pu64]),
     ("su3_info", ctypes.c_int, [_h, _pi, _pd, _pu64, _pi]),
     ("su3_set_block_size", ctypes.c_int, [_h, ctypes.c_int]),
+    ("su3_set_heatbath", ctypes.c_int, [_h, ctypes.c_int]),
     ("su3_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _pd, _pu64, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(_h)]),
     ("su3_batch_sweep", ctypes.c_int, [_h, ctypes.c_int]),
@@ -204,6 +205,11 @@ def su3_set_block_size(h, threads):
     _check(load_library().su3_set_block_size(h, threads))
 
 
+def su3_set_heatbath(h, max_tries):
+    """1: one-hit heatbath (default); > 1: repeat until accepted, at most max_tries proposals."""
+    _check(load_library().su3_set_heatbath(h, int(max_tries)))
+
+
 def su3_batch_create(dims, betas, seeds, start, precision, cuda_stream=None):
     """dims: sequence of n (L0, L1, L2, L3); betas, seeds: length n."""
     n = len(dims)
@@ -347,6 +353,9 @@ class Batch:
     def autotune(self):
         return su3_batch_autotune(self.handle)
 
+    def set_heatbath(self, max_tries):
+        su3_set_heatbath(self.handle, max_tries)
+
     def debug(self, wait_limit_s, withhold_item=-1):
         su3_batch_debug(self.handle, wait_limit_s, withhold_item)
 
@@ -418,3 +427,6 @@ class Lattice:
 
     def set_block_size(self, threads):
         su3_set_block_size(self.handle, threads)
+
+    def set_heatbath(self, max_tries):
+        su3_set_heatbath(self.handle, max_tries)

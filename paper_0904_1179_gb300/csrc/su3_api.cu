@@ -96,6 +96,7 @@ HalfSweepArgs half_sweep_args(const su3_lattice* h, int parity) {
   a.beta = h->beta;
   a.inv_beta15 = (float)(1.5 / h->beta);
   a.inv_beta15_f64 = 1.5 / h->beta;
+  a.max_tries = h->max_tries;
   a.sweep = h->d_sweep;
   a.links = h->links;
   a.stats = h->d_stats;
@@ -381,6 +382,19 @@ int su3_info(su3_handle h, int dims[4], double* beta, uint64_t* seed, int* preci
   if (beta) *beta = h->beta;
   if (seed) *seed = h->seed;
   if (precision) *precision = h->precision;
+  return SU3_OK;
+}
+
+int su3_set_heatbath(su3_handle h, int max_tries) {
+  if (!h) return fail(SU3_EINVAL, "su3_set_heatbath: NULL handle");
+  if (max_tries < 1 || max_tries > kMaxHeatbathTries)
+    return fail(SU3_EINVAL, "su3_set_heatbath: max_tries %d not in [1, %d]", max_tries, kMaxHeatbathTries);
+  if (max_tries != h->max_tries) {
+    SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_set_heatbath");
+    drop_graphs(h);
+    if (h->batch) su3_batch_invalidate(h->batch);
+    h->max_tries = max_tries;
+  }
   return SU3_OK;
 }
 

@@ -61,6 +61,7 @@ struct BatchArgs {
   void* links;
   long long wait_ns;
   int withhold_item;  // fault-injection hook: this item never signals completion (-1: none)
+  int max_tries;      // SU(2) proposals per subgroup (1: one-hit heatbath)
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -81,24 +82,25 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-template <typename T, bool EFT>
-__device__ __forceinline__ void update_item(int mu, const ReplicaDesc& rd, void* links, int h, int p, uint64_t t) {
-  const UpdateConsts uc{rd.inv_beta15_f64, rd.inv_beta15};
+template <typename T, bool EFT, bool REPEAT>
+__device__ __forceinline__ void update_item(int mu, const ReplicaDesc& rd, void* links, int h, int p, uint64_t t,
+                                            int max_tries) {
+  const UpdateConsts uc{rd.inv_beta15_f64, rd.inv_beta15, max_tries};
   if constexpr (std::is_same<T, double>::value) {
     double2* U = (double2*)links + rd.offset;
     switch (mu) {
-      case 0: update_link_f64<0, true>(rd.g, U, h, p, t, rd.key, uc); break;
-      case 1: update_link_f64<1, true>(rd.g, U, h, p, t, rd.key, uc); break;
-      case 2: update_link_f64<2, true>(rd.g, U, h, p, t, rd.key, uc); break;
-      default: update_link_f64<3, true>(rd.g, U, h, p, t, rd.key, uc); break;
+      case 0: update_link_f64<0, true, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
+      case 1: update_link_f64<1, true, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
+      case 2: update_link_f64<2, true, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
+      default: update_link_f64<3, true, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
     }
   } else {
     float4* U = (float4*)links + rd.offset;
     switch (mu) {
-      case 0: update_link_f32<0, true, EFT>(rd.g, U, h, p, t, rd.key, uc); break;
-      case 1: update_link_f32<1, true, EFT>(rd.g, U, h, p, t, rd.key, uc); break;
-      case 2: update_link_f32<2, true, EFT>(rd.g, U, h, p, t, rd.key, uc); break;
-      default: update_link_f32<3, true, EFT>(rd.g, U, h, p, t, rd.key, uc); break;
+      case 0: update_link_f32<0, true, EFT, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
+      case 1: update_link_f32<1, true, EFT, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
+      case 2: update_link_f32<2, true, EFT, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
+      default: update_link_f32<3, true, EFT, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
     }
   }
 }
@@ -111,7 +113,7 @@ __device__ __forceinline__ void update_item(int mu, const ReplicaDesc& rd, void*
 #define SU3_BATCH_F32_MINBLOCKS 3
 #endif
 
-template <typename T, bool EFT>
+template <typename T, bool EFT, bool REPEAT>
 __global__ void __launch_bounds__(SU3_BATCH_LB_THREADS, std::is_same<T, float>::value ? SU3_BATCH_F32_MINBLOCKS : 1)
     k_batch_sweep(BatchArgs a) {
   __shared__ int4 s_item;
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(SU3_BATCH_LB_THREADS, std::is_same<T, float>::
     const int4 it = s_item;
     if (s_stop) return;
     const int h = it.z * (int)blockDim.x + (int)threadIdx.x;
-    if (h < s_rep.g.Vh) update_item<T, EFT>(it.y >> 1, s_rep, a.links, h, it.y & 1, t);
+    if (h < s_rep.g.Vh) update_item<T, EFT, REPEAT>(it.y >> 1, s_rep, a.links, h, it.y & 1, t, a.max_tries);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -167,12 +169,23 @@ __global__ void __launch_bounds__(SU3_BATCH_LB_THREADS, std::is_same<T, float>::
 }
 
 cudaError_t launch_batch(const BatchArgs& a, int precision, int blocks, int threads, cudaStream_t s) {
-  if (precision == SU3_FP64)
-    k_batch_sweep<double, false><<<blocks, threads, 0, s>>>(a);
-  else if (precision == SU3_FP32_EFT)
-    k_batch_sweep<float, true><<<blocks, threads, 0, s>>>(a);
-  else
-    k_batch_sweep<float, false><<<blocks, threads, 0, s>>>(a);
+  const bool rep = a.max_tries > 1;
+  if (precision == SU3_FP64) {
+    if (rep)
+      k_batch_sweep<double, false, true><<<blocks, threads, 0, s>>>(a);
+    else
+      k_batch_sweep<double, false, false><<<blocks, threads, 0, s>>>(a);
+  } else if (precision == SU3_FP32_EFT) {
+    if (rep)
+      k_batch_sweep<float, true, true><<<blocks, threads, 0, s>>>(a);
+    else
+      k_batch_sweep<float, true, false><<<blocks, threads, 0, s>>>(a);
+  } else {
+    if (rep)
+      k_batch_sweep<float, false, true><<<blocks, threads, 0, s>>>(a);
+    else
+      k_batch_sweep<float, false, false><<<blocks, threads, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -180,10 +193,10 @@ int max_blocks_per_sm(int precision, int threads) {
   int n = 0;
   cudaError_t e =
       precision == SU3_FP64
-          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<double, false>, threads, 0)
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<double, false, false>, threads, 0)
           : precision == SU3_FP32_EFT
-                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<float, true>, threads, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<float, false>, threads, 0);
+                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<float, true, false>, threads, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<float, false, false>, threads, 0);
   return e == cudaSuccess ? n : 0;
 }
 
@@ -216,6 +229,13 @@ struct su3_batch {
   int withhold_item = -1;
   std::string tune_key;
 };
+
+void su3_batch_invalidate(su3_batch* b) {
+  if (b && b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
 
 void su3_batch_release(su3_batch* b) {
   if (!b) return;
@@ -301,6 +321,7 @@ int enqueue_batch_sweep(su3_lattice* h, int blocks) {
   a.links = h->links;
   a.wait_ns = b->wait_ns;
   a.withhold_item = b->withhold_item;
+  a.max_tries = h->max_tries;
   SU3_CUDA(launch_batch(a, h->precision, blocks, b->threads, h->stream), "batch sweep launch");
   SU3_CUDA(su3k_launch_increment(h->d_sweep, 1, h->stream), "sweep counter launch");
   return SU3_OK;

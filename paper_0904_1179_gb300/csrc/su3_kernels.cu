@@ -32,39 +32,37 @@ namespace {
 // Single-lattice half-sweeps: one thread per link of (mu, parity).
 // ---------------------------------------------------------------------------
 template <bool STATS>
-__device__ __forceinline__ void count_stats(int accepted, bool active, unsigned long long* stats) {
+__device__ __forceinline__ void count_stats(UpdateCount c, unsigned long long* stats) {
   if (STATS) {
-    const unsigned m = __ballot_sync(0xffffffffu, active);
-    const int acc = __reduce_add_sync(0xffffffffu, accepted);
+    const int acc = __reduce_add_sync(0xffffffffu, c.accepted);
+    const int prop = __reduce_add_sync(0xffffffffu, c.proposed);
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(&stats[0], (unsigned long long)acc);
-      atomicAdd(&stats[1], 3ull * (unsigned long long)__popc(m));
+      atomicAdd(&stats[1], (unsigned long long)prop);
     }
   }
 }
 
-template <int MU, bool STATS>
+template <int MU, bool STATS, bool REPEAT>
 __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64(HalfSweepArgs args) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = h < args.geom.Vh;
-  int accepted = 0;
-  if (active) {
-    const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15};
-    accepted = update_link_f64<MU, false>(args.geom, (double2*)args.links, h, args.parity, *args.sweep, args.key, uc);
+  UpdateCount c{0, 0};
+  if (h < args.geom.Vh) {
+    const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15, args.max_tries};
+    c = update_link_f64<MU, false, REPEAT>(args.geom, (double2*)args.links, h, args.parity, *args.sweep, args.key, uc);
   }
-  count_stats<STATS>(accepted, active, args.stats);
+  count_stats<STATS>(c, args.stats);
 }
 
-template <int MU, bool STATS, bool EFT>
+template <int MU, bool STATS, bool EFT, bool REPEAT>
 __global__ void __launch_bounds__(SU3_F32_LB_THREADS, SU3_F32_MINBLOCKS) k_half_sweep_f32(HalfSweepArgs args) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = h < args.geom.Vh;
-  int accepted = 0;
-  if (active) {
-    const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15};
-    accepted = update_link_f32<MU, false, EFT>(args.geom, (float4*)args.links, h, args.parity, *args.sweep, args.key, uc);
+  UpdateCount c{0, 0};
+  if (h < args.geom.Vh) {
+    const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15, args.max_tries};
+    c = update_link_f32<MU, false, EFT, REPEAT>(args.geom, (float4*)args.links, h, args.parity, *args.sweep, args.key, uc);
   }
-  count_stats<STATS>(accepted, active, args.stats);
+  count_stats<STATS>(c, args.stats);
 }
 
 __global__ void k_increment(uint64_t* counter, uint64_t n) { *counter += n; }
@@ -318,25 +316,31 @@ __global__ void k_store_to_canon(ConvArgs args) {
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
-template <int MU, bool STATS, bool EFT>
+template <int MU, bool STATS, bool EFT, bool REPEAT>
 static cudaError_t launch_f32(const HalfSweepArgs& a, int blocks, int threads, cudaStream_t s) {
-  k_half_sweep_f32<MU, STATS, EFT><<<blocks, threads, 0, s>>>(a);
+  k_half_sweep_f32<MU, STATS, EFT, REPEAT><<<blocks, threads, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int MU, bool STATS, bool REPEAT>
+static cudaError_t launch_prec(const HalfSweepArgs& a, int precision, int blocks, int threads, cudaStream_t s) {
+  if (precision == 0) {
+    k_half_sweep_f64<MU, STATS, REPEAT><<<blocks, threads, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  if (precision == 2) return launch_f32<MU, STATS, true, REPEAT>(a, blocks, threads, s);
+  return launch_f32<MU, STATS, false, REPEAT>(a, blocks, threads, s);
 }
 
 template <int MU>
 static cudaError_t launch_half_sweep_mu(const HalfSweepArgs& a, int precision, bool stats, int threads, cudaStream_t s) {
   const int blocks = (a.geom.Vh + threads - 1) / threads;
-  if (precision == 0) {
-    if (stats)
-      k_half_sweep_f64<MU, true><<<blocks, threads, 0, s>>>(a);
-    else
-      k_half_sweep_f64<MU, false><<<blocks, threads, 0, s>>>(a);
-    return cudaGetLastError();
-  }
-  if (precision == 2)
-    return stats ? launch_f32<MU, true, true>(a, blocks, threads, s) : launch_f32<MU, false, true>(a, blocks, threads, s);
-  return stats ? launch_f32<MU, true, false>(a, blocks, threads, s) : launch_f32<MU, false, false>(a, blocks, threads, s);
+  const bool repeat = a.max_tries > 1;
+  if (stats)
+    return repeat ? launch_prec<MU, true, true>(a, precision, blocks, threads, s)
+                  : launch_prec<MU, true, false>(a, precision, blocks, threads, s);
+  return repeat ? launch_prec<MU, false, true>(a, precision, blocks, threads, s)
+                : launch_prec<MU, false, false>(a, precision, blocks, threads, s);
 }
 
 cudaError_t su3k_launch_half_sweep(const HalfSweepArgs& a, int mu, int precision, bool stats, int threads, cudaStream_t s) {

@@ -17,6 +17,7 @@ struct HalfSweepArgs {
   double beta;        // FP64 path
   double inv_beta15_f64;  // FP64 path: 1.5 / beta
   float inv_beta15;   // FP32 path: 1.5 / beta, so that 1/alpha = inv_beta15 / k
+  int max_tries;      // SU(2) proposals per subgroup: 1 = one-hit heatbath
   const uint64_t* sweep;  // device sweep counter (RNG position)
   void* links;
   unsigned long long* stats;  // [accepted, proposed], used when counting

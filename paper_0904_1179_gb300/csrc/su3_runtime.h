@@ -40,6 +40,7 @@ struct su3_lattice {
   cudaEvent_t ev_conv[2] = {nullptr, nullptr};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // indexed by stats_on
   int threads = kSu3DefaultThreads;
+  int max_tries = 1;  // SU(2) proposals per subgroup (1: one-hit heatbath)
   su3dev::Geometry geom{};
   su3dev::PhiloxKey key{};
   su3_batch* batch = nullptr;  // non-null for a batch of replicas
@@ -58,6 +59,11 @@ int su3_transfer(su3_lattice* h, const su3dev::Geometry& g, void* links, double*
 void su3_release_handle(su3_lattice* h);
 // Free the batch part of a handle (defined in su3_batch.cu).
 void su3_batch_release(su3_batch* b);
+// Drop the batch's captured sweep graph (its parameters changed).
+void su3_batch_invalidate(su3_batch* b);
+// Largest number of SU(2) proposals per subgroup (the try index has 26 bits
+// in the Philox counter).
+constexpr int kMaxHeatbathTries = 1 << 20;
 
 #define SU3_CUDA(call, what)                               \
   do {                                                     \

@@ -140,16 +140,23 @@ __device__ __forceinline__ int subrow_j(int sub) { return sub == 0 ? 1 : 2; }
 struct UpdateConsts {
   double inv_beta15_f64;  // 1.5 / beta: 1/alpha = 3/(2 beta k) = inv_beta15 / k
   float inv_beta15;
+  int max_tries;  // 1: one-hit heatbath; > 1: repeat until accepted, at most this many proposals
+};
+
+// Accepted and drawn SU(2) proposals of one link update (a degenerate
+// subgroup counts as one proposal).
+struct UpdateCount {
+  int accepted, proposed;
 };
 
 // ---------------------------------------------------------------------------
 // One FP64 link update: staple, three one-hit SU(2) heatbath steps, FP64
 // Gram-Schmidt, store.  Returns the number of accepted SU(2) proposals.
 // ---------------------------------------------------------------------------
-template <int MU, bool CG, typename KEY>
-__device__ __forceinline__ int update_link_f64(const Geometry& g, double2* U, int h, int p, uint64_t t, const KEY& key,
-                                               const UpdateConsts& uc) {
-  int accepted = 0;
+template <int MU, bool CG, bool REPEAT, typename KEY>
+__device__ __forceinline__ UpdateCount update_link_f64(const Geometry& g, double2* U, int h, int p, uint64_t t,
+                                                       const KEY& key, const UpdateConsts& uc) {
+  UpdateCount cnt{0, 0};
   const Site st = site_of(g, h, p);
   const uint32_t s = (uint32_t)canon(g, st);
   const mat3<double> A = staple<double, MU, CG>(g, U, st, h, p);
@@ -160,31 +167,40 @@ __device__ __forceinline__ int update_link_f64(const Geometry& g, double2* U, in
     double r[4];
     su2_projection(u, A, i, j, r);
     const double kk = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
-    double uu[6];
-#pragma unroll
-    for (int call = 0; call < 3; ++call) {
-      const uint4 w = philox4x32_10(rng_counter(s, (uint32_t)(MU | (sub << 2) | (call << 4)), t, kTagUpdate), key);
-      uu[2 * call] = u01_f64(w.x, w.y);
-      uu[2 * call + 1] = u01_f64(w.z, w.w);
+    if (!(kk > 0.0)) {  // k = 0: degenerate staple (measure zero), leave the subgroup
+      ++cnt.proposed;
+      continue;
     }
-    if (!(kk > 0.0)) continue;  // k = 0: degenerate staple (measure zero), leave the subgroup
     const double ik = rsqrt(kk);
     const double inv_alpha = uc.inv_beta15_f64 * ik;  // 1/alpha = 3 / (2 beta k)
-    const double c = cospi(2.0 * uu[1]);  // cos(2 pi u1)
-    const double delta = -(log(uu[0]) + c * c * log(uu[2])) * inv_alpha;
-    if (uu[3] * uu[3] > 1.0 - 0.5 * delta) continue;
-    const double a0 = 1.0 - delta;
-    double rho = 1.0 - a0 * a0;
-    rho = rho > 0.0 ? sqrt(rho) : 0.0;
-    const double ct = 1.0 - 2.0 * uu[4];
-    double sn = 1.0 - ct * ct;
-    sn = sn > 0.0 ? sqrt(sn) : 0.0;
-    double sphi, cphi;
-    sincospi(2.0 * uu[5], &sphi, &cphi);  // angle 2 pi u5
-    const double a[4] = {a0, rho * sn * cphi, rho * sn * sphi, rho * ct};
-    const double v[4] = {r[0] * ik, r[1] * ik, r[2] * ik, r[3] * ik};
-    apply_su2(u, i, j, a, v);
-    ++accepted;
+    const int ntries = REPEAT ? uc.max_tries : 1;
+    for (int tr = 0; tr < ntries; ++tr) {
+      double uu[6];
+#pragma unroll
+      for (int call = 0; call < 3; ++call) {
+        const uint32_t w1 = (uint32_t)(MU | (sub << 2) | (call << 4)) | ((uint32_t)tr << 6);
+        const uint4 w = philox4x32_10(rng_counter(s, w1, t, kTagUpdate), key);
+        uu[2 * call] = u01_f64(w.x, w.y);
+        uu[2 * call + 1] = u01_f64(w.z, w.w);
+      }
+      ++cnt.proposed;
+      const double c = cospi(2.0 * uu[1]);  // cos(2 pi u1)
+      const double delta = -(log(uu[0]) + c * c * log(uu[2])) * inv_alpha;
+      if (uu[3] * uu[3] > 1.0 - 0.5 * delta) continue;
+      const double a0 = 1.0 - delta;
+      double rho = 1.0 - a0 * a0;
+      rho = rho > 0.0 ? sqrt(rho) : 0.0;
+      const double ct = 1.0 - 2.0 * uu[4];
+      double sn = 1.0 - ct * ct;
+      sn = sn > 0.0 ? sqrt(sn) : 0.0;
+      double sphi, cphi;
+      sincospi(2.0 * uu[5], &sphi, &cphi);  // angle 2 pi u5
+      const double a[4] = {a0, rho * sn * cphi, rho * sn * sphi, rho * ct};
+      const double v[4] = {r[0] * ik, r[1] * ik, r[2] * ik, r[3] * ik};
+      apply_su2(u, i, j, a, v);
+      ++cnt.accepted;
+      break;
+    }
   }
   cx<double> r0[3] = {u.e[0][0], u.e[0][1], u.e[0][2]};
   cx<double> r1[3] = {u.e[1][0], u.e[1][1], u.e[1][2]};
@@ -197,7 +213,7 @@ __device__ __forceinline__ int update_link_f64(const Geometry& g, double2* U, in
   }
   complete_row2(out);
   store_f64(U, MU, p, h, g.Vh, out);
-  return accepted;
+  return cnt;
 }
 
 // ---------------------------------------------------------------------------
@@ -250,12 +266,13 @@ __device__ __forceinline__ pm3 staple_p(const Geometry& g, const float4* U, cons
 // ---------------------------------------------------------------------------
 // One FP32-mixed link update: FP32 storage (rows 0,1), FP32 staple and
 // heatbath, Gram-Schmidt coefficients in FP64 (EFT = false) or as
-// compensated FP32 sums of FP64-class accuracy (EFT = true).
+// compensated FP32 sums of FP64-class accuracy (EFT = true).  REPEAT = false
+// compiles the one-hit heatbath without the retry loop.
 // ---------------------------------------------------------------------------
-template <int MU, bool CG, bool EFT, typename KEY>
-__device__ __forceinline__ int update_link_f32(const Geometry& g, float4* U, int h, int p, uint64_t t, const KEY& key,
-                                               const UpdateConsts& uc) {
-  int accepted = 0;
+template <int MU, bool CG, bool EFT, bool REPEAT, typename KEY>
+__device__ __forceinline__ UpdateCount update_link_f32(const Geometry& g, float4* U, int h, int p, uint64_t t,
+                                                       const KEY& key, const UpdateConsts& uc) {
+  UpdateCount cnt{0, 0};
   const Site st = site_of(g, h, p);
   const uint32_t s = (uint32_t)canon(g, st);
   const pm3 A = staple_p<MU, CG>(g, U, st, h, p);
@@ -304,24 +321,39 @@ __device__ __forceinline__ int update_link_f32(const Geometry& g, float4* U, int
     const float r[4] = {0.5f * (wii.re + wjj.re), 0.5f * (wij.im + wji.im), 0.5f * (wij.re - wji.re),
                         0.5f * (wii.im - wjj.im)};
     const float kk = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
-    const uint4 w0 = philox4x32_10(rng_counter(s, (uint32_t)(MU | (sub << 2)), t, kTagUpdate), key);
-    const uint4 w1 = philox4x32_10(rng_counter(s, (uint32_t)(MU | (sub << 2) | (1 << 4)), t, kTagUpdate), key);
-    if (!(kk > 1e-30f)) continue;  // degenerate staple (measure zero): leave the subgroup
+    if (!(kk > 1e-30f)) {  // degenerate staple (measure zero): leave the subgroup
+      ++cnt.proposed;
+      continue;
+    }
     const float ik = rsqrtf(kk);
     const float ia = inv_beta15 * ik;  // 1/alpha = 3 / (2 beta k)
-    const float u0 = u01_f32(w0.x), u1 = u01_f32(w0.y), u2 = u01_f32(w0.z), u3 = u01_f32(w0.w);
-    const float cc = __cosf(fmaf(6.2831853f, u1, -3.14159265f));  // -cos(2 pi u1); only its square is used
-    const float delta = -(__logf(u0) + cc * cc * __logf(u2)) * ia;
-    if (u3 * u3 > 1.0f - 0.5f * delta) continue;
-    const float u4 = u01_f32(w1.x), u5 = u01_f32(w1.y);
-    const float a0 = 1.0f - delta;
-    const float rho = sqrtf(fmaxf(0.0f, delta * (2.0f - delta)));  // sqrt(1 - a0^2)
-    const float ct = 1.0f - 2.0f * u4;
-    const float sn = 2.0f * sqrtf(u4 * (1.0f - u4));  // sqrt(1 - ct^2)
-    float sphi, cphi;
-    __sincosf(fmaf(6.2831853f, u5, -3.14159265f), &sphi, &cphi);  // angle 2 pi u5 - pi
-    const float rs = -rho * sn;                                     // undo the shift by pi
-    const float a[4] = {a0, rs * cphi, rs * sphi, rho * ct};
+    bool acc = false;
+    float a[4];
+    const int ntries = REPEAT ? uc.max_tries : 1;
+    for (int tr = 0; tr < ntries; ++tr) {
+      const uint32_t w1b = (uint32_t)(MU | (sub << 2)) | ((uint32_t)tr << 6);
+      const uint4 w0 = philox4x32_10(rng_counter(s, w1b, t, kTagUpdate), key);
+      const uint4 w1 = philox4x32_10(rng_counter(s, w1b | (1u << 4), t, kTagUpdate), key);
+      ++cnt.proposed;
+      const float u0 = u01_f32(w0.x), u1 = u01_f32(w0.y), u2 = u01_f32(w0.z), u3 = u01_f32(w0.w);
+      const float cc = __cosf(fmaf(6.2831853f, u1, -3.14159265f));  // -cos(2 pi u1); only its square is used
+      const float delta = -(__logf(u0) + cc * cc * __logf(u2)) * ia;
+      if (u3 * u3 > 1.0f - 0.5f * delta) continue;
+      const float u4 = u01_f32(w1.x), u5 = u01_f32(w1.y);
+      const float rho = sqrtf(fmaxf(0.0f, delta * (2.0f - delta)));  // sqrt(1 - a0^2)
+      const float ct = 1.0f - 2.0f * u4;
+      const float sn = 2.0f * sqrtf(u4 * (1.0f - u4));  // sqrt(1 - ct^2)
+      float sphi, cphi;
+      __sincosf(fmaf(6.2831853f, u5, -3.14159265f), &sphi, &cphi);  // angle 2 pi u5 - pi
+      const float rs = -rho * sn;                                     // undo the shift by pi
+      a[0] = 1.0f - delta;
+      a[1] = rs * cphi;
+      a[2] = rs * sphi;
+      a[3] = rho * ct;
+      acc = true;
+      break;
+    }
+    if (!acc) continue;
     const float v[4] = {r[0] * ik, r[1] * ik, r[2] * ik, r[3] * ik};
     // R = Y V^+ with Y = m(a), V = m(v), m(q) = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]]
     const cx<float> y00 = mk(a[0], a[3]), y01 = mk(a[2], a[1]);
@@ -340,7 +372,7 @@ __device__ __forceinline__ int update_link_f32(const Geometry& g, float4* U, int
         pset(u, j, c, mac(mul(R10, ui), R11, uj));
       }
     }
-    ++accepted;
+    ++cnt.accepted;
   }
   cx<float> r0[3], r1[3];
 #pragma unroll
@@ -351,7 +383,7 @@ __device__ __forceinline__ int update_link_f32(const Geometry& g, float4* U, int
   float o[12];
   reunitarise_f32<EFT>(r0, r1, o);
   store_f32_rows01(U, MU, p, h, g.Vh, o);
-  return accepted;
+  return cnt;
 }
 
 }  // namespace su3dev

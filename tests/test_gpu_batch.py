@@ -137,3 +137,14 @@ def test_single_calls_reject_batch_handles():
         out = np.empty(su3.links_shape(MIX[0]), dtype=np.float64)
         with pytest.raises(su3.Su3Error):
             su3.su3_batch_links_get(b.handle, 5, out)
+
+
+def test_batch_repeat_until_accepted_equals_single_lattices():
+    with su3.Batch(MIX, BETAS, SEEDS, start=su3.SU3_HOT, precision=su3.SU3_FP32_MIXED) as b:
+        b.set_heatbath(4)
+        b.sweep(2)
+        for r, L in enumerate(MIX):
+            with su3.Lattice(L, BETAS[r], SEEDS[r], start=su3.SU3_HOT, precision=su3.SU3_FP32_MIXED) as lat:
+                lat.set_heatbath(4)
+                lat.sweep(2)
+                assert np.array_equal(b.get_links(r), lat.get_links()), r

@@ -439,3 +439,63 @@ def test_philox_matches_curand():
             assert oracle.philox4x32_10(r[0:4], r[4:6]) == r[6:10]
     finally:
         shutil.rmtree(d)
+
+
+# ---------------------------------------------------------------------------
+# repeat-until-accepted heatbath (max_tries > 1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (6, 4, 10, 8)])
+def test_fp64_repeat_until_accepted_matches_oracle(L):
+    seed, tries = 41, 8
+    U0 = oracle.hot_start(L, 12)
+    for mu, p in ((0, 0), (3, 1)):
+        with su3.Lattice(L, BETA, seed, start=su3.SU3_COLD) as lat:
+            lat.set_heatbath(tries)
+            lat.set_links(U0)
+            lat.sweep_count = 2
+            lat.set_stats(True)
+            lat.half_sweep(mu, p)
+            G = lat.get_links()
+            gstats = lat.stats()
+        O = U0.copy()
+        ostats = oracle.half_sweep(L, BETA, seed, 2, mu, p, O, max_tries=tries)
+        assert np.abs(G - O).max() < F64_TOL
+        assert gstats == ostats and ostats[1] > ostats[0]
+    # a full sweep
+    O = U0.copy()
+    ostats, _ = oracle.sweep(L, BETA, seed, 0, 1, O, max_tries=tries)
+    with su3.Lattice(L, BETA, seed, start=su3.SU3_COLD) as lat:
+        lat.set_heatbath(tries)
+        lat.set_links(U0)
+        lat.set_stats(True)
+        lat.sweep(1)
+        assert np.abs(lat.get_links() - O).max() < F64_TOL
+        assert lat.stats() == ostats
+
+
+@pytest.mark.parametrize("prec", [su3.SU3_FP32_MIXED, su3.SU3_FP32_EFT])
+def test_fp32_repeat_until_accepted_matches_oracle_reading(prec):
+    L = (8, 8, 8, 8)
+    seed, t, tries = 43, 3, 8
+    U0 = oracle.hot_start(L, 9, f32=True)
+    with su3.Lattice(L, BETA, seed, start=su3.SU3_COLD, precision=prec) as lat:
+        lat.set_heatbath(tries)
+        for mu, p in ((1, 0), (2, 1)):
+            lat.set_links(U0)
+            lat.sweep_count = t
+            lat.half_sweep(mu, p)
+            G = flat_links(lat.get_links())
+            sites = site_list(L, p)
+            O, marg = oracle.updated_links(L, BETA, seed, t, mu, sites, U0, f32=True, with_margins=True,
+                                           max_tries=tries)
+            d = np.abs(G[sites, mu] - O).max(axis=(1, 2, 3))
+            assert (d > F32_TOL).sum() <= 2, d.max()
+
+
+def test_heatbath_setting_validated():
+    with su3.Lattice((4, 4, 4, 4), BETA, 1, start=su3.SU3_COLD) as lat:
+        for bad in (0, -3, (1 << 20) + 1):
+            with pytest.raises(su3.Su3Error):
+                lat.set_heatbath(bad)
+        lat.set_heatbath(1)

@@ -394,3 +394,71 @@ def test_one_hit_acceptance_near_paper_value():
     (acc, prop), _ = oracle.sweep(L, 5.7, 61, 60, 20, U)
     rate = acc / prop
     assert 0.95 < rate < 0.99, rate
+
+
+# --------------------------------------------------------------------------
+# repeat-until-accepted heatbath (the non-MPI program's sampler, Sec. 2.1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("alpha", [0.5, 8.0])
+def test_kp_repeat_until_accepted(alpha):
+    # every draw accepted; a0 still follows sqrt(1-a0^2) e^{alpha a0}; the
+    # number of proposals is geometric with mean 1/p_acc
+    from scipy import stats
+    n = 400_000
+    q, acc, tries = oracle.kp_draws(alpha, 99, n, max_tries=64, with_tries=True)
+    assert acc.all()
+    a0 = q[:, 0]
+    lo = -1.0 if alpha < 4 else max(-1.0, 1.0 - 12.0 / alpha)
+    edges = np.linspace(lo, 1.0, 31)
+    edges[0] = -1.0
+    probs = kp_target_bin_probs(alpha, edges)
+    counts, _ = np.histogram(a0, bins=edges)
+    keep = probs * n > 20
+    chi2 = (((counts - probs * n) ** 2) / (probs * n))[keep].sum()
+    assert stats.chi2.sf(chi2, keep.sum() - 1) > 1e-4, chi2
+    p = kp_acceptance_exact(alpha)
+    mean_tries = tries / n
+    sd = math.sqrt((1 - p) / p ** 2 / n)
+    assert abs(mean_tries - 1 / p) < 5 * sd, (mean_tries, 1 / p)
+
+
+def test_single_link_equilibrium_repeat_until_accepted():
+    L = (4, 4, 4, 4)
+    beta = 2.0
+    U = oracle.hot_start(L, 31)
+    x = (1, 2, 0, 3)
+    mu = 1
+    s = site_index(L, x)
+    A = cplx(oracle.staple(L, U, s, mu))
+    n = 20000
+    f = np.empty(n)
+    prop = acc = 0
+    for t in range(n):
+        acc_t, prop_t = oracle.update_links(L, beta, 78, t, mu, [s], U, max_tries=64)
+        acc += acc_t
+        prop += prop_t
+        u = cplx(U[x[3], x[2], x[1], x[0], mu])
+        f[t] = np.real(np.trace(u @ A)) / 3.0
+    bins = f.reshape(40, -1).mean(axis=1)
+    chain, chain_err = bins.mean(), bins.std(ddof=1) / math.sqrt(40)
+    rng = np.random.default_rng(6)
+    H = haar_su3_numpy(rng, 2_000_000)
+    g = np.real(np.einsum("nij,ji->n", H, A)) / 3.0
+    w = np.exp(beta * (g - g.max()))
+    exact = (g * w).sum() / w.sum()
+    exact_err = math.sqrt((((g - exact) * w) ** 2).sum()) / w.sum()
+    assert abs(chain - exact) < 4.5 * math.hypot(chain_err, exact_err), (chain, chain_err, exact, exact_err)
+    assert acc >= 0.9999 * 3 * n and prop > 3 * n  # nearly every subgroup accepted, after redraws
+
+
+def test_one_try_is_the_one_hit_heatbath():
+    L = (4, 4, 4, 4)
+    a = oracle.hot_start(L, 3)
+    b = a.copy()
+    sa = oracle.sweep(L, 5.7, 17, 0, 2, a)
+    sb = oracle.sweep(L, 5.7, 17, 0, 2, b, max_tries=1)
+    assert np.array_equal(a, b) and sa[0] == sb[0]
+    c = a.copy()
+    (acc, prop), _ = oracle.sweep(L, 5.7, 17, 2, 2, c, max_tries=8)
+    assert acc == 2 * 4 * 256 * 3 and prop > acc  # every subgroup accepted, after some retries
