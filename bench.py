@@ -294,6 +294,41 @@ def variant_fp32(su3, stream, steps, warmup, world, hbm_peak, peak_kind, precisi
                          "kernel_ms": kernel_ms}}
 
 
+def variant_measured(su3, stream, steps, warmup, precision):
+    """Sweeps that also measure the plaquette after every sweep: fused into the
+    update kernels (su3_sweep_measured) against a separate su3_plaquette pass
+    after each sweep; both timed with CUDA events on the lattice's stream."""
+    import numpy as np
+    import torch
+    V = int(np.prod(DIMS))
+    n = steps * SWEEPS_PER_STEP
+    out = {}
+    with su3.Lattice(DIMS, BETA, SEED, start=su3.SU3_HOT, precision=precision,
+                     stream=stream.cuda_stream) as lat:
+        lat.sweep_measured(warmup * SWEEPS_PER_STEP)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fused = lat.sweep_measured(n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["fused"] = {"value": 4 * V * n / (ms * 1e-3), "ms_per_sweep": ms / n}
+        e0.record(stream)
+        sep = []
+        for _ in range(n):
+            lat.sweep(1)
+            sep.append(lat.plaquette())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["separate"] = {"value": 4 * V * n / (ms * 1e-3), "ms_per_sweep": ms / n}
+    out.update({"unit": UNIT, "plaquettes_fused_last": float(fused[-1]), "plaquettes_separate_last": sep[-1],
+                "workload": "32^4 beta=5.7 hot start seed 7, %s, plaquette after every sweep"
+                            % ("FP64" if precision == su3.SU3_FP64 else "FP32-mixed")})
+    return out
+
+
 def run_profile_case(case):
     import paper_0904_1179_gb300 as su3
     if case == "batched":
@@ -495,6 +530,8 @@ def main():
         variants["fp32_eft"] = variant_fp32(su3, stream, args.steps, args.warmup, 1, hbm_peak, peak_kind,
                                             su3.SU3_FP32_EFT)
         variants["batched"] = variant_batched(su3, stream, args.steps, args.warmup, hbm_peak, peak_kind)
+        variants["measured_fp64"] = variant_measured(su3, stream, args.steps, args.warmup, su3.SU3_FP64)
+        variants["measured_fp32_mixed"] = variant_measured(su3, stream, args.steps, args.warmup, su3.SU3_FP32_MIXED)
     e2e = time_e2e(su3, DIMS, su3.SU3_FP64, max(3, args.steps // 4), 3, SWEEPS_PER_STEP)
     cpu = None if args.no_cpu_baseline else cpu_baseline_sample(False)
     line = {

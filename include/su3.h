@@ -111,6 +111,19 @@ SU3_API int su3_destroy(su3_handle h);
  * half-sweep kernels followed by the sweep-counter increment. */
 SU3_API int su3_sweep(su3_handle h, int nsweeps);
 
+/* nsweeps sweeps like su3_sweep, with the mean plaquette after each sweep
+ * written to plaq_out[0..nsweeps-1] (the paper leaves measurement routines to
+ * the user and asks to evaluate their cost, Sec. 2.2).  The plaquette is fused
+ * into the sweep: after the update of U_mu(x) in the odd-site half-sweeps of
+ * mu = 1, 2, 3, Re Tr(U_mu(x)_new A_<) -- A_< the staple terms of the
+ * directions nu < mu, all already final -- is the sum of the plaquettes of
+ * the planes (mu, nu < mu) at x and x - nu-hat; over the three half-sweeps
+ * every plaquette of the new configuration is counted once, with no extra
+ * pass over the links.  Sums in FP64, fixed-order reduction (reproducible;
+ * equal to su3_plaquette up to summation order).  Synchronises once per 4096
+ * sweeps.  Acceptance statistics must be off (SU3_EINVAL otherwise). */
+SU3_API int su3_sweep_measured(su3_handle h, int nsweeps, double* plaq_out);
+
 /* One checkerboard half-sweep: update every U_mu(x) with parity(x) == parity
  * at the current sweep index, without advancing it.  A full sweep equals the
  * eight calls mu = 0..3, parity 0 then 1, followed by

@@ -18,7 +18,7 @@ import numpy as np
 
 __all__ = [
     "SU3_COLD", "SU3_HOT", "SU3_FP64", "SU3_FP32_MIXED", "SU3_FP32_EFT", "Su3Error", "load_library", "library_path",
-    "su3_create", "su3_create_ex", "su3_destroy", "su3_sweep", "su3_half_sweep", "su3_plaquette",
+    "su3_create", "su3_create_ex", "su3_destroy", "su3_sweep", "su3_sweep_measured", "su3_half_sweep", "su3_plaquette",
     "su3_links_get", "su3_links_set", "su3_sweep_count", "su3_set_sweep_count", "su3_set_stats", "su3_stats",
     "su3_info", "su3_set_block_size", "su3_set_heatbath", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
     "su3_batch_links_get", "su3_batch_links_set", "su3_batch_size", "su3_batch_config", "su3_batch_get_config",
@@ -49,6 +49,7 @@ EXPORTS = [
                                                             ctypes.c_void_p, ctypes.POINTER(_h)]),
     ("su3_destroy", ctypes.c_int, [_h]),
     ("su3_sweep", ctypes.c_int, [_h, ctypes.c_int]),
+    ("su3_sweep_measured", ctypes.c_int, [_h, ctypes.c_int, _pd]),
     ("su3_half_sweep", ctypes.c_int, [_h, ctypes.c_int, ctypes.c_int]),
     ("su3_plaquette", ctypes.c_double, [_h]),
     ("su3_links_get", ctypes.c_int, [_h, _pd, ctypes.c_size_t]),
@@ -140,6 +141,13 @@ def su3_destroy(h):
 
 def su3_sweep(h, nsweeps):
     _check(load_library().su3_sweep(h, nsweeps))
+
+
+def su3_sweep_measured(h, nsweeps):
+    """nsweeps sweeps with the fused plaquette; returns the plaquette after each sweep."""
+    out = np.empty(max(int(nsweeps), 0), dtype=np.float64)
+    _check(load_library().su3_sweep_measured(h, int(nsweeps), out.ctypes.data_as(_pd)))
+    return out
 
 
 def su3_half_sweep(h, mu, parity):
@@ -396,6 +404,9 @@ class Lattice:
 
     def sweep(self, n=1):
         su3_sweep(self.handle, n)
+
+    def sweep_measured(self, n):
+        return su3_sweep_measured(self.handle, n)
 
     def half_sweep(self, mu, parity):
         su3_half_sweep(self.handle, mu, parity)

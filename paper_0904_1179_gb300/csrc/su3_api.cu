@@ -63,6 +63,10 @@ void drop_graphs(su3_lattice* h) {
       cudaGraphExecDestroy(g);
       g = nullptr;
     }
+  if (h->graph_meas) {
+    cudaGraphExecDestroy(h->graph_meas);
+    h->graph_meas = nullptr;
+  }
 }
 
 void release(su3_lattice* h) {
@@ -77,6 +81,9 @@ void release(su3_lattice* h) {
   cudaFree(h->d_plaq);
   cudaFree(h->d_stage);
   cudaFree(h->d_stage2);
+  cudaFree(h->d_meas_parts);
+  cudaFree(h->d_meas);
+  cudaFreeHost(h->h_meas);
   for (int b = 0; b < 2; ++b) {
     if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);
     if (h->ev_conv[b]) cudaEventDestroy(h->ev_conv[b]);
@@ -90,6 +97,7 @@ void release(su3_lattice* h) {
 
 HalfSweepArgs half_sweep_args(const su3_lattice* h, int parity) {
   HalfSweepArgs a{};
+  a.meas = nullptr;
   a.geom = h->geom;
   a.key = su3dev::philox_round_keys(h->key);
   a.parity = parity;
@@ -103,21 +111,33 @@ HalfSweepArgs half_sweep_args(const su3_lattice* h, int parity) {
   return a;
 }
 
-int enqueue_sweep_body(su3_lattice* h) {
+// One sweep: mu = 0..3, even then odd sites, then the sweep counter.  With
+// `measured`, the odd-site phases of mu = 1, 2, 3 also leave block partials of
+// Re Tr(U_new A_<) (A_< = staple terms of nu < mu); together they hold every
+// plaquette of the updated configuration once, and a last kernel sums them
+// into the ring slot of this sweep.
+int enqueue_sweep_body(su3_lattice* h, bool measured) {
+  const int blocks = (h->geom.Vh + h->threads - 1) / h->threads;
   for (int mu = 0; mu < 4; ++mu)
-    for (int p = 0; p < 2; ++p)
-      SU3_CUDA(su3k_launch_half_sweep(half_sweep_args(h, p), mu, h->precision, h->stats_on, h->threads, h->stream),
-               "half-sweep launch");
+    for (int p = 0; p < 2; ++p) {
+      HalfSweepArgs a = half_sweep_args(h, p);
+      if (measured && p == 1 && mu >= 1) a.meas = h->d_meas_parts + (size_t)(mu - 1) * blocks;
+      SU3_CUDA(su3k_launch_half_sweep(a, mu, h->precision, h->stats_on, h->threads, h->stream), "half-sweep launch");
+    }
+  if (measured)
+    SU3_CUDA(su3k_launch_meas_final(h->d_meas_parts, 3 * blocks, 1.0 / (6.0 * (double)h->V), h->d_sweep, h->d_meas,
+                                    h->meas_cap, h->stream),
+             "plaquette reduction launch");
   SU3_CUDA(su3k_launch_increment(h->d_sweep, 1, h->stream), "sweep counter launch");
   return SU3_OK;
 }
 
-int ensure_graph(su3_lattice* h) {
-  cudaGraphExec_t& exec = h->graph[h->stats_on ? 1 : 0];
+int ensure_graph(su3_lattice* h, bool measured = false) {
+  cudaGraphExec_t& exec = measured ? h->graph_meas : h->graph[h->stats_on ? 1 : 0];
   if (exec) return SU3_OK;
   cudaGraph_t graph = nullptr;
   SU3_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
-  const int rc = enqueue_sweep_body(h);
+  const int rc = enqueue_sweep_body(h, measured);
   const cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
   if (rc != SU3_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -300,6 +320,47 @@ int su3_sweep(su3_handle h, int nsweeps) {
   cudaGraphExec_t exec = h->graph[h->stats_on ? 1 : 0];
   for (int n = 0; n < nsweeps; ++n) SU3_CUDA(cudaGraphLaunch(exec, h->stream), "su3_sweep: graph launch");
   h->sweep_host += (uint64_t)nsweeps;
+  return SU3_OK;
+}
+
+int su3_sweep_measured(su3_handle h, int nsweeps, double* plaq_out) {
+  if (!h) return fail(SU3_EINVAL, "su3_sweep_measured: NULL handle");
+  if (is_batch(h)) return fail(SU3_EINVAL, "su3_sweep_measured: batch handle (use su3_batch_plaquettes)");
+  if (nsweeps < 0 || (nsweeps > 0 && !plaq_out)) return fail(SU3_EINVAL, "su3_sweep_measured: bad nsweeps or NULL out");
+  if (h->stats_on) return fail(SU3_EINVAL, "su3_sweep_measured: disable acceptance statistics first");
+  if (nsweeps == 0) return SU3_OK;
+  const int blocks = (h->geom.Vh + h->threads - 1) / h->threads;
+  if (h->meas_blocks != blocks || !h->d_meas) {
+    SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_sweep_measured");
+    if (h->graph_meas) {
+      cudaGraphExecDestroy(h->graph_meas);
+      h->graph_meas = nullptr;
+    }
+    cudaFree(h->d_meas_parts);
+    h->d_meas_parts = nullptr;
+    SU3_CUDA(cudaMalloc(&h->d_meas_parts, (size_t)3 * blocks * sizeof(double)), "su3_sweep_measured: partials");
+    h->meas_blocks = blocks;
+    if (!h->d_meas) {
+      h->meas_cap = 4096;
+      SU3_CUDA(cudaMalloc(&h->d_meas, (size_t)h->meas_cap * sizeof(double)), "su3_sweep_measured: ring");
+      SU3_CUDA(cudaMallocHost(&h->h_meas, (size_t)h->meas_cap * sizeof(double)), "su3_sweep_measured: ring");
+    }
+  }
+  int rc = ensure_graph(h, true);
+  if (rc != SU3_OK) return rc;
+  for (int done = 0; done < nsweeps;) {
+    const int n = (nsweeps - done) < h->meas_cap ? (nsweeps - done) : h->meas_cap;
+    const uint64_t t0 = h->sweep_host;
+    for (int i = 0; i < n; ++i) SU3_CUDA(cudaGraphLaunch(h->graph_meas, h->stream), "su3_sweep_measured: graph launch");
+    h->sweep_host += (uint64_t)n;
+    SU3_CUDA(cudaMemcpyAsync(h->h_meas, h->d_meas, (size_t)h->meas_cap * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream),
+             "su3_sweep_measured: copy");
+    rc = sync(h, "su3_sweep_measured");
+    if (rc != SU3_OK) return rc;
+    for (int i = 0; i < n; ++i) plaq_out[done + i] = h->h_meas[(t0 + (uint64_t)i) % (uint64_t)h->meas_cap];
+    done += n;
+  }
   return SU3_OK;
 }
 

@@ -43,29 +43,67 @@ __device__ __forceinline__ void count_stats(UpdateCount c, unsigned long long* s
   }
 }
 
-template <int MU, bool STATS, bool REPEAT>
+// Block sum of one value per thread into out[blockIdx.x] (fixed order).
+__device__ __forceinline__ void block_partial(double v, double* out) {
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) out[blockIdx.x] = w;
+  }
+}
+
+template <int MU, bool STATS, bool REPEAT, bool MEAS>
 __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64(HalfSweepArgs args) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   UpdateCount c{0, 0};
+  double m = 0.0;
   if (h < args.geom.Vh) {
     const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15, args.max_tries};
-    c = update_link_f64<MU, false, REPEAT>(args.geom, (double2*)args.links, h, args.parity, *args.sweep, args.key, uc);
+    c = update_link_f64<MU, false, REPEAT, MEAS>(args.geom, (double2*)args.links, h, args.parity, *args.sweep, args.key,
+                                                 uc, &m);
   }
   count_stats<STATS>(c, args.stats);
+  if (MEAS) block_partial(m, args.meas);
 }
 
-template <int MU, bool STATS, bool EFT, bool REPEAT>
+template <int MU, bool STATS, bool EFT, bool REPEAT, bool MEAS>
 __global__ void __launch_bounds__(SU3_F32_LB_THREADS, SU3_F32_MINBLOCKS) k_half_sweep_f32(HalfSweepArgs args) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   UpdateCount c{0, 0};
+  double m = 0.0;
   if (h < args.geom.Vh) {
     const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15, args.max_tries};
-    c = update_link_f32<MU, false, EFT, REPEAT>(args.geom, (float4*)args.links, h, args.parity, *args.sweep, args.key, uc);
+    c = update_link_f32<MU, false, EFT, REPEAT, MEAS>(args.geom, (float4*)args.links, h, args.parity, *args.sweep,
+                                                      args.key, uc, &m);
   }
   count_stats<STATS>(c, args.stats);
+  if (MEAS) block_partial(m, args.meas);
 }
 
 __global__ void k_increment(uint64_t* counter, uint64_t n) { *counter += n; }
+
+__global__ void __launch_bounds__(1024) k_meas_final(const double* parts, int n, double scale, const uint64_t* sweep,
+                                                     double* out, int cap) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += parts[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) out[*sweep % (uint64_t)cap] = w * scale;
+  }
+}
 __global__ void k_set_counter(uint64_t* counter, uint64_t n) { *counter = n; }
 
 // ---------------------------------------------------------------------------
@@ -316,31 +354,35 @@ __global__ void k_store_to_canon(ConvArgs args) {
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
-template <int MU, bool STATS, bool EFT, bool REPEAT>
+template <int MU, bool STATS, bool EFT, bool REPEAT, bool MEAS>
 static cudaError_t launch_f32(const HalfSweepArgs& a, int blocks, int threads, cudaStream_t s) {
-  k_half_sweep_f32<MU, STATS, EFT, REPEAT><<<blocks, threads, 0, s>>>(a);
+  k_half_sweep_f32<MU, STATS, EFT, REPEAT, MEAS><<<blocks, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int MU, bool STATS, bool REPEAT>
+template <int MU, bool STATS, bool REPEAT, bool MEAS>
 static cudaError_t launch_prec(const HalfSweepArgs& a, int precision, int blocks, int threads, cudaStream_t s) {
   if (precision == 0) {
-    k_half_sweep_f64<MU, STATS, REPEAT><<<blocks, threads, 0, s>>>(a);
+    k_half_sweep_f64<MU, STATS, REPEAT, MEAS><<<blocks, threads, 0, s>>>(a);
     return cudaGetLastError();
   }
-  if (precision == 2) return launch_f32<MU, STATS, true, REPEAT>(a, blocks, threads, s);
-  return launch_f32<MU, STATS, false, REPEAT>(a, blocks, threads, s);
+  if (precision == 2) return launch_f32<MU, STATS, true, REPEAT, MEAS>(a, blocks, threads, s);
+  return launch_f32<MU, STATS, false, REPEAT, MEAS>(a, blocks, threads, s);
 }
 
 template <int MU>
 static cudaError_t launch_half_sweep_mu(const HalfSweepArgs& a, int precision, bool stats, int threads, cudaStream_t s) {
   const int blocks = (a.geom.Vh + threads - 1) / threads;
   const bool repeat = a.max_tries > 1;
+  if (MU > 0 && a.meas) {  // fused plaquette (statistics are not counted in these phases)
+    return repeat ? launch_prec<MU, false, true, (MU > 0)>(a, precision, blocks, threads, s)
+                  : launch_prec<MU, false, false, (MU > 0)>(a, precision, blocks, threads, s);
+  }
   if (stats)
-    return repeat ? launch_prec<MU, true, true>(a, precision, blocks, threads, s)
-                  : launch_prec<MU, true, false>(a, precision, blocks, threads, s);
-  return repeat ? launch_prec<MU, false, true>(a, precision, blocks, threads, s)
-                : launch_prec<MU, false, false>(a, precision, blocks, threads, s);
+    return repeat ? launch_prec<MU, true, true, false>(a, precision, blocks, threads, s)
+                  : launch_prec<MU, true, false, false>(a, precision, blocks, threads, s);
+  return repeat ? launch_prec<MU, false, true, false>(a, precision, blocks, threads, s)
+                : launch_prec<MU, false, false, false>(a, precision, blocks, threads, s);
 }
 
 cudaError_t su3k_launch_half_sweep(const HalfSweepArgs& a, int mu, int precision, bool stats, int threads, cudaStream_t s) {
@@ -354,6 +396,12 @@ cudaError_t su3k_launch_half_sweep(const HalfSweepArgs& a, int mu, int precision
 
 cudaError_t su3k_launch_increment(uint64_t* counter, uint64_t n, cudaStream_t s) {
   k_increment<<<1, 1, 0, s>>>(counter, n);
+  return cudaGetLastError();
+}
+
+cudaError_t su3k_launch_meas_final(const double* parts, int nparts, double scale, const uint64_t* sweep, double* out,
+                                   int cap, cudaStream_t s) {
+  k_meas_final<<<1, 1024, 0, s>>>(parts, nparts, scale, sweep, out, cap);
   return cudaGetLastError();
 }
 

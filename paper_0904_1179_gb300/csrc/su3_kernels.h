@@ -21,6 +21,7 @@ struct HalfSweepArgs {
   const uint64_t* sweep;  // device sweep counter (RNG position)
   void* links;
   unsigned long long* stats;  // [accepted, proposed], used when counting
+  double* meas;               // fused plaquette: per-block partial sums of this phase (nullptr: off)
 };
 
 struct InitArgs {
@@ -46,6 +47,10 @@ struct ConvArgs {
 
 cudaError_t su3k_launch_half_sweep(const HalfSweepArgs& a, int mu, int precision, bool stats, int threads, cudaStream_t s);
 cudaError_t su3k_launch_increment(uint64_t* counter, uint64_t n, cudaStream_t s);
+// Sum the nparts fused-plaquette partials of one sweep (fixed order) into
+// out[*sweep % cap] * scale.
+cudaError_t su3k_launch_meas_final(const double* parts, int nparts, double scale, const uint64_t* sweep, double* out,
+                                   int cap, cudaStream_t s);
 cudaError_t su3k_launch_set_counter(uint64_t* counter, uint64_t n, cudaStream_t s);
 cudaError_t su3k_launch_init(const InitArgs& a, bool hot, cudaStream_t s);
 int su3k_plaquette_blocks(const su3dev::Geometry& g);

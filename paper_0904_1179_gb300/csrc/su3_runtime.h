@@ -39,6 +39,12 @@ struct su3_lattice {
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_conv[2] = {nullptr, nullptr};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // indexed by stats_on
+  cudaGraphExec_t graph_meas = nullptr;           // sweep with the fused plaquette
+  double* d_meas_parts = nullptr;  // fused plaquette: block partials of the 3 measuring phases
+  int meas_blocks = 0;             // blocks per phase the partials were sized for
+  double* d_meas = nullptr;        // plaquette per sweep, ring of meas_cap entries
+  double* h_meas = nullptr;        // pinned copy
+  int meas_cap = 0;
   int threads = kSu3DefaultThreads;
   int max_tries = 1;  // SU(2) proposals per subgroup (1: one-hit heatbath)
   su3dev::Geometry geom{};

@@ -55,8 +55,12 @@ struct Store<float, CG> {
 //   sum_{nu != mu} U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ + U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu).
 // Each three-link path is an SU(3) matrix, so only its rows 0 and 1 are
 // multiplied out and row 2 is completed as conj(row0 x row1).
+// Apart (optional): receives the sum of the terms with nu < MU.  After the
+// update, Re Tr(U_new Apart) is the sum of the plaquettes of the planes
+// (MU, nu < MU) at x and at x - nu-hat.
 template <typename T, int MU, bool CG>
-__device__ __forceinline__ mat3<T> staple(const Geometry& g, const void* U, const Site& st, int h, int p) {
+__device__ __forceinline__ mat3<T> staple(const Geometry& g, const void* U, const Site& st, int h, int p,
+                                          mat3<T>* Apart = nullptr) {
   const int q = p ^ 1;
   mat3<T> A = zero3<T>();
   const int h_pmu = nb_half(g, st, MU, +1);
@@ -89,6 +93,7 @@ __device__ __forceinline__ mat3<T> staple(const Geometry& g, const void* U, cons
       complete_row2(b);
       acc_full(A, b);
     }
+    if (Apart && nu == MU - 1) *Apart = A;
   }
   return A;
 }
@@ -153,13 +158,16 @@ struct UpdateCount {
 // One FP64 link update: staple, three one-hit SU(2) heatbath steps, FP64
 // Gram-Schmidt, store.  Returns the number of accepted SU(2) proposals.
 // ---------------------------------------------------------------------------
-template <int MU, bool CG, bool REPEAT, typename KEY>
+// MEAS: also return in *meas (1/3) Re Tr(U_new A_<), A_< the staple terms of
+// the directions nu < MU (see staple()).
+template <int MU, bool CG, bool REPEAT, bool MEAS = false, typename KEY>
 __device__ __forceinline__ UpdateCount update_link_f64(const Geometry& g, double2* U, int h, int p, uint64_t t,
-                                                       const KEY& key, const UpdateConsts& uc) {
+                                                       const KEY& key, const UpdateConsts& uc, double* meas = nullptr) {
   UpdateCount cnt{0, 0};
   const Site st = site_of(g, h, p);
   const uint32_t s = (uint32_t)canon(g, st);
-  const mat3<double> A = staple<double, MU, CG>(g, U, st, h, p);
+  mat3<double> Apart;
+  const mat3<double> A = staple<double, MU, CG>(g, U, st, h, p, MEAS ? &Apart : nullptr);
   mat3<double> u = load_f64<CG>(U, MU, p, h, g.Vh);
 #pragma unroll
   for (int sub = 0; sub < 3; ++sub) {
@@ -213,6 +221,14 @@ __device__ __forceinline__ UpdateCount update_link_f64(const Geometry& g, double
   }
   complete_row2(out);
   store_f64(U, MU, p, h, g.Vh, out);
+  if (MEAS) {
+    double tr = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) tr = fma(out.e[i][k].re, Apart.e[k][i].re, fma(-out.e[i][k].im, Apart.e[k][i].im, tr));
+    *meas = tr * (1.0 / 3.0);
+  }
   return cnt;
 }
 
@@ -222,7 +238,8 @@ __device__ __forceinline__ UpdateCount update_link_f64(const Geometry& g, double
 // is completed.
 // ---------------------------------------------------------------------------
 template <int MU, bool CG>
-__device__ __forceinline__ pm3 staple_p(const Geometry& g, const float4* U, const Site& st, int h, int p) {
+__device__ __forceinline__ pm3 staple_p(const Geometry& g, const float4* U, const Site& st, int h, int p,
+                                        pm3* Apart = nullptr) {
   const int q = p ^ 1;
   pm3 A = zero_p();
   const int h_pmu = nb_half(g, st, MU, +1);
@@ -259,6 +276,7 @@ __device__ __forceinline__ pm3 staple_p(const Geometry& g, const float4* U, cons
       complete_row2_p(b);
       acc_p(A, b);
     }
+    if (Apart && nu == MU - 1) *Apart = A;
   }
   return A;
 }
@@ -269,13 +287,14 @@ __device__ __forceinline__ pm3 staple_p(const Geometry& g, const float4* U, cons
 // compensated FP32 sums of FP64-class accuracy (EFT = true).  REPEAT = false
 // compiles the one-hit heatbath without the retry loop.
 // ---------------------------------------------------------------------------
-template <int MU, bool CG, bool EFT, bool REPEAT, typename KEY>
+template <int MU, bool CG, bool EFT, bool REPEAT, bool MEAS = false, typename KEY>
 __device__ __forceinline__ UpdateCount update_link_f32(const Geometry& g, float4* U, int h, int p, uint64_t t,
-                                                       const KEY& key, const UpdateConsts& uc) {
+                                                       const KEY& key, const UpdateConsts& uc, double* meas = nullptr) {
   UpdateCount cnt{0, 0};
   const Site st = site_of(g, h, p);
   const uint32_t s = (uint32_t)canon(g, st);
-  const pm3 A = staple_p<MU, CG>(g, U, st, h, p);
+  pm3 Apart;
+  const pm3 A = staple_p<MU, CG>(g, U, st, h, p, MEAS ? &Apart : nullptr);
   pm3 u = load_pm3<CG>(U, MU, p, h, g.Vh);
   complete_row2_p(u);
   const float inv_beta15 = uc.inv_beta15;
@@ -383,6 +402,25 @@ __device__ __forceinline__ UpdateCount update_link_f32(const Geometry& g, float4
   float o[12];
   reunitarise_f32<EFT>(r0, r1, o);
   store_f32_rows01(U, MU, p, h, g.Vh, o);
+  if (MEAS) {
+    // the stored link, row 2 completed, against A_<
+    mat3<float> un;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      un.e[0][k] = mk(o[2 * k], o[2 * k + 1]);
+      un.e[1][k] = mk(o[6 + 2 * k], o[6 + 2 * k + 1]);
+    }
+    complete_row2(un);
+    float tr = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const cx<float> ak = pget(Apart, k, i);
+        tr = fmaf(un.e[i][k].re, ak.re, fmaf(-un.e[i][k].im, ak.im, tr));
+      }
+    *meas = (double)tr * (1.0 / 3.0);
+  }
   return cnt;
 }
 

@@ -499,3 +499,69 @@ def test_heatbath_setting_validated():
             with pytest.raises(su3.Su3Error):
                 lat.set_heatbath(bad)
         lat.set_heatbath(1)
+
+
+# ---------------------------------------------------------------------------
+# plaquette fused into the sweep (su3_sweep_measured)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (6, 4, 10, 8), (2, 2, 2, 2)])
+def test_fp64_fused_plaquette_matches_oracle(L):
+    # per-sweep plaquettes of the updated configuration, against the oracle's
+    # separate plaquette pass after each sweep
+    seed, n = 17, 4
+    U0 = oracle.hot_start(L, 5)
+    O = U0.copy()
+    _, plaq = oracle.sweep(L, BETA, seed, 0, n, O)
+    with su3.Lattice(L, BETA, seed, start=su3.SU3_COLD) as lat:
+        lat.set_links(U0)
+        got = lat.sweep_measured(n)
+        assert lat.sweep_count == n
+        assert np.abs(lat.get_links() - O).max() < F64_TOL
+        assert abs(lat.plaquette() - got[-1]) < 1e-14
+    assert np.abs(got - plaq).max() < 1e-13
+
+
+@pytest.mark.parametrize("prec", [su3.SU3_FP64, su3.SU3_FP32_MIXED, su3.SU3_FP32_EFT])
+def test_fused_plaquette_same_chain_as_sweep(prec):
+    # the measuring sweep updates exactly like su3_sweep; its plaquette equals
+    # su3_plaquette of the same configuration up to summation order (FP64) or
+    # the FP32 staple rounding (~1e-7 per plaquette, averaged over the lattice)
+    L = (8, 8, 8, 16)
+    tol = 1e-13 if prec == su3.SU3_FP64 else 2e-6
+    with su3.Lattice(L, BETA, 3, start=su3.SU3_HOT, precision=prec) as a, \
+            su3.Lattice(L, BETA, 3, start=su3.SU3_HOT, precision=prec) as b:
+        ref = []
+        for _ in range(3):
+            a.sweep(1)
+            ref.append(a.plaquette())
+        got = b.sweep_measured(3)
+        assert np.array_equal(a.get_links(), b.get_links())
+        assert np.abs(got - np.array(ref)).max() < tol
+        b.set_block_size(64)  # partials are re-sized with the block size
+        a.sweep(1)
+        got2 = b.sweep_measured(1)
+        assert np.array_equal(a.get_links(), b.get_links())
+        assert abs(got2[0] - a.plaquette()) < tol
+
+
+def test_fused_plaquette_ring_wraps_and_needs_stats_off():
+    L = (4, 4, 4, 4)
+    n = 4100  # more than one ring of per-sweep results
+    with su3.Lattice(L, BETA, 8, start=su3.SU3_HOT) as a, su3.Lattice(L, BETA, 8, start=su3.SU3_HOT) as b:
+        got = a.sweep_measured(n)
+        b.sweep(n - 5)
+        ref = []
+        for _ in range(5):
+            b.sweep(1)
+            ref.append(b.plaquette())
+        assert np.abs(got[-5:] - np.array(ref)).max() < 1e-13
+        assert np.all(np.isfinite(got)) and np.all(np.abs(got) <= 1.0)
+        assert len(a.sweep_measured(0)) == 0
+        a.set_stats(True)
+        with pytest.raises(su3.Su3Error):
+            a.sweep_measured(1)
+        a.set_stats(False)
+        a.sweep_measured(1)
+        with pytest.raises(su3.Su3Error):
+            su3.su3_sweep_measured(a.handle, -1)
