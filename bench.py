@@ -42,6 +42,8 @@ SEED = 7
 SWEEPS_PER_STEP = 2
 # Paper, Table 1: 32^4, 2 sweeps, non-MPI program on one 2 GHz Intel E5405 core: 48.9 s.
 PAPER_UPS = 4 * 32 ** 4 * 2 / 48.9
+# Table 1, first row (non-MPI program, one core), per column 8^4 x 512, 12^4 x 101, 16^4 x 32, 32^4 x 2.
+PAPER_TABLE1_SECONDS = [48.2, 48.3, 48.7, 48.9]
 
 # Algorithmic cost per link update of one half-sweep (mu, parity): the V/2
 # updated links, the V/2 opposite-parity links of direction mu and the 3V links
@@ -66,8 +68,9 @@ def peaks():
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one ncu capture of each kernel as of commit 5c3fa88 (profiles/*.md).
-NCU_TRAFFIC = {"fp64": 687.6e6, "fp32_mixed": 222.0e6, "fp32_eft": 222.4e6, "batched": 3.407e9}
+# one ncu capture of each kernel as of commit 3e331bd (profiles/*.md); None
+# where the kernel changed after its last capture.
+NCU_TRAFFIC = {"fp64": 688.2e6, "fp32_mixed": 225.5e6, "fp32_eft": 225.9e6, "batched": None}
 
 # Peak FP64 FMA rate of GB300: 1.006 TFLOP/s measured by an FMA loop at the
 # 2070 MHz maximum SM clock (the nominal figure is 1.25 TFLOP/s).
@@ -335,7 +338,7 @@ def run_profile_case(case):
         from paper_0904_1179_gb300.workloads import batch_96
         dims, betas, seeds = batch_96()
         with su3.Batch(dims, betas, seeds, start=su3.SU3_HOT, precision=su3.SU3_FP32_MIXED) as b:
-            b.config(64, 8, 0)
+            b.config(128, 6, 0)  # the autotuner's usual choice on GB300
             b.sweep(3)
             p = b.plaquettes()
         print(json.dumps({"profile_case": case, "replicas": len(dims), "sweeps": 3, "plaquette_0": p[0]}))
@@ -447,6 +450,58 @@ def run_chains(args):
     return 0
 
 
+def run_table1(args):
+    """The paper's Table 1 workloads in full, FP64 on the GPU: 8^4 x 512, 12^4 x 101,
+    16^4 x 32 and 32^4 x 2 sweeps at beta 5.7 from the seed-7 hot start (each column
+    the same 8.39 M link updates).  CUDA events around the n sweeps of each column
+    (the sweep graph built beforehand, the start configuration restored).  With the
+    CPU baseline on, the oracle runs the four columns in full at the same time, one
+    spawned single-thread process per column."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import numpy as np
+    from paper_0904_1179_gb300.workloads import TABLE1, HEADLINE_SEED
+    pool = futs = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        pool = cf.ProcessPoolExecutor(max_workers=len(TABLE1), mp_context=mp.get_context("spawn"))
+        futs = [pool.submit(oracle.hot_chain, L, BETA, HEADLINE_SEED, n) for L, n in TABLE1]
+    import torch
+    import paper_0904_1179_gb300 as su3
+    stream = torch.cuda.Stream()
+    cols = []
+    for (L, n), paper_s in zip(TABLE1, PAPER_TABLE1_SECONDS):
+        V = int(np.prod(L))
+        row = {"lattice": list(L), "sweeps": n, "updates": 4 * V * n, "paper_1core_s": paper_s}
+        for prec, name in ((su3.SU3_FP64, "fp64"), (su3.SU3_FP32_MIXED, "fp32_mixed")):
+            with su3.Lattice(L, BETA, HEADLINE_SEED, start=su3.SU3_HOT, precision=prec,
+                             stream=stream.cuda_stream) as lat:
+                U0 = lat.get_links()
+                lat.sweep(1)  # builds the sweep graph
+                lat.set_links(U0)
+                lat.sweep_count = 0
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lat.sweep(n)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                row[name] = {"seconds": ms * 1e-3, "value": 4 * V * n / (ms * 1e-3), "plaquette": lat.plaquette()}
+        cols.append(row)
+    if futs:
+        for row, f in zip(cols, futs):
+            _, plaq, _, secs = f.result()
+            row["oracle_1core"] = {"seconds": secs, "us_per_update": secs / row["updates"] * 1e6,
+                                   "plaquette": float(plaq[-1])}
+        pool.shutdown()
+    print(json.dumps({"mode": "table1", "unit": UNIT, "beta": BETA, "seed": HEADLINE_SEED, "columns": cols,
+                      "note": "paper: non-MPI Fortran program on one 2 GHz Intel E5405 core (Table 1, first row); "
+                              "oracle: plain C FP64 program, one host core per column, four columns at once"}))
+    return 0
+
+
 def run_large(args):
     """64^4 at beta 6.0, hot start seed 7, 100 sweeps: FP64 against FP32-mixed side by side."""
     import numpy as np
@@ -482,6 +537,8 @@ def main():
     ap.add_argument("--chains-therm", type=int, default=200)
     ap.add_argument("--chains-meas", type=int, default=1000)
     ap.add_argument("--large", action="store_true", help="64^4 beta 6.0, FP64 vs FP32-mixed")
+    ap.add_argument("--table1", action="store_true",
+                    help="the paper's Table 1 columns in full (FP64 and FP32-mixed), with the oracle beside them")
     ap.add_argument("--large-sweeps", type=int, default=100)
     ap.add_argument("--profile", choices=["fp64", "fp32_mixed", "fp32_eft", "batched", "fp64_64", "fp32_mixed_64"],
                     help="small case for ncu: create the 32^4 lattice (or the 96-replica batch) and run 3 graphed "
@@ -493,6 +550,8 @@ def main():
         return run_chains(args)
     if args.large:
         return run_large(args)
+    if args.table1:
+        return run_table1(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

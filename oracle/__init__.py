@@ -225,3 +225,17 @@ def kp_draws(alpha, seed, n, max_tries=1, with_tries=False):
 def as_complex(U):
     """View (..., 3, 3, 2) real links as (..., 3, 3) complex128."""
     return U[..., 0] + 1j * U[..., 1]
+
+
+def hot_chain(L, beta, seed, nsweeps, f32=False):
+    """Hot start from `seed`, then `nsweeps` sweeps from sweep index 0.
+
+    Returns (links, plaquette per sweep, (accepted, proposed), seconds spent in
+    the sweeps).  A module-level function so that a `spawn` process pool can
+    run several chains at once (each in one thread)."""
+    import time
+    build()
+    U = hot_start(L, seed, f32=f32)
+    t0 = time.perf_counter()
+    stats, plaq = sweep(L, beta, seed, 0, nsweeps, U, f32=f32)
+    return U, plaq, stats, time.perf_counter() - t0

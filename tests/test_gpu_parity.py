@@ -565,3 +565,49 @@ def test_fused_plaquette_ring_wraps_and_needs_stats_off():
         a.sweep_measured(1)
         with pytest.raises(su3.Su3Error):
             su3.su3_sweep_measured(a.handle, -1)
+
+
+# ---------------------------------------------------------------------------
+# the paper's Table 1 workloads in full: 8^4 x 512, 12^4 x 101, 16^4 x 32,
+# 32^4 x 2 sweeps, FP64, beta 5.7, hot start from seed 7.
+#
+# Two chains that share every random number but differ by rounding do not
+# stay together forever: at beta 5.7 a 1e-15 difference grows about 2x per
+# sweep (the oracle against itself with one entry changed by 1e-15 reaches
+# 1e-10 after 15 sweeps, 1e-4 after 65, and an accept decision flips near
+# sweep 74, after which the chains are unrelated samples of the same
+# distribution).  So: per-sweep plaquettes to 1e-12 over the first 8 sweeps,
+# every link of the 32^4 column after its 2 sweeps to 1e-12, and the 8^4
+# chain's equilibrium plaquette and acceptance statistically.
+# ---------------------------------------------------------------------------
+
+def _binned(x, nb):
+    x = np.asarray(x)[: len(x) // nb * nb].reshape(nb, -1).mean(axis=1)
+    return x.mean(), x.std(ddof=1) / math.sqrt(nb)
+
+
+def test_table1_chains_match_oracle():
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from paper_0904_1179_gb300.workloads import TABLE1, HEADLINE_SEED
+    horizon = 8
+    # the four oracle chains run at once (spawned processes, one thread each)
+    with cf.ProcessPoolExecutor(max_workers=len(TABLE1), mp_context=mp.get_context("spawn")) as ex:
+        futs = [ex.submit(oracle.hot_chain, L, BETA, HEADLINE_SEED, n) for L, n in TABLE1]
+        gpu = []
+        for L, n in TABLE1:
+            with su3.Lattice(L, BETA, HEADLINE_SEED, start=su3.SU3_HOT) as lat:
+                plaq = lat.sweep_measured(n)
+                gpu.append((lat.get_links() if n <= horizon else None, plaq))
+        ref = [f.result() for f in futs]
+    for (L, n), (G, gp), (O, op, _, _) in zip(TABLE1, gpu, ref):
+        k = min(n, horizon)
+        assert np.abs(gp[:k] - op[:k]).max() < 1e-12, (L, np.abs(gp[:k] - op[:k]).max())
+        if G is not None:
+            assert np.abs(G - O).max() < 1e-12, (L, np.abs(G - O).max())
+    # 8^4 x 512: equilibrium plaquette after 112 thermalisation sweeps, 20 bins
+    g_mean, g_err = _binned(gpu[0][1][112:], 20)
+    o_mean, o_err = _binned(ref[0][1][112:], 20)
+    assert abs(g_mean - o_mean) < 4 * math.hypot(g_err, o_err), (g_mean, g_err, o_mean, o_err)
+
+
