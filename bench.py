@@ -502,6 +502,54 @@ def run_table1(args):
     return 0
 
 
+def run_decomp(args):
+    """Table 1's structure on one GPU: each column (8^4 x 512 ... 32^4 x 2 sweeps, FP64,
+    beta 5.7) undivided and cut like the paper's rows -- ndmpi = 1 with one sublattice and
+    the boundary exchange on ("1"), then np = 2, 4, 8, 16 (ndmpi 1..4, mpifactor 2).  CUDA
+    events around the n sweeps of each run (sweep graph built and sublattices filled by one
+    sweep beforehand)."""
+    import numpy as np
+    import torch
+    import paper_0904_1179_gb300 as su3
+    from paper_0904_1179_gb300.workloads import TABLE1, HEADLINE_SEED
+    rows = [("plain", None), ("1F", (1, 1, 0)), ("1", (1, 1, 1)), ("2", (1, 2, 1)), ("4", (2, 2, 1)),
+            ("8", (3, 2, 1)), ("16", (4, 2, 1))]
+    stream = torch.cuda.Stream()
+    precs = [(su3.SU3_FP64, "fp64"), (su3.SU3_FP32_MIXED, "fp32_mixed")]
+    out = []
+    for L, n in TABLE1:
+        V = int(np.prod(L))
+        col = {"lattice": list(L), "sweeps": n, "rows": {}}
+        for prec, pname in precs:
+            base = None
+            for name, dec in rows:
+                with su3.Lattice(L, BETA, HEADLINE_SEED, start=su3.SU3_HOT, precision=prec, decomp=dec,
+                                 stream=stream.cuda_stream) as lat:
+                    lat.sweep(1)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    lat.sweep(n)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    sec = e0.elapsed_time(e1) * 1e-3
+                    info = lat.decomp_info()
+                if base is None:
+                    base = sec
+                link_bytes = 144 if prec == su3.SU3_FP64 else 48
+                col["rows"].setdefault(name, {})[pname] = {
+                    "seconds": sec, "value": 4 * V * n / sec, "vs_plain": sec / base,
+                    "np": info[3], "halo_links_per_sweep": info[4],
+                    "halo_bytes_per_sweep": 2 * info[4] * link_bytes}
+        out.append(col)
+    print(json.dumps({"mode": "decomp", "unit": UNIT, "beta": BETA, "columns": out,
+                      "note": "rows as in Table 1: plain = single-lattice kernels; 1F = one sublattice, "
+                              "exchange off; 1 = one sublattice exchanging with itself; 2..16 = np sublattices "
+                              "(ndmpi 1..4, mpifactor 2); halo bytes count the read and the write of every "
+                              "copied link"}))
+    return 0
+
+
 def run_large(args):
     """64^4 at beta 6.0, hot start seed 7, 100 sweeps: FP64 against FP32-mixed side by side."""
     import numpy as np
@@ -537,6 +585,8 @@ def main():
     ap.add_argument("--chains-therm", type=int, default=200)
     ap.add_argument("--chains-meas", type=int, default=1000)
     ap.add_argument("--large", action="store_true", help="64^4 beta 6.0, FP64 vs FP32-mixed")
+    ap.add_argument("--decomp", action="store_true",
+                    help="Table 1's rows on one GPU: the domain decomposition emulated, exchange cost measured")
     ap.add_argument("--table1", action="store_true",
                     help="the paper's Table 1 columns in full (FP64 and FP32-mixed), with the oracle beside them")
     ap.add_argument("--large-sweeps", type=int, default=100)
@@ -552,6 +602,8 @@ def main():
         return run_large(args)
     if args.table1:
         return run_table1(args)
+    if args.decomp:
+        return run_decomp(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -175,6 +175,42 @@ SU3_API int su3_info(su3_handle h, int dims[4], double* beta, uint64_t* seed, in
 SU3_API int su3_set_block_size(su3_handle h, int threads);
 
 /* ---------------------------------------------------------------------------
+ * Domain decomposition emulated on one device (Sec. 2.1, Eq. (MPInp), Tables
+ * 1 and 2): the first ndmpi directions are cut into mpifactor parts each,
+ * giving np = mpifactor^ndmpi sublattices (the PBC case nlat = 1; the printed
+ * Eq. (MPInp) reads "ndmpi**mpifactor", which Tables 1-3 contradict:
+ * np = 1296 for ndmpi 4, mpifactor 6).  Each sublattice keeps its own
+ * extended store with one ghost layer on each side of a cut direction; after
+ * every checkerboard half-sweep the updated links on the sublattice faces are
+ * copied into the ghost cells that the neighbours' staples read (the
+ * boundary exchange, Appendix A Eq. (mscb18)), by one gather launch over all
+ * sublattices.  lbcex = 0 (only with mpifactor 1) is the paper's "exchange
+ * off" run: plain periodic wrap, the single-lattice kernels.  Results are bit
+ * for bit those of su3_create_ex with the same arguments: the random numbers
+ * are keyed by the global site.
+ * ------------------------------------------------------------------------- */
+
+/* Create a decomposed lattice.  Arguments as for su3_create_ex plus
+ *   ndmpi: number of cut directions, 1..4 (directions 0..ndmpi-1);
+ *   mpifactor: parts per cut direction, >= 1; every cut extent must split
+ *     into even parts of at least 2 sites;
+ *   lbcex: 1 = boundary exchange on, 0 = off (mpifactor 1 only).
+ * The handle accepts every single-lattice call: su3_sweep and su3_half_sweep
+ * run the decomposed sweep; su3_plaquette, su3_links_get and su3_links_set
+ * first gather the sublattices into (or scatter them from) the handle's
+ * global store.  Not available on it: su3_sweep_measured, and max_tries > 1
+ * in su3_set_heatbath (SU3_EINVAL).  Errors: SU3_EINVAL (arguments),
+ * SU3_ENOMEM / SU3_ECUDA (allocation). */
+SU3_API int su3_decomp_create(int L0, int L1, int L2, int L3, double beta, uint64_t seed, int start, int precision,
+                              int ndmpi, int mpifactor, int lbcex, void* cuda_stream, su3_handle* out);
+
+/* Decomposition of a handle (any pointer may be NULL): ndmpi, mpifactor,
+ * lbcex, the number of sublattices, and the links the boundary exchange
+ * copies per sweep.  A handle from su3_create reports 0, 1, 0, 1, 0. */
+SU3_API int su3_decomp_info(su3_handle h, int* ndmpi, int* mpifactor, int* lbcex, int* nsub,
+                            long long* halo_links_per_sweep);
+
+/* ---------------------------------------------------------------------------
  * Batches: n independent replicas, each with its own extents, beta and Philox
  * seed (the same counter layout, keyed by the replica's seed), swept together
  * by ONE persistent kernel launch per sweep, captured in a CUDA graph.  Each

@@ -19,6 +19,7 @@ import numpy as np
 __all__ = [
     "SU3_COLD", "SU3_HOT", "SU3_FP64", "SU3_FP32_MIXED", "SU3_FP32_EFT", "Su3Error", "load_library", "library_path",
     "su3_create", "su3_create_ex", "su3_destroy", "su3_sweep", "su3_sweep_measured", "su3_half_sweep", "su3_plaquette",
+    "su3_decomp_create", "su3_decomp_info",
     "su3_links_get", "su3_links_set", "su3_sweep_count", "su3_set_sweep_count", "su3_set_stats", "su3_stats",
     "su3_info", "su3_set_block_size", "su3_set_heatbath", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
     "su3_batch_links_get", "su3_batch_links_set", "su3_batch_size", "su3_batch_config", "su3_batch_get_config",
@@ -50,6 +51,12 @@ EXPORTS = [
     ("su3_destroy", ctypes.c_int, [_h]),
     ("su3_sweep", ctypes.c_int, [_h, ctypes.c_int]),
     ("su3_sweep_measured", ctypes.c_int, [_h, ctypes.c_int, _pd]),
+    ("su3_decomp_create", ctypes.c_int, [ctypes.c_int] * 4 + [ctypes.c_double, _u64, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.POINTER(_h)]),
+    ("su3_decomp_info", ctypes.c_int, [_h, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_longlong)]),
     ("su3_half_sweep", ctypes.c_int, [_h, ctypes.c_int, ctypes.c_int]),
     ("su3_plaquette", ctypes.c_double, [_h]),
     ("su3_links_get", ctypes.c_int, [_h, _pd, ctypes.c_size_t]),
@@ -133,6 +140,21 @@ def su3_create_ex(L0, L1, L2, L3, beta, seed, start, precision, cuda_stream=None
     _check(load_library().su3_create_ex(L0, L1, L2, L3, beta, seed, start, precision,
                                         ctypes.c_void_p(cuda_stream or None), ctypes.byref(h)))
     return h
+
+
+def su3_decomp_create(L0, L1, L2, L3, beta, seed, start, precision, ndmpi, mpifactor, lbcex=1, cuda_stream=None):
+    h = _h()
+    _check(load_library().su3_decomp_create(L0, L1, L2, L3, beta, seed, start, precision, ndmpi, mpifactor, lbcex,
+                                            ctypes.c_void_p(cuda_stream or None), ctypes.byref(h)))
+    return h
+
+
+def su3_decomp_info(h):
+    """(ndmpi, mpifactor, lbcex, number of sublattices, links copied by the exchange per sweep)."""
+    v = [ctypes.c_int() for _ in range(4)]
+    n = ctypes.c_longlong()
+    _check(load_library().su3_decomp_info(h, *[ctypes.byref(x) for x in v], ctypes.byref(n)))
+    return tuple(x.value for x in v) + (n.value,)
 
 
 def su3_destroy(h):
@@ -374,9 +396,15 @@ class Batch:
 class Lattice:
     """Owning wrapper of one su3 handle."""
 
-    def __init__(self, dims, beta, seed, start=SU3_HOT, precision=SU3_FP64, stream=None):
+    def __init__(self, dims, beta, seed, start=SU3_HOT, precision=SU3_FP64, stream=None, decomp=None):
+        """decomp = (ndmpi, mpifactor, lbcex): the domain decomposition emulated on one device."""
         self.dims = tuple(int(x) for x in dims)
-        self.handle = su3_create_ex(*self.dims, float(beta), int(seed), int(start), int(precision), stream)
+        if decomp is None:
+            self.handle = su3_create_ex(*self.dims, float(beta), int(seed), int(start), int(precision), stream)
+        else:
+            nd, nf, ex = (tuple(decomp) + (1,))[:3]
+            self.handle = su3_decomp_create(*self.dims, float(beta), int(seed), int(start), int(precision), int(nd),
+                                            int(nf), int(ex), stream)
         self.beta = float(beta)
         self.seed = int(seed)
         self.precision = int(precision)
@@ -404,6 +432,9 @@ class Lattice:
 
     def sweep(self, n=1):
         su3_sweep(self.handle, n)
+
+    def decomp_info(self):
+        return su3_decomp_info(self.handle)
 
     def sweep_measured(self, n):
         return su3_sweep_measured(self.handle, n)

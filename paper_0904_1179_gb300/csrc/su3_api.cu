@@ -74,6 +74,7 @@ void release(su3_lattice* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graphs(h);
   if (h->batch) su3_batch_release(h->batch);
+  if (h->decomp) su3_decomp_release(h->decomp);
   cudaFree(h->links);
   cudaFree(h->d_sweep);
   cudaFree(h->d_stats);
@@ -315,6 +316,7 @@ int su3_sweep(su3_handle h, int nsweeps) {
   if (is_batch(h)) return fail(SU3_EINVAL, "su3_sweep: batch handle (use the su3_batch_* calls)");
   if (nsweeps < 0) return fail(SU3_EINVAL, "su3_sweep: nsweeps < 0");
   if (nsweeps == 0) return SU3_OK;
+  if (su3_decomp_active(h)) return su3_decomp_sweep(h, nsweeps);
   int rc = ensure_graph(h);
   if (rc != SU3_OK) return rc;
   cudaGraphExec_t exec = h->graph[h->stats_on ? 1 : 0];
@@ -328,6 +330,7 @@ int su3_sweep_measured(su3_handle h, int nsweeps, double* plaq_out) {
   if (is_batch(h)) return fail(SU3_EINVAL, "su3_sweep_measured: batch handle (use su3_batch_plaquettes)");
   if (nsweeps < 0 || (nsweeps > 0 && !plaq_out)) return fail(SU3_EINVAL, "su3_sweep_measured: bad nsweeps or NULL out");
   if (h->stats_on) return fail(SU3_EINVAL, "su3_sweep_measured: disable acceptance statistics first");
+  if (su3_decomp_active(h)) return fail(SU3_EINVAL, "su3_sweep_measured: not available on a decomposed lattice");
   if (nsweeps == 0) return SU3_OK;
   const int blocks = (h->geom.Vh + h->threads - 1) / h->threads;
   if (h->meas_blocks != blocks || !h->d_meas) {
@@ -368,6 +371,7 @@ int su3_half_sweep(su3_handle h, int mu, int parity) {
   if (!h) return fail(SU3_EINVAL, "su3_half_sweep: NULL handle");
   if (is_batch(h)) return fail(SU3_EINVAL, "su3_half_sweep: batch handle (use the su3_batch_* calls)");
   if (mu < 0 || mu > 3 || parity < 0 || parity > 1) return fail(SU3_EINVAL, "su3_half_sweep: bad mu/parity");
+  if (su3_decomp_active(h)) return su3_decomp_half_sweep(h, mu, parity);
   SU3_CUDA(su3k_launch_half_sweep(half_sweep_args(h, parity), mu, h->precision, h->stats_on, h->threads, h->stream),
            "su3_half_sweep");
   return SU3_OK;
@@ -378,6 +382,7 @@ double su3_plaquette(su3_handle h) {
     fail(SU3_EINVAL, h ? "su3_plaquette: batch handle (use su3_batch_plaquettes)" : "su3_plaquette: NULL handle");
     return NAN;
   }
+  if (su3_decomp_sync_global(h) != SU3_OK) return NAN;
   PlaqArgs a{h->geom, h->links, h->d_partials};
   cudaError_t e = su3k_launch_plaquette(a, h->precision, h->d_plaq, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_plaq, h->d_plaq, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -393,6 +398,8 @@ int su3_links_get(su3_handle h, double* host, size_t n_doubles) {
   if (!h || !host) return fail(SU3_EINVAL, "su3_links_get: NULL argument");
   if (is_batch(h)) return fail(SU3_EINVAL, "su3_links_get: batch handle (use the su3_batch_* calls)");
   if (n_doubles != (size_t)h->V * 72) return fail(SU3_ESIZE, "su3_links_get: n = %zu, expected %lld", n_doubles, h->V * 72);
+  const int rc = su3_decomp_sync_global(h);
+  if (rc != SU3_OK) return rc;
   return su3_transfer(h, h->geom, h->links, host, true, "su3_links_get");
 }
 
@@ -400,7 +407,9 @@ int su3_links_set(su3_handle h, const double* host, size_t n_doubles) {
   if (!h || !host) return fail(SU3_EINVAL, "su3_links_set: NULL argument");
   if (is_batch(h)) return fail(SU3_EINVAL, "su3_links_set: batch handle (use the su3_batch_* calls)");
   if (n_doubles != (size_t)h->V * 72) return fail(SU3_ESIZE, "su3_links_set: n = %zu, expected %lld", n_doubles, h->V * 72);
-  return su3_transfer(h, h->geom, h->links, const_cast<double*>(host), false, "su3_links_set");
+  const int rc = su3_transfer(h, h->geom, h->links, const_cast<double*>(host), false, "su3_links_set");
+  if (rc == SU3_OK) su3_decomp_global_written(h);
+  return rc;
 }
 
 int su3_sweep_count(su3_handle h, uint64_t* out) {
@@ -450,6 +459,8 @@ int su3_set_heatbath(su3_handle h, int max_tries) {
   if (!h) return fail(SU3_EINVAL, "su3_set_heatbath: NULL handle");
   if (max_tries < 1 || max_tries > kMaxHeatbathTries)
     return fail(SU3_EINVAL, "su3_set_heatbath: max_tries %d not in [1, %d]", max_tries, kMaxHeatbathTries);
+  if (max_tries > 1 && su3_decomp_active(h))
+    return fail(SU3_EINVAL, "su3_set_heatbath: a decomposed lattice runs the one-hit heatbath only");
   if (max_tries != h->max_tries) {
     SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_set_heatbath");
     drop_graphs(h);
@@ -468,6 +479,7 @@ int su3_set_block_size(su3_handle h, int threads) {
   if (threads != h->threads) {
     SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_set_block_size");
     drop_graphs(h);
+    if (h->decomp) su3_decomp_invalidate(h->decomp);
     h->threads = threads;
   }
   return SU3_OK;

@@ -1,0 +1,491 @@
+// su3_decomp.cu -- the paper's domain decomposition emulated on one device.
+//
+// Berg & Wu (arXiv:0904.1179, Sec. 2.1) cut the first ndmpi directions of the
+// lattice into mpifactor parts each; every sublattice lives in its own MPI
+// process and, between checkerboard steps, sends the boundary links its
+// neighbours need (Appendix A: the checkerboard link storage of a face,
+// Eq. (mscb18)).  With np = 1 the switch lbcex turns that exchange off (plain
+// periodic wrap) or on (the sublattice exchanges with itself), the "1F" and
+// "1" rows of Tables 1 and 2.
+//
+// Here all np sublattices live on one GPU, each in its own extended-box store
+// with a ghost layer on both sides of every cut direction.  One sweep is, for
+// mu = 0..3 and parity even then odd:
+//   1. one launch updating the (mu, parity) links of every sublattice (the
+//      same per-link code as the single lattice, on the sublattice geometry);
+//   2. one launch of the boundary exchange: the updated (mu, parity) links on
+//      the sublattice faces are copied into the ghost cells that read them
+//      (faces, and the edges x + a - b that the staples' corner paths reach),
+//      from gather lists built once on the host.
+// The random numbers are keyed by the global site, so every link comes out
+// bit for bit as in the undivided lattice; what the emulation adds is the
+// measured cost of the exchange on a GB300.
+#include <cstdarg>
+#include <cstdio>
+#include <new>
+#include <vector>
+
+#include "su3_device.cuh"
+#include "su3_kernels.h"
+#include "su3_runtime.h"
+#include "su3_update.cuh"
+
+using namespace su3dev;
+
+struct su3_decomp {
+  int ndmpi = 0, nf = 1, np = 1, lbcex = 1;
+  bool active = false;         // false: np = 1 with the exchange off -- the plain lattice
+  SubGeometry geo{};           // sublattice geometry, origin 0
+  size_t sub_elems = 0;        // double2 (FP64) or float4 (FP32) elements per sublattice store
+  void* d_sub = nullptr;       // np stores
+  int4* d_ghost[2] = {nullptr, nullptr};  // gather lists per parity: {dst sub, dst half, src sub, src half}
+  int nghost[2] = {0, 0};
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // indexed by stats_on
+  bool subs_current = false;   // sublattice stores hold the configuration
+  bool global_current = true;  // the handle's global store holds it
+};
+
+namespace {
+
+struct DecompArgs {
+  SubGeometry g;
+  int nf, ndmpi;
+  PhiloxRoundKeys key;
+  int parity;
+  double inv_beta15_f64;
+  float inv_beta15;
+  const uint64_t* sweep;
+  void* subs;
+  size_t sub_elems;
+  unsigned long long* stats;
+};
+
+// Origin of sublattice k (index k = k0 + nf*(k1 + nf*...) over the cut directions).
+__device__ __forceinline__ SubGeometry sub_geometry(const SubGeometry& base, int nf, int ndmpi, int k) {
+  SubGeometry g = base;
+  const int l[4] = {base.in.L0, base.in.L1, base.in.L2, base.in.L3};
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    g.o[d] = d < ndmpi ? (k % nf) * l[d] : 0;
+    if (d < ndmpi) k /= nf;
+  }
+  return g;
+}
+
+template <bool STATS>
+__device__ __forceinline__ void count_stats_d(UpdateCount c, unsigned long long* stats) {
+  if (STATS) {
+    const int acc = __reduce_add_sync(0xffffffffu, c.accepted);
+    const int prop = __reduce_add_sync(0xffffffffu, c.proposed);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&stats[0], (unsigned long long)acc);
+      atomicAdd(&stats[1], (unsigned long long)prop);
+    }
+  }
+}
+
+template <int MU, bool STATS>
+__global__ void __launch_bounds__(kMaxSweepThreads) k_decomp_half_sweep_f64(DecompArgs a) {
+  const int k = blockIdx.y;
+  const SubGeometry g = sub_geometry(a.g, a.nf, a.ndmpi, k);
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  UpdateCount c{0, 0};
+  if (h < g.in.Vh) {
+    const UpdateConsts uc{a.inv_beta15_f64, a.inv_beta15, 1};
+    double2* U = (double2*)a.subs + (size_t)k * a.sub_elems;
+    c = update_link_f64<MU, false, false>(g, U, h, a.parity, *a.sweep, a.key, uc);
+  }
+  count_stats_d<STATS>(c, a.stats);
+}
+
+template <int MU, bool STATS, bool EFT>
+__global__ void __launch_bounds__(kMaxSweepThreads, 4) k_decomp_half_sweep_f32(DecompArgs a) {
+  const int k = blockIdx.y;
+  const SubGeometry g = sub_geometry(a.g, a.nf, a.ndmpi, k);
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  UpdateCount c{0, 0};
+  if (h < g.in.Vh) {
+    const UpdateConsts uc{a.inv_beta15_f64, a.inv_beta15, 1};
+    float4* U = (float4*)a.subs + (size_t)k * a.sub_elems;
+    c = update_link_f32<MU, false, EFT, false>(g, U, h, a.parity, *a.sweep, a.key, uc);
+  }
+  count_stats_d<STATS>(c, a.stats);
+}
+
+// Boundary exchange of the (mu, parity) links: one thread per ghost cell.
+template <typename E, int NC>
+__global__ void k_decomp_exchange(const int4* __restrict__ list, int n, int mu, int parity, E* subs,
+                                  size_t sub_elems, int Vh) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int4 e = list[i];
+  const size_t off = link_base(mu, parity, Vh, NC);
+  const E* src = subs + (size_t)e.z * sub_elems + off + e.w;
+  E* dst = subs + (size_t)e.x * sub_elems + off + e.y;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) dst[(size_t)c * Vh] = src[(size_t)c * Vh];
+}
+
+// Global store <-> sublattice interiors, all four directions of each site.
+template <typename E, int NC, bool TO_SUBS>
+__global__ void k_decomp_move(SubGeometry base, int nf, int ndmpi, E* global, int Vh_global, E* subs,
+                              size_t sub_elems) {
+  const int k = blockIdx.y, p = blockIdx.z;
+  const SubGeometry g = sub_geometry(base, nf, ndmpi, k);
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= g.in.Vh) return;
+  const SubSite st = site_of(g, h, p);
+  const int hg = st.s >> 1;
+  const int hs = store_index(g, st, h);
+  E* sub = subs + (size_t)k * sub_elems;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    E* a = global + link_base(mu, p, Vh_global, NC) + hg;
+    E* b = sub + link_base(mu, p, g.Vh, NC) + hs;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (TO_SUBS)
+        b[(size_t)c * g.Vh] = a[(size_t)c * Vh_global];
+      else
+        a[(size_t)c * Vh_global] = b[(size_t)c * g.Vh];
+    }
+  }
+}
+
+template <int MU>
+cudaError_t launch_update_mu(const DecompArgs& a, int precision, bool stats, int threads, int np, cudaStream_t s) {
+  const dim3 grid((a.g.in.Vh + threads - 1) / threads, np);
+  if (precision == SU3_FP64) {
+    if (stats)
+      k_decomp_half_sweep_f64<MU, true><<<grid, threads, 0, s>>>(a);
+    else
+      k_decomp_half_sweep_f64<MU, false><<<grid, threads, 0, s>>>(a);
+  } else if (precision == SU3_FP32_EFT) {
+    if (stats)
+      k_decomp_half_sweep_f32<MU, true, true><<<grid, threads, 0, s>>>(a);
+    else
+      k_decomp_half_sweep_f32<MU, false, true><<<grid, threads, 0, s>>>(a);
+  } else {
+    if (stats)
+      k_decomp_half_sweep_f32<MU, true, false><<<grid, threads, 0, s>>>(a);
+    else
+      k_decomp_half_sweep_f32<MU, false, false><<<grid, threads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const DecompArgs& a, int mu, int precision, bool stats, int threads, int np, cudaStream_t s) {
+  switch (mu) {
+    case 0: return launch_update_mu<0>(a, precision, stats, threads, np, s);
+    case 1: return launch_update_mu<1>(a, precision, stats, threads, np, s);
+    case 2: return launch_update_mu<2>(a, precision, stats, threads, np, s);
+    default: return launch_update_mu<3>(a, precision, stats, threads, np, s);
+  }
+}
+
+cudaError_t launch_exchange(const su3_decomp* d, int precision, int mu, int parity, cudaStream_t s) {
+  const int n = d->nghost[parity];
+  if (n == 0) return cudaSuccess;
+  const int threads = 256, blocks = (n + threads - 1) / threads;
+  if (precision == SU3_FP64)
+    k_decomp_exchange<double2, kEntriesF64><<<blocks, threads, 0, s>>>(d->d_ghost[parity], n, mu, parity,
+                                                                       (double2*)d->d_sub, d->sub_elems, d->geo.Vh);
+  else
+    k_decomp_exchange<float4, kGroupsF32><<<blocks, threads, 0, s>>>(d->d_ghost[parity], n, mu, parity,
+                                                                     (float4*)d->d_sub, d->sub_elems, d->geo.Vh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_move(const su3_lattice* h, bool to_subs) {
+  const su3_decomp* d = h->decomp;
+  const int threads = 256;
+  const dim3 grid((d->geo.in.Vh + threads - 1) / threads, d->np, 2);
+  if (h->precision == SU3_FP64) {
+    if (to_subs)
+      k_decomp_move<double2, kEntriesF64, true><<<grid, threads, 0, h->stream>>>(
+          d->geo, d->nf, d->ndmpi, (double2*)h->links, h->geom.Vh, (double2*)d->d_sub, d->sub_elems);
+    else
+      k_decomp_move<double2, kEntriesF64, false><<<grid, threads, 0, h->stream>>>(
+          d->geo, d->nf, d->ndmpi, (double2*)h->links, h->geom.Vh, (double2*)d->d_sub, d->sub_elems);
+  } else {
+    if (to_subs)
+      k_decomp_move<float4, kGroupsF32, true><<<grid, threads, 0, h->stream>>>(
+          d->geo, d->nf, d->ndmpi, (float4*)h->links, h->geom.Vh, (float4*)d->d_sub, d->sub_elems);
+    else
+      k_decomp_move<float4, kGroupsF32, false><<<grid, threads, 0, h->stream>>>(
+          d->geo, d->nf, d->ndmpi, (float4*)h->links, h->geom.Vh, (float4*)d->d_sub, d->sub_elems);
+  }
+  return cudaGetLastError();
+}
+
+DecompArgs decomp_args(const su3_lattice* h, int parity) {
+  const su3_decomp* d = h->decomp;
+  DecompArgs a{};
+  a.g = d->geo;
+  a.nf = d->nf;
+  a.ndmpi = d->ndmpi;
+  a.key = philox_round_keys(h->key);
+  a.parity = parity;
+  a.inv_beta15_f64 = 1.5 / h->beta;
+  a.inv_beta15 = (float)(1.5 / h->beta);
+  a.sweep = h->d_sweep;
+  a.subs = d->d_sub;
+  a.sub_elems = d->sub_elems;
+  a.stats = h->d_stats;
+  return a;
+}
+
+int enqueue_phase(su3_lattice* h, int mu, int parity) {
+  su3_decomp* d = h->decomp;
+  SU3_CUDA(launch_update(decomp_args(h, parity), mu, h->precision, h->stats_on, h->threads, d->np, h->stream),
+           "decomposed half-sweep launch");
+  SU3_CUDA(launch_exchange(d, h->precision, mu, parity, h->stream), "boundary exchange launch");
+  return SU3_OK;
+}
+
+// Bring the sublattice stores up to date from the global store (after a start
+// configuration or su3_links_set): scatter the interiors, then fill every ghost.
+int ensure_subs(su3_lattice* h) {
+  su3_decomp* d = h->decomp;
+  if (d->subs_current) return SU3_OK;
+  SU3_CUDA(launch_move(h, true), "decomposition scatter");
+  for (int mu = 0; mu < 4; ++mu)
+    for (int p = 0; p < 2; ++p) SU3_CUDA(launch_exchange(d, h->precision, mu, p, h->stream), "ghost fill");
+  d->subs_current = true;
+  return SU3_OK;
+}
+
+int ensure_decomp_graph(su3_lattice* h) {
+  su3_decomp* d = h->decomp;
+  cudaGraphExec_t& exec = d->graph[h->stats_on ? 1 : 0];
+  if (exec) return SU3_OK;
+  cudaGraph_t graph = nullptr;
+  SU3_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
+  int rc = SU3_OK;
+  for (int mu = 0; mu < 4 && rc == SU3_OK; ++mu)
+    for (int p = 0; p < 2 && rc == SU3_OK; ++p) rc = enqueue_phase(h, mu, p);
+  if (rc == SU3_OK) {
+    const cudaError_t e = su3k_launch_increment(h->d_sweep, 1, h->stream);
+    if (e != cudaSuccess) rc = su3_cuda_fail(e, "sweep counter launch");
+  }
+  const cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  if (rc != SU3_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  SU3_CUDA(e, "graph capture end");
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  SU3_CUDA(ei, "graph instantiate");
+  return SU3_OK;
+}
+
+// Gather lists of the boundary exchange.  A ghost cell is read by a staple if
+// exactly one cut coordinate lies outside the interior (a face: x +- nu), or
+// two do with one above and one below (an edge: x + mu - nu).
+void build_ghost_lists(const su3_lattice* h, const su3_decomp* d, std::vector<int4> lists[2]) {
+  const SubGeometry& g = d->geo;
+  const int* e = g.e;
+  const int l[4] = {g.in.L0, g.in.L1, g.in.L2, g.in.L3};
+  for (int k = 0; k < d->np; ++k) {
+    int o[4] = {0, 0, 0, 0}, kk = k;
+    for (int dd = 0; dd < d->ndmpi; ++dd) {
+      o[dd] = (kk % d->nf) * l[dd];
+      kk /= d->nf;
+    }
+    for (int y3 = 0; y3 < e[3]; ++y3)
+      for (int y2 = 0; y2 < e[2]; ++y2)
+        for (int y1 = 0; y1 < e[1]; ++y1)
+          for (int y0 = 0; y0 < e[0]; ++y0) {
+            const int y[4] = {y0, y1, y2, y3};
+            int below = 0, above = 0;
+            for (int dd = 0; dd < 4; ++dd) {
+              if (!((g.cut >> dd) & 1)) continue;
+              if (y[dd] == 0) ++below;
+              if (y[dd] == e[dd] - 1) ++above;
+            }
+            const int out = below + above;
+            if (out == 0 || out > 2 || (out == 2 && (below != 1 || above != 1))) continue;
+            int x[4], ys[4], ksrc = 0, mul = 1, par = 0;
+            for (int dd = 0; dd < 4; ++dd) {
+              const int c = (g.cut >> dd) & 1;
+              x[dd] = ((y[dd] - c + o[dd]) % h->L[dd] + h->L[dd]) % h->L[dd];
+              par += x[dd];
+              if (c) {
+                ksrc += (x[dd] / l[dd]) * mul;
+                mul *= d->nf;
+                ys[dd] = x[dd] % l[dd] + 1;
+              } else {
+                ys[dd] = x[dd];
+              }
+            }
+            const int dst = (y[0] >> 1) + g.he0 * (y[1] + e[1] * (y[2] + e[2] * y[3]));
+            const int src = (ys[0] >> 1) + g.he0 * (ys[1] + e[1] * (ys[2] + e[2] * ys[3]));
+            lists[par & 1].push_back(make_int4(k, dst, ksrc, src));
+          }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Hooks for su3_api.cu.
+// ---------------------------------------------------------------------------
+bool su3_decomp_active(const su3_lattice* h) { return h && h->decomp && h->decomp->active; }
+
+void su3_decomp_invalidate(su3_decomp* d) {
+  for (auto& g : d->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+void su3_decomp_release(su3_decomp* d) {
+  if (!d) return;
+  su3_decomp_invalidate(d);
+  cudaFree(d->d_sub);
+  cudaFree(d->d_ghost[0]);
+  cudaFree(d->d_ghost[1]);
+  delete d;
+}
+
+int su3_decomp_sweep(su3_lattice* h, int nsweeps) {
+  int rc = ensure_subs(h);
+  if (rc != SU3_OK) return rc;
+  rc = ensure_decomp_graph(h);
+  if (rc != SU3_OK) return rc;
+  cudaGraphExec_t exec = h->decomp->graph[h->stats_on ? 1 : 0];
+  for (int n = 0; n < nsweeps; ++n) SU3_CUDA(cudaGraphLaunch(exec, h->stream), "su3_sweep: graph launch");
+  h->sweep_host += (uint64_t)nsweeps;
+  h->decomp->global_current = false;
+  return SU3_OK;
+}
+
+int su3_decomp_half_sweep(su3_lattice* h, int mu, int parity) {
+  int rc = ensure_subs(h);
+  if (rc != SU3_OK) return rc;
+  rc = enqueue_phase(h, mu, parity);
+  if (rc != SU3_OK) return rc;
+  h->decomp->global_current = false;
+  return SU3_OK;
+}
+
+// Before anything reads the handle's global store.
+int su3_decomp_sync_global(su3_lattice* h) {
+  if (!su3_decomp_active(h) || h->decomp->global_current) return SU3_OK;
+  SU3_CUDA(launch_move(h, false), "decomposition gather");
+  h->decomp->global_current = true;
+  return SU3_OK;
+}
+
+// After the global store was written (su3_links_set).
+void su3_decomp_global_written(su3_lattice* h) {
+  if (!su3_decomp_active(h)) return;
+  h->decomp->global_current = true;
+  h->decomp->subs_current = false;
+}
+
+extern "C" {
+
+int su3_decomp_create(int L0, int L1, int L2, int L3, double beta, uint64_t seed, int start, int precision,
+                      int ndmpi, int mpifactor, int lbcex, void* cuda_stream, su3_handle* out) {
+  if (!out) return su3_fail(SU3_EINVAL, "su3_decomp_create: out is NULL");
+  *out = nullptr;
+  const int L[4] = {L0, L1, L2, L3};
+  if (ndmpi < 1 || ndmpi > 4) return su3_fail(SU3_EINVAL, "su3_decomp_create: ndmpi %d not in [1, 4]", ndmpi);
+  if (mpifactor < 1) return su3_fail(SU3_EINVAL, "su3_decomp_create: mpifactor %d < 1", mpifactor);
+  if (lbcex != 0 && lbcex != 1) return su3_fail(SU3_EINVAL, "su3_decomp_create: lbcex must be 0 or 1");
+  if (!lbcex && mpifactor > 1)
+    return su3_fail(SU3_EINVAL, "su3_decomp_create: the exchange can be off only for one sublattice (mpifactor 1)");
+  for (int d = 0; d < ndmpi; ++d)
+    if (L[d] % mpifactor || (L[d] / mpifactor) % 2 || L[d] / mpifactor < 2)
+      return su3_fail(SU3_EINVAL, "su3_decomp_create: L%d = %d does not split into %d even parts >= 2", d, L[d],
+                      mpifactor);
+  long long np = 1;
+  for (int d = 0; d < ndmpi; ++d) np *= mpifactor;
+  if (np > 65535) return su3_fail(SU3_EINVAL, "su3_decomp_create: %lld sublattices (at most 65535)", np);
+
+  su3_handle h = nullptr;
+  int rc = su3_create_ex(L0, L1, L2, L3, beta, seed, start, precision, cuda_stream, &h);
+  if (rc != SU3_OK) return rc;
+  su3_decomp* d = new (std::nothrow) su3_decomp;
+  if (!d) {
+    su3_release_handle(h);
+    return su3_fail(SU3_ENOMEM, "su3_decomp_create: host allocation failed");
+  }
+  h->decomp = d;
+  d->ndmpi = ndmpi;
+  d->nf = mpifactor;
+  d->np = (int)np;
+  d->lbcex = lbcex;
+  d->active = lbcex != 0;
+  if (!d->active) {  // one sublattice without exchange: the plain periodic lattice
+    *out = h;
+    return SU3_OK;
+  }
+  SubGeometry& g = d->geo;
+  int l[4];
+  long long ext = 1;
+  g.cut = 0;
+  for (int dd = 0; dd < 4; ++dd) {
+    const bool cut = dd < ndmpi;
+    l[dd] = cut ? L[dd] / mpifactor : L[dd];
+    g.e[dd] = l[dd] + (cut ? 2 : 0);
+    g.o[dd] = 0;
+    if (cut) g.cut |= 1 << dd;
+    ext *= g.e[dd];
+  }
+  g.in.L0 = l[0];
+  g.in.L1 = l[1];
+  g.in.L2 = l[2];
+  g.in.L3 = l[3];
+  g.in.hL0 = l[0] / 2;
+  g.in.Vh = (int)((long long)l[0] * l[1] * l[2] * l[3] / 2);
+  g.in.s1 = l[0];
+  g.in.s2 = l[0] * l[1];
+  g.in.s3 = l[0] * l[1] * l[2];
+  g.he0 = g.e[0] / 2;
+  g.L0 = L0;
+  g.L1 = L1;
+  g.L2 = L2;
+  g.Vh = (int)(ext / 2);
+  const int ncomp = precision == SU3_FP64 ? kEntriesF64 : kGroupsF32;
+  const size_t elem = precision == SU3_FP64 ? sizeof(double2) : sizeof(float4);
+  d->sub_elems = (size_t)8 * ncomp * g.Vh;
+  std::vector<int4> lists[2];
+  build_ghost_lists(h, d, lists);
+  cudaError_t e = cudaMalloc(&d->d_sub, d->sub_elems * elem * np);
+  for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+    d->nghost[p] = (int)lists[p].size();
+    if (d->nghost[p] == 0) continue;
+    e = cudaMalloc(&d->d_ghost[p], lists[p].size() * sizeof(int4));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(d->d_ghost[p], lists[p].data(), lists[p].size() * sizeof(int4), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    rc = su3_cuda_fail(e, "su3_decomp_create: allocation");
+    cudaGetLastError();
+    su3_release_handle(h);
+    return rc;
+  }
+  // the sublattices need no zero fill: every interior cell is scattered and
+  // every ghost cell a staple reads is filled before the first sweep
+  d->subs_current = false;
+  d->global_current = true;
+  *out = h;
+  return SU3_OK;
+}
+
+int su3_decomp_info(su3_handle h, int* ndmpi, int* mpifactor, int* lbcex, int* nsub, long long* halo_links_per_sweep) {
+  if (!h) return su3_fail(SU3_EINVAL, "su3_decomp_info: NULL handle");
+  const su3_decomp* d = h->decomp;
+  if (ndmpi) *ndmpi = d ? d->ndmpi : 0;
+  if (mpifactor) *mpifactor = d ? d->nf : 1;
+  if (lbcex) *lbcex = d ? d->lbcex : 0;
+  if (nsub) *nsub = d ? d->np : 1;
+  if (halo_links_per_sweep) *halo_links_per_sweep = d ? 4LL * ((long long)d->nghost[0] + d->nghost[1]) : 0;
+  return SU3_OK;
+}
+
+}  // extern "C"

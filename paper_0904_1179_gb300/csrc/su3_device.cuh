@@ -296,6 +296,82 @@ __device__ __forceinline__ int nb_half2(const Geometry& g, const Site& s, int nu
   return (t.x0 >> 1) + g.hL0 * t.r;
 }
 
+// Storage half index of the thread's own site (the plain lattice stores the
+// site where it enumerates it).
+__device__ __forceinline__ int store_index(const Geometry&, const Site&, int h) { return h; }
+
+// ---------------------------------------------------------------------------
+// Sublattice with ghost layers: the paper's domain decomposition (Sec. 2.1:
+// the first ndmpi directions cut into mpifactor parts each) emulated on one
+// device.  A sublattice stores an extended box: extent l_d + 2 in a cut
+// direction (one ghost layer on each side, filled by the boundary exchange),
+// l_d = L_d otherwise (periodic wrap inside the sublattice).  Threads
+// enumerate the interior sites of one parity with the plain rule on the
+// interior extents; the global site (for the random numbers) is the
+// interior coordinate plus the sublattice origin.  Interior extents in cut
+// directions are even, so origins are even and local parity is global
+// parity.
+// ---------------------------------------------------------------------------
+struct SubGeometry {
+  Geometry in;         // interior extents (thread enumeration)
+  int e[4];            // extended extents
+  int he0;             // e0 / 2
+  int Vh;              // extended sites / 2: the storage stride
+  int cut;             // bit d set: direction d is cut (ghost layers)
+  int o[4];            // global coordinate of the interior origin
+  int L0, L1, L2;      // global extents for the canonical index
+};
+
+struct SubSite {
+  int y0, y1, y2, y3;  // extended-box coordinates
+  int r;               // y1 + e1*(y2 + e2*y3)
+  int s;               // global canonical index
+};
+
+__device__ __forceinline__ SubSite site_of(const SubGeometry& g, int h, int p) {
+  const Site t = site_of(g.in, h, p);
+  SubSite st;
+  const int c0 = g.cut & 1, c1 = (g.cut >> 1) & 1, c2 = (g.cut >> 2) & 1, c3 = (g.cut >> 3) & 1;
+  st.y0 = t.x0 + c0;
+  st.y1 = t.x1 + c1;
+  st.y2 = t.x2 + c2;
+  st.y3 = t.x3 + c3;
+  st.r = st.y1 + g.e[1] * (st.y2 + g.e[2] * st.y3);
+  st.s = (t.x0 + g.o[0]) + g.L0 * ((t.x1 + g.o[1]) + g.L1 * ((t.x2 + g.o[2]) + g.L2 * (t.x3 + g.o[3])));
+  return st;
+}
+
+__device__ __forceinline__ int canon(const SubGeometry&, const SubSite& s) { return s.s; }
+
+__device__ __forceinline__ int store_index(const SubGeometry& g, const SubSite& st, int) {
+  return (st.y0 >> 1) + g.he0 * st.r;
+}
+
+// Step d (+1 or -1) along nu: into the ghost layer in a cut direction,
+// periodic inside the sublattice otherwise.
+__device__ __forceinline__ int sub_step(const SubGeometry& g, int y, int nu, int d) {
+  y += d;
+  if (!((g.cut >> nu) & 1)) y = y < 0 ? y + g.e[nu] : (y >= g.e[nu] ? y - g.e[nu] : y);
+  return y;
+}
+
+__device__ __forceinline__ int sub_half(const SubGeometry& g, int y0, int y1, int y2, int y3) {
+  return (y0 >> 1) + g.he0 * (y1 + g.e[1] * (y2 + g.e[2] * y3));
+}
+
+__device__ __forceinline__ int nb_half(const SubGeometry& g, const SubSite& s, int nu, int d) {
+  int y[4] = {s.y0, s.y1, s.y2, s.y3};
+  y[nu] = sub_step(g, y[nu], nu, d);
+  return sub_half(g, y[0], y[1], y[2], y[3]);
+}
+
+__device__ __forceinline__ int nb_half2(const SubGeometry& g, const SubSite& s, int nu, int rho) {
+  int y[4] = {s.y0, s.y1, s.y2, s.y3};
+  y[nu] = sub_step(g, y[nu], nu, +1);
+  y[rho] = sub_step(g, y[rho], rho, -1);
+  return sub_half(g, y[0], y[1], y[2], y[3]);
+}
+
 // ---------------------------------------------------------------------------
 // Link loads and stores.
 // ---------------------------------------------------------------------------

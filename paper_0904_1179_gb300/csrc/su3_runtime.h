@@ -14,6 +14,7 @@ constexpr int kSu3DefaultThreads = 128;
 constexpr long long kChunkSites = 1LL << 16;
 
 struct su3_batch;
+struct su3_decomp;
 
 struct su3_lattice {
   int L[4] = {0, 0, 0, 0};
@@ -49,7 +50,8 @@ struct su3_lattice {
   int max_tries = 1;  // SU(2) proposals per subgroup (1: one-hit heatbath)
   su3dev::Geometry geom{};
   su3dev::PhiloxKey key{};
-  su3_batch* batch = nullptr;  // non-null for a batch of replicas
+  su3_batch* batch = nullptr;    // non-null for a batch of replicas
+  su3_decomp* decomp = nullptr;  // non-null for a decomposed lattice (su3_decomp_create)
 };
 
 // Record a failure for su3_last_error(); returns code.
@@ -67,6 +69,15 @@ void su3_release_handle(su3_lattice* h);
 void su3_batch_release(su3_batch* b);
 // Drop the batch's captured sweep graph (its parameters changed).
 void su3_batch_invalidate(su3_batch* b);
+// Decomposed lattices (defined in su3_decomp.cu).  The handle's global store
+// and the sublattice stores are kept in step lazily.
+bool su3_decomp_active(const su3_lattice* h);
+void su3_decomp_release(su3_decomp* d);
+void su3_decomp_invalidate(su3_decomp* d);
+int su3_decomp_sweep(su3_lattice* h, int nsweeps);
+int su3_decomp_half_sweep(su3_lattice* h, int mu, int parity);
+int su3_decomp_sync_global(su3_lattice* h);   // before reading the global store
+void su3_decomp_global_written(su3_lattice* h);  // after writing it
 // Largest number of SU(2) proposals per subgroup (the try index has 26 bits
 // in the Philox counter).
 constexpr int kMaxHeatbathTries = 1 << 20;

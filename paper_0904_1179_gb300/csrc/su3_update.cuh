@@ -58,8 +58,8 @@ struct Store<float, CG> {
 // Apart (optional): receives the sum of the terms with nu < MU.  After the
 // update, Re Tr(U_new Apart) is the sum of the plaquettes of the planes
 // (MU, nu < MU) at x and at x - nu-hat.
-template <typename T, int MU, bool CG>
-__device__ __forceinline__ mat3<T> staple(const Geometry& g, const void* U, const Site& st, int h, int p,
+template <typename T, int MU, bool CG, typename G, typename S>
+__device__ __forceinline__ mat3<T> staple(const G& g, const void* U, const S& st, int h, int p,
                                           mat3<T>* Apart = nullptr) {
   const int q = p ^ 1;
   mat3<T> A = zero3<T>();
@@ -160,12 +160,15 @@ struct UpdateCount {
 // ---------------------------------------------------------------------------
 // MEAS: also return in *meas (1/3) Re Tr(U_new A_<), A_< the staple terms of
 // the directions nu < MU (see staple()).
-template <int MU, bool CG, bool REPEAT, bool MEAS = false, typename KEY>
-__device__ __forceinline__ UpdateCount update_link_f64(const Geometry& g, double2* U, int h, int p, uint64_t t,
+// G: Geometry (periodic lattice) or SubGeometry (sublattice with ghost
+// layers); h enumerates the sites of parity p, hs is where the site is stored.
+template <int MU, bool CG, bool REPEAT, bool MEAS = false, typename KEY, typename G>
+__device__ __forceinline__ UpdateCount update_link_f64(const G& g, double2* U, int h, int p, uint64_t t,
                                                        const KEY& key, const UpdateConsts& uc, double* meas = nullptr) {
   UpdateCount cnt{0, 0};
-  const Site st = site_of(g, h, p);
+  const auto st = site_of(g, h, p);
   const uint32_t s = (uint32_t)canon(g, st);
+  h = store_index(g, st, h);
   mat3<double> Apart;
   const mat3<double> A = staple<double, MU, CG>(g, U, st, h, p, MEAS ? &Apart : nullptr);
   mat3<double> u = load_f64<CG>(U, MU, p, h, g.Vh);
@@ -237,8 +240,8 @@ __device__ __forceinline__ UpdateCount update_link_f64(const Geometry& g, double
 // SU(3) matrix, so rows 0,1 are multiplied out two rows at a time and row 2
 // is completed.
 // ---------------------------------------------------------------------------
-template <int MU, bool CG>
-__device__ __forceinline__ pm3 staple_p(const Geometry& g, const float4* U, const Site& st, int h, int p,
+template <int MU, bool CG, typename G, typename S>
+__device__ __forceinline__ pm3 staple_p(const G& g, const float4* U, const S& st, int h, int p,
                                         pm3* Apart = nullptr) {
   const int q = p ^ 1;
   pm3 A = zero_p();
@@ -287,12 +290,13 @@ __device__ __forceinline__ pm3 staple_p(const Geometry& g, const float4* U, cons
 // compensated FP32 sums of FP64-class accuracy (EFT = true).  REPEAT = false
 // compiles the one-hit heatbath without the retry loop.
 // ---------------------------------------------------------------------------
-template <int MU, bool CG, bool EFT, bool REPEAT, bool MEAS = false, typename KEY>
-__device__ __forceinline__ UpdateCount update_link_f32(const Geometry& g, float4* U, int h, int p, uint64_t t,
+template <int MU, bool CG, bool EFT, bool REPEAT, bool MEAS = false, typename KEY, typename G>
+__device__ __forceinline__ UpdateCount update_link_f32(const G& g, float4* U, int h, int p, uint64_t t,
                                                        const KEY& key, const UpdateConsts& uc, double* meas = nullptr) {
   UpdateCount cnt{0, 0};
-  const Site st = site_of(g, h, p);
+  const auto st = site_of(g, h, p);
   const uint32_t s = (uint32_t)canon(g, st);
+  h = store_index(g, st, h);
   pm3 Apart;
   const pm3 A = staple_p<MU, CG>(g, U, st, h, p, MEAS ? &Apart : nullptr);
   pm3 u = load_pm3<CG>(U, MU, p, h, g.Vh);

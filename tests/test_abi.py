@@ -76,6 +76,16 @@ def test_create_rejects_bad_enums(lib):
     assert lib.su3_create_ex(4, 4, 4, 4, 5.7, 1, 0, 0, None, None) == su3.SU3_EINVAL
 
 
+@pytest.mark.parametrize("args", [(0, 2, 1), (5, 2, 1), (1, 0, 1), (1, 2, 0), (3, 4, 1), (2, 3, 1), (1, 2, 2)])
+def test_decomp_create_rejects_bad_decompositions(lib, args):
+    # ndmpi out of range, mpifactor < 1, exchange off with several
+    # sublattices, parts of odd extent (12 / 4 = 3) or not dividing (8 / 3)
+    h = ctypes.c_void_p()
+    rc = lib.su3_decomp_create(8, 8, 12, 8, 5.7, 1, 0, 0, *args, None, ctypes.byref(h))
+    assert rc == su3.SU3_EINVAL and not h.value
+    assert "su3_decomp_create" in su3.su3_last_error()
+
+
 def test_null_handle_calls(lib):
     assert lib.su3_destroy(None) == su3.SU3_OK
     assert lib.su3_sweep(None, 1) == su3.SU3_EINVAL
