@@ -108,14 +108,16 @@ __device__ __forceinline__ uint4 rng_counter(uint32_t site, uint32_t w1, uint64_
 }
 
 // Uniform in [2^-53, 1-2^-53]: 52 bits (a<<20 | b>>12) centred in its bin.
+// Built from the bits: 1 + x 2^-52 is exact, and subtracting 1 - 2^-53 leaves
+// (x + 1/2) 2^-52 exactly (Sterbenz), without an integer-to-FP64 conversion.
 __device__ __forceinline__ double u01_f64(uint32_t a, uint32_t b) {
   const uint64_t x = ((uint64_t)a << 20) | (uint64_t)(b >> 12);
-  return ((double)x + 0.5) * 0x1p-52;
+  return __longlong_as_double((long long)(0x3FF0000000000000ull | x)) - (1.0 - 0x1p-53);
 }
 
 // Uniform in [2^-24, 1-2^-24]: 23 bits centred in the bin, exact in float.
 __device__ __forceinline__ float u01_f32(uint32_t a) {
-  return ((float)(a >> 9) + 0.5f) * 0x1p-23f;
+  return __int_as_float((int)(0x3F800000u | (a >> 9))) - (1.0f - 0x1p-24f);  // (m + 1/2) 2^-23, exact
 }
 
 // ---------------------------------------------------------------------------

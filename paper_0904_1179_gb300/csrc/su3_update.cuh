@@ -284,6 +284,14 @@ __device__ __forceinline__ pm3 staple_p(const G& g, const float4* U, const S& st
   return A;
 }
 
+// The hardware square root (about 1 ulp): the FP32 heatbath needs no
+// correctly rounded one.
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // ---------------------------------------------------------------------------
 // One FP32-mixed link update: FP32 storage (rows 0,1), FP32 staple and
 // heatbath, Gram-Schmidt coefficients in FP64 (EFT = false) or as
@@ -363,9 +371,9 @@ __device__ __forceinline__ UpdateCount update_link_f32(const G& g, float4* U, in
       const float delta = -(__logf(u0) + cc * cc * __logf(u2)) * ia;
       if (u3 * u3 > 1.0f - 0.5f * delta) continue;
       const float u4 = u01_f32(w1.x), u5 = u01_f32(w1.y);
-      const float rho = sqrtf(fmaxf(0.0f, delta * (2.0f - delta)));  // sqrt(1 - a0^2)
+      const float rho = sqrt_approx(fmaxf(0.0f, delta * (2.0f - delta)));  // sqrt(1 - a0^2)
       const float ct = 1.0f - 2.0f * u4;
-      const float sn = 2.0f * sqrtf(u4 * (1.0f - u4));  // sqrt(1 - ct^2)
+      const float sn = 2.0f * sqrt_approx(u4 * (1.0f - u4));  // sqrt(1 - ct^2)
       float sphi, cphi;
       __sincosf(fmaf(6.2831853f, u5, -3.14159265f), &sphi, &cphi);  // angle 2 pi u5 - pi
       const float rs = -rho * sn;                                     // undo the shift by pi
