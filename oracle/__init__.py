@@ -15,6 +15,7 @@ the oracle itself (``tests/test_oracle_pins.py``).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -36,51 +37,74 @@ _f64p = ctypes.POINTER(ctypes.c_double)
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile one oracle source file into a shared library (gcc, -O2, no FP contraction)."""
+    tmp = out + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-Wall", "-Wextra", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile su3_oracle.c into libsu3_oracle.so (gcc, -O2, no FP contraction)."""
+    """Compile su3_oracle.c into libsu3_oracle.so."""
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
-    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return compile_source(_SRC, _LIB_PATH)
+
+
+@contextlib.contextmanager
+def use_library(path):
+    """Route every wrapper of this module through another build of the oracle
+    (the mutation tests plant mistakes in copies of su3_oracle.c)."""
+    global _lib
+    with _lock:
+        saved = _lib
+        _lib = _bind(ctypes.CDLL(os.path.abspath(path)))
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = saved
 
 
 def _load():
     global _lib
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
-        lib.oracle_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
-        lib.oracle_philox4x32_10.restype = None
-        lib.oracle_u01_f64.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
-        lib.oracle_u01_f64.restype = ctypes.c_double
-        lib.oracle_u01_f32.argtypes = [ctypes.c_uint32]
-        lib.oracle_u01_f32.restype = ctypes.c_double
-        lib.oracle_cold_start.argtypes = [_i32p, _f64p]
-        lib.oracle_hot_start.argtypes = [_i32p, ctypes.c_uint64, ctypes.c_int, _f64p]
-        lib.oracle_plaquette.argtypes = [_i32p, _f64p, ctypes.c_int]
-        lib.oracle_plaquette.restype = ctypes.c_double
-        lib.oracle_staple.argtypes = [_i32p, _f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _f64p]
-        lib.oracle_half_sweep.argtypes = [_i32p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
-                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, _f64p, _u64p, ctypes.c_int]
-        lib.oracle_sweep.argtypes = [_i32p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
-                                     ctypes.c_int, _f64p, _u64p, _f64p, ctypes.c_int]
-        lib.oracle_update_links.argtypes = [_i32p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
-                                            _i64p, ctypes.c_int64, ctypes.c_int, _f64p, _u64p, ctypes.c_int]
-        lib.oracle_updated_links.argtypes = [_i32p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
-                                             ctypes.c_int, _i64p, ctypes.c_int64, ctypes.c_int, _f64p, _f64p, _f64p,
-                                             ctypes.c_int]
-        lib.oracle_gauge_transform.argtypes = [_i32p, ctypes.c_uint64, _f64p]
-        lib.oracle_kp_draws.argtypes = [ctypes.c_double, ctypes.c_uint64, ctypes.c_int64, _f64p, _u8p, ctypes.c_int,
-                                         _i64p]
-        lib.oracle_kp_draws.restype = ctypes.c_int64
-        _lib = lib
-        return lib
+        if _lib is None:
+            _lib = _bind(ctypes.CDLL(build()))
+        return _lib
+
+
+def _bind(lib):
+    """Declare the argument and result types of every exported oracle function."""
+    lib.oracle_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+    lib.oracle_philox4x32_10.restype = None
+    lib.oracle_u01_f64.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+    lib.oracle_u01_f64.restype = ctypes.c_double
+    lib.oracle_u01_f32.argtypes = [ctypes.c_uint32]
+    lib.oracle_u01_f32.restype = ctypes.c_double
+    lib.oracle_cold_start.argtypes = [_i32p, _f64p]
+    lib.oracle_hot_start.argtypes = [_i32p, ctypes.c_uint64, ctypes.c_int, _f64p]
+    lib.oracle_plaquette.argtypes = [_i32p, _f64p, ctypes.c_int]
+    lib.oracle_plaquette.restype = ctypes.c_double
+    lib.oracle_staple.argtypes = [_i32p, _f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _f64p]
+    lib.oracle_half_sweep.argtypes = [_i32p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, _f64p, _u64p, ctypes.c_int]
+    lib.oracle_sweep.argtypes = [_i32p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                 ctypes.c_int, _f64p, _u64p, _f64p, ctypes.c_int]
+    lib.oracle_update_links.argtypes = [_i32p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                        _i64p, ctypes.c_int64, ctypes.c_int, _f64p, _u64p, ctypes.c_int]
+    lib.oracle_updated_links.argtypes = [_i32p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
+                                         ctypes.c_int, _i64p, ctypes.c_int64, ctypes.c_int, _f64p, _f64p, _f64p,
+                                         ctypes.c_int]
+    lib.oracle_gauge_transform.argtypes = [_i32p, ctypes.c_uint64, _f64p]
+    lib.oracle_kp_draws.argtypes = [ctypes.c_double, ctypes.c_uint64, ctypes.c_int64, _f64p, _u8p, ctypes.c_int,
+                                     _i64p]
+    lib.oracle_kp_draws.restype = ctypes.c_int64
+    return lib
 
 
 def _dims(L):
