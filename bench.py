@@ -223,39 +223,119 @@ def time_e2e(su3, L, prec, steps, warmup, sweeps_per_step):
             "step": "su3_links_set(host) + %d sweeps + su3_plaquette + su3_links_get(host)" % sweeps_per_step}
 
 
+# --- the oracle on every host core -------------------------------------------
+# The links of one checkerboard half-sweep never enter each other's staples, so
+# disjoint site subsets of a half-sweep can be updated in place by separate
+# processes running the unchanged oracle.  The configuration lives in a
+# file-backed shared mapping; the pool is spawned (never forked).
+_POOL_U = None
+
+
+def _pool_attach(path, shape):
+    global _POOL_U
+    import numpy as np
+    _POOL_U = np.memmap(path, dtype=np.float64, mode="r+", shape=shape)
+
+
+def _pool_update(job):
+    import oracle
+    L, beta, seed, t, mu, sites = job
+    oracle.update_links(L, beta, seed, t, mu, sites, _POOL_U)
+    return len(sites)
+
+
+class OraclePool:
+    """The oracle's half-sweep split over `procs` spawned single-thread processes."""
+
+    def __init__(self, L, U0, procs=None):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        import tempfile
+        import numpy as np
+        self.L = tuple(L)
+        self.procs = procs or os.cpu_count() or 1
+        fd, self.path = tempfile.mkstemp(prefix="su3_oracle_links_", suffix=".bin")
+        os.close(fd)
+        U = np.memmap(self.path, dtype=np.float64, mode="w+", shape=U0.shape)
+        U[...] = U0
+        U.flush()
+        self.U = U
+        s = np.arange(int(np.prod(L)), dtype=np.int64)
+        x0 = s % L[0]
+        r = s // L[0]
+        par = (x0 + r % L[1] + (r // L[1]) % L[2] + r // (L[1] * L[2])) & 1
+        self.sites = [np.array_split(s[par == p], self.procs) for p in (0, 1)]
+        self.ex = cf.ProcessPoolExecutor(max_workers=self.procs, mp_context=mp.get_context("spawn"),
+                                         initializer=_pool_attach, initargs=(self.path, U0.shape))
+
+    def half_sweep(self, beta, seed, t, mu, p):
+        jobs = [(self.L, beta, seed, t, mu, c) for c in self.sites[p]]
+        return sum(self.ex.map(_pool_update, jobs))
+
+    def close(self):
+        self.ex.shutdown()
+        del self.U
+        os.remove(self.path)
+
+
 def cpu_baseline_sample(f32):
-    """The oracle as it stands (single thread) on one full sweep of the same 32^4 workload."""
+    """The oracle as it stands on the same 32^4 workload: on every host core (spawned
+    processes on disjoint site subsets of each half-sweep, two full sweeps), and on one
+    core (one full sweep)."""
     import oracle
     oracle.build()
     U = oracle.hot_start(DIMS, SEED, f32=f32)
+    pool = OraclePool(DIMS, U)
+    try:
+        pool.half_sweep(BETA, SEED, 0, 0, 0)  # start the workers, load the library
+        t0 = time.perf_counter()
+        n = 0
+        for t in range(1, 3):
+            for mu in range(4):
+                for p in range(2):
+                    n += pool.half_sweep(BETA, SEED, t, mu, p)
+        dt_all = time.perf_counter() - t0
+        procs = pool.procs
+    finally:
+        pool.close()
     t0 = time.perf_counter()
     oracle.sweep(DIMS, BETA, SEED, 0, 1, U, f32=f32)
     dt = time.perf_counter() - t0
-    ups = 4 * 32 ** 4 / dt
-    return {"value": ups, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one full sweep (4*32^4 link updates) of the 32^4 beta=5.7 hot-start lattice, %s, "
-                      "single thread, %.1f s" % ("FP32-mixed reading" if f32 else "FP64", dt),
-            "us_per_update": dt / (4 * 32 ** 4) * 1e6}
+    one = 4 * 32 ** 4 / dt
+    return {"value": n / dt_all, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": "two full sweeps (2*4*32^4 link updates) of the 32^4 beta=5.7 hot-start lattice, %s, "
+                      "%d single-thread processes on disjoint site subsets of each half-sweep, %.1f s"
+                      % ("FP32-mixed reading" if f32 else "FP64", procs, dt_all),
+            "one_core": {"value": one, "cores": 1, "us_per_update": dt / (4 * 32 ** 4) * 1e6,
+                         "sample": "one full sweep, single thread, %.1f s" % dt}}
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands on every host core (spawned
+    single-thread processes on disjoint site subsets); one step = one checkerboard
+    half-sweep of the 32^4 lattice."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return 0
     import oracle
     oracle.build()
-    U = oracle.hot_start(DIMS, SEED)
+    pool = OraclePool(DIMS, oracle.hot_start(DIMS, SEED))
     phases = [(mu, p) for mu in range(4) for p in range(2)]
-    for i in range(args.warmup):
-        mu, p = phases[i % 8]
-        oracle.half_sweep(DIMS, BETA, SEED, 0, mu, p, U)
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        mu, p = phases[(args.warmup + i) % 8]
-        oracle.half_sweep(DIMS, BETA, SEED, (args.warmup + i) // 8, mu, p, U)
-    dt = time.perf_counter() - t0
-    ups = 4 * 32 ** 4 / 8 * args.steps / dt
+    try:
+        for i in range(args.warmup):
+            mu, p = phases[i % 8]
+            pool.half_sweep(BETA, SEED, i // 8, mu, p)
+        t0 = time.perf_counter()
+        n = 0
+        for i in range(args.steps):
+            mu, p = phases[(args.warmup + i) % 8]
+            n += pool.half_sweep(BETA, SEED, (args.warmup + i) // 8, mu, p)
+        dt = time.perf_counter() - t0
+        procs = pool.procs
+    finally:
+        pool.close()
+    ups = n / dt
     line = {"impl": "reference", "metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": ups / PAPER_UPS, "dtype": "f64",
@@ -263,8 +343,9 @@ def run_reference(args):
             "config": {"workload": "32^4 beta=5.7 hot start seed 7, FP64 checkerboard heatbath; reference step = "
                                    "one half-sweep (V/2 link updates) of the FP64 CPU oracle",
                        "lattice": list(DIMS), "beta": BETA},
-            "cpu_baseline": {"value": ups, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "one checkerboard half-sweep of the 32^4 lattice per step, single thread"},
+            "cpu_baseline": {"value": ups, "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "sample": "one checkerboard half-sweep of the 32^4 lattice per step, %d single-thread "
+                                       "processes on disjoint site subsets" % procs},
             "e2e": {"value": ups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -414,32 +495,55 @@ def binned_mean(x, nbins=20):
     return float(b.mean()), float(b.std(ddof=1) / np.sqrt(nbins))
 
 
+def tau_int(x, c=6.0):
+    """Integrated autocorrelation time with the self-consistent window W >= c tau
+    (Madras and Sokal, J. Stat. Phys. 50 (1988) 109), from the FFT autocovariance."""
+    import numpy as np
+    x = np.asarray(x, dtype=np.float64) - np.mean(x)
+    n = x.size
+    f = np.fft.rfft(x, 2 * n)
+    acf = np.fft.irfft(f * np.conj(f))[:n] / np.arange(n, 0, -1)
+    acf /= acf[0]
+    tau = 0.5
+    for w in range(1, n // 4):
+        tau += acf[w]
+        if w >= c * tau:
+            break
+    return float(tau)
+
+
 def run_chains(args):
     """Plaquette chains of the precision study: 32^4 and 48^4 at beta 5.7 and 6.0, hot start,
-    200 thermalisation + 1000 measured sweeps with the plaquette after every sweep, in FP64,
-    FP32-mixed and FP32-EFT from the same Philox seed; prints one JSON line per (lattice, beta)
-    with binned means, errors and the deviations of the FP32 chains from the FP64 chain."""
+    thermalisation then measured sweeps with the plaquette after every sweep (fused into the
+    sweep), in FP64, FP32-mixed and FP32-EFT from the same Philox seed; prints one JSON line
+    per (lattice, beta) with the means, errors from 20 bins (each bin many autocorrelation
+    times long), the integrated autocorrelation time, and the deviations of the FP32 chains
+    from the FP64 chain."""
+    import numpy as np
     import paper_0904_1179_gb300 as su3
     cases = [((32, 32, 32, 32), 5.7), ((32, 32, 32, 32), 6.0), ((48, 48, 48, 48), 5.7), ((48, 48, 48, 48), 6.0)]
     if args.chains_small:
         cases = [((8, 8, 8, 8), 5.7)]
-    ntherm, nmeas = args.chains_therm, args.chains_meas
     precs = [("fp64", su3.SU3_FP64), ("fp32_mixed", su3.SU3_FP32_MIXED), ("fp32_eft", su3.SU3_FP32_EFT)]
     for L, beta in cases:
+        big = int(np.prod(L)) > 32 ** 4
+        ntherm = args.chains_therm if not big else max(args.chains_therm * 3 // 5, 1)
+        nmeas = args.chains_meas if not big else max(args.chains_meas * 5 // 16, 20)
         res = {}
         for name, prec in precs:
             t0 = time.perf_counter()
             with su3.Lattice(L, beta, 11, start=su3.SU3_HOT, precision=prec) as lat:
                 lat.sweep(ntherm)
-                plaq = []
-                for _ in range(nmeas):
-                    lat.sweep(1)
-                    plaq.append(lat.plaquette())
+                plaq = lat.sweep_measured(nmeas)
                 lat.set_stats(True)
                 lat.sweep(10)
                 acc, prop = lat.stats()
             m, e = binned_mean(plaq)
-            res[name] = {"mean": m, "err": e, "acceptance": acc / prop, "seconds": time.perf_counter() - t0}
+            _, e40 = binned_mean(plaq, 40)
+            tau = tau_int(plaq)
+            res[name] = {"mean": m, "err": e, "err_40bins": e40, "tau_int": tau,
+                         "err_tau": float(np.std(plaq, ddof=1) * np.sqrt(2 * tau / len(plaq))),
+                         "acceptance": acc / prop, "seconds": time.perf_counter() - t0}
         out = {"chains": True, "lattice": list(L), "beta": beta, "therm": ntherm, "measured": nmeas, "seed": 11,
                "start": "hot", "bins": 20, **res}
         for name in ("fp32_mixed", "fp32_eft"):
@@ -582,8 +686,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--chains", action="store_true", help="precision study: FP64 vs FP32 plaquette chains")
     ap.add_argument("--chains-small", action="store_true", help="one small chain (8^4) instead of 32^4/48^4")
-    ap.add_argument("--chains-therm", type=int, default=200)
-    ap.add_argument("--chains-meas", type=int, default=1000)
+    ap.add_argument("--chains-therm", type=int, default=500, help="thermalisation sweeps (48^4: 3/5 of it)")
+    ap.add_argument("--chains-meas", type=int, default=8000, help="measured sweeps (48^4: 5/16 of it)")
     ap.add_argument("--large", action="store_true", help="64^4 beta 6.0, FP64 vs FP32-mixed")
     ap.add_argument("--decomp", action="store_true",
                     help="Table 1's rows on one GPU: the domain decomposition emulated, exchange cost measured")
