@@ -424,6 +424,12 @@ def run_profile_case(case):
             p = b.plaquettes()
         print(json.dumps({"profile_case": case, "replicas": len(dims), "sweeps": 3, "plaquette_0": p[0]}))
         return 0
+    if case == "decomp16":
+        with su3.Lattice(DIMS, BETA, SEED, start=su3.SU3_HOT, precision=su3.SU3_FP32_MIXED, decomp=(4, 2, 1)) as lat:
+            lat.sweep(3)
+            print(json.dumps({"profile_case": case, "lattice": list(DIMS), "decomp": [4, 2, 1],
+                              "halo_links_per_sweep": lat.decomp_info()[4], "plaquette": lat.plaquette()}))
+        return 0
     dims, beta = (DIMS, BETA)
     if case.endswith("_64"):
         dims, beta, case = (64, 64, 64, 64), 6.0, case[:-3]
@@ -524,6 +530,10 @@ def run_chains(args):
     cases = [((32, 32, 32, 32), 5.7), ((32, 32, 32, 32), 6.0), ((48, 48, 48, 48), 5.7), ((48, 48, 48, 48), 6.0)]
     if args.chains_small:
         cases = [((8, 8, 8, 8), 5.7)]
+    if args.chains_case:
+        ext, b = args.chains_case.split(":")
+        cases = [((int(ext),) * 4, float(b))]
+    seed = args.chains_seed
     precs = [("fp64", su3.SU3_FP64), ("fp32_mixed", su3.SU3_FP32_MIXED), ("fp32_eft", su3.SU3_FP32_EFT)]
     for L, beta in cases:
         big = int(np.prod(L)) > 32 ** 4
@@ -532,7 +542,7 @@ def run_chains(args):
         res = {}
         for name, prec in precs:
             t0 = time.perf_counter()
-            with su3.Lattice(L, beta, 11, start=su3.SU3_HOT, precision=prec) as lat:
+            with su3.Lattice(L, beta, seed, start=su3.SU3_HOT, precision=prec) as lat:
                 lat.sweep(ntherm)
                 plaq = lat.sweep_measured(nmeas)
                 lat.set_stats(True)
@@ -544,7 +554,7 @@ def run_chains(args):
             res[name] = {"mean": m, "err": e, "err_40bins": e40, "tau_int": tau,
                          "err_tau": float(np.std(plaq, ddof=1) * np.sqrt(2 * tau / len(plaq))),
                          "acceptance": acc / prop, "seconds": time.perf_counter() - t0}
-        out = {"chains": True, "lattice": list(L), "beta": beta, "therm": ntherm, "measured": nmeas, "seed": 11,
+        out = {"chains": True, "lattice": list(L), "beta": beta, "therm": ntherm, "measured": nmeas, "seed": seed,
                "start": "hot", "bins": 20, **res}
         for name in ("fp32_mixed", "fp32_eft"):
             d = res[name]["mean"] - res["fp64"]["mean"]
@@ -686,6 +696,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--chains", action="store_true", help="precision study: FP64 vs FP32 plaquette chains")
     ap.add_argument("--chains-small", action="store_true", help="one small chain (8^4) instead of 32^4/48^4")
+    ap.add_argument("--chains-seed", type=int, default=11)
+    ap.add_argument("--chains-case", help="one case only, extent:beta, e.g. 48:5.7")
     ap.add_argument("--chains-therm", type=int, default=500, help="thermalisation sweeps (48^4: 3/5 of it)")
     ap.add_argument("--chains-meas", type=int, default=8000, help="measured sweeps (48^4: 5/16 of it)")
     ap.add_argument("--large", action="store_true", help="64^4 beta 6.0, FP64 vs FP32-mixed")
@@ -694,7 +706,7 @@ def main():
     ap.add_argument("--table1", action="store_true",
                     help="the paper's Table 1 columns in full (FP64 and FP32-mixed), with the oracle beside them")
     ap.add_argument("--large-sweeps", type=int, default=100)
-    ap.add_argument("--profile", choices=["fp64", "fp32_mixed", "fp32_eft", "batched", "fp64_64", "fp32_mixed_64"],
+    ap.add_argument("--profile", choices=["fp64", "fp32_mixed", "fp32_eft", "batched", "fp64_64", "fp32_mixed_64", "decomp16"],
                     help="small case for ncu: create the 32^4 lattice (or the 96-replica batch) and run 3 graphed "
                          "sweeps, nothing else")
     args = ap.parse_args()

@@ -169,9 +169,11 @@ SU3_API int su3_set_heatbath(su3_handle h, int max_tries);
 SU3_API int su3_info(su3_handle h, int dims[4], double* beta, uint64_t* seed, int* precision);
 
 /* Threads per block of the half-sweep kernels (a multiple of 32 in
- * [32, 256]); 0 restores the default.  Results do not depend on it: every
- * link update is independent inside a half-sweep and its random numbers are
- * keyed by its site. */
+ * [32, 256]); 0 restores the default: 128, halved (down to 32) while a
+ * half-sweep would have fewer blocks than the GPU has SMs, so that the links
+ * of a small lattice spread over as many SMs as possible.  Results do not
+ * depend on it: every link update is independent inside a half-sweep and its
+ * random numbers are keyed by its site. */
 SU3_API int su3_set_block_size(su3_handle h, int threads);
 
 /* ---------------------------------------------------------------------------

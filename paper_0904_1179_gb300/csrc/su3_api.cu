@@ -53,6 +53,22 @@ int cuda_fail(cudaError_t e, const char* what) { return su3_cuda_fail(e, what); 
 
 constexpr int kDefaultThreads = kSu3DefaultThreads;
 
+// Default block size for a half-sweep of Vh links: 128 threads, fewer (down
+// to one warp) when that would leave SMs idle, so that a small lattice's
+// links spread over as many SMs as there are warps (each link's update is a
+// long serial chain, and on the FP64 pipe a few warps saturate an SM).
+int default_threads(int Vh) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms <= 0) {
+    cudaGetLastError();
+    return kDefaultThreads;
+  }
+  int t = kDefaultThreads;
+  while (t > 32 && (Vh + t - 1) / t < sms) t /= 2;
+  return t;
+}
+
 }  // namespace
 
 namespace {
@@ -255,6 +271,7 @@ int su3_create_ex(int L0, int L1, int L2, int L3, double beta, uint64_t seed, in
   h->geom.s3 = L0 * L1 * L2;
   h->key.k0 = (uint32_t)seed;
   h->key.k1 = (uint32_t)(seed >> 32);
+  h->threads = default_threads(h->geom.Vh);
 
   cudaError_t e;
   if (cuda_stream) {
@@ -473,7 +490,7 @@ int su3_set_heatbath(su3_handle h, int max_tries) {
 int su3_set_block_size(su3_handle h, int threads) {
   if (!h) return fail(SU3_EINVAL, "su3_set_block_size: NULL handle");
   if (is_batch(h)) return fail(SU3_EINVAL, "su3_set_block_size: batch handle (use the su3_batch_* calls)");
-  if (threads == 0) threads = kDefaultThreads;
+  if (threads == 0) threads = default_threads(h->geom.Vh);
   if (threads < 32 || threads > kMaxSweepThreads || (threads & 31))
     return fail(SU3_EINVAL, "su3_set_block_size: %d is not a multiple of 32 in [32, %d]", threads, kMaxSweepThreads);
   if (threads != h->threads) {
