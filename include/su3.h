@@ -206,6 +206,15 @@ SU3_API int su3_set_block_size(su3_handle h, int threads);
 SU3_API int su3_decomp_create(int L0, int L1, int L2, int L3, double beta, uint64_t seed, int start, int precision,
                               int ndmpi, int mpifactor, int lbcex, void* cuda_stream, su3_handle* out);
 
+/* Plan a decomposition without a GPU (host computation only): validates the
+ * arguments exactly as su3_decomp_create does and returns the number of
+ * sublattices and the links the boundary exchange copies per sweep (every
+ * ghost cell a staple reads -- faces of the cut directions and the x + a - b
+ * edges -- refreshed for its four directions once per sweep; 0 with the
+ * exchange off).  Pointers may be NULL.  Errors: SU3_EINVAL. */
+SU3_API int su3_decomp_plan(int L0, int L1, int L2, int L3, int ndmpi, int mpifactor, int lbcex, int* nsub,
+                            long long* halo_links_per_sweep);
+
 /* Decomposition of a handle (any pointer may be NULL): ndmpi, mpifactor,
  * lbcex, the number of sublattices, and the links the boundary exchange
  * copies per sweep.  A handle from su3_create reports 0, 1, 0, 1, 0. */

@@ -19,7 +19,7 @@ import numpy as np
 __all__ = [
     "SU3_COLD", "SU3_HOT", "SU3_FP64", "SU3_FP32_MIXED", "SU3_FP32_EFT", "Su3Error", "load_library", "library_path",
     "su3_create", "su3_create_ex", "su3_destroy", "su3_sweep", "su3_sweep_measured", "su3_half_sweep", "su3_plaquette",
-    "su3_decomp_create", "su3_decomp_info",
+    "su3_decomp_create", "su3_decomp_plan", "su3_decomp_info",
     "su3_links_get", "su3_links_set", "su3_sweep_count", "su3_set_sweep_count", "su3_set_stats", "su3_stats",
     "su3_info", "su3_set_block_size", "su3_set_heatbath", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
     "su3_batch_links_get", "su3_batch_links_set", "su3_batch_size", "su3_batch_config", "su3_batch_get_config",
@@ -54,6 +54,8 @@ EXPORTS = [
     ("su3_decomp_create", ctypes.c_int, [ctypes.c_int] * 4 + [ctypes.c_double, _u64, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.POINTER(_h)]),
+    ("su3_decomp_plan", ctypes.c_int, [ctypes.c_int] * 7 + [ctypes.POINTER(ctypes.c_int),
+                                                           ctypes.POINTER(ctypes.c_longlong)]),
     ("su3_decomp_info", ctypes.c_int, [_h, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_longlong)]),
@@ -147,6 +149,15 @@ def su3_decomp_create(L0, L1, L2, L3, beta, seed, start, precision, ndmpi, mpifa
     _check(load_library().su3_decomp_create(L0, L1, L2, L3, beta, seed, start, precision, ndmpi, mpifactor, lbcex,
                                             ctypes.c_void_p(cuda_stream or None), ctypes.byref(h)))
     return h
+
+
+def su3_decomp_plan(L, ndmpi, mpifactor, lbcex=1):
+    """(number of sublattices, links copied by the exchange per sweep), computed on the host."""
+    n = ctypes.c_int()
+    halo = ctypes.c_longlong()
+    _check(load_library().su3_decomp_plan(*[int(x) for x in L], int(ndmpi), int(mpifactor), int(lbcex),
+                                          ctypes.byref(n), ctypes.byref(halo)))
+    return n.value, halo.value
 
 
 def su3_decomp_info(h):

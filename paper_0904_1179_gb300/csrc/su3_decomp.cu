@@ -283,15 +283,14 @@ int ensure_decomp_graph(su3_lattice* h) {
 // Gather lists of the boundary exchange.  A ghost cell is read by a staple if
 // exactly one cut coordinate lies outside the interior (a face: x +- nu), or
 // two do with one above and one below (an edge: x + mu - nu).
-void build_ghost_lists(const su3_lattice* h, const su3_decomp* d, std::vector<int4> lists[2]) {
-  const SubGeometry& g = d->geo;
+void build_ghost_lists(const int L[4], int ndmpi, int nf, int np, const SubGeometry& g, std::vector<int4> lists[2]) {
   const int* e = g.e;
   const int l[4] = {g.in.L0, g.in.L1, g.in.L2, g.in.L3};
-  for (int k = 0; k < d->np; ++k) {
+  for (int k = 0; k < np; ++k) {
     int o[4] = {0, 0, 0, 0}, kk = k;
-    for (int dd = 0; dd < d->ndmpi; ++dd) {
-      o[dd] = (kk % d->nf) * l[dd];
-      kk /= d->nf;
+    for (int dd = 0; dd < ndmpi; ++dd) {
+      o[dd] = (kk % nf) * l[dd];
+      kk /= nf;
     }
     for (int y3 = 0; y3 < e[3]; ++y3)
       for (int y2 = 0; y2 < e[2]; ++y2)
@@ -309,11 +308,11 @@ void build_ghost_lists(const su3_lattice* h, const su3_decomp* d, std::vector<in
             int x[4], ys[4], ksrc = 0, mul = 1, par = 0;
             for (int dd = 0; dd < 4; ++dd) {
               const int c = (g.cut >> dd) & 1;
-              x[dd] = ((y[dd] - c + o[dd]) % h->L[dd] + h->L[dd]) % h->L[dd];
+              x[dd] = ((y[dd] - c + o[dd]) % L[dd] + L[dd]) % L[dd];
               par += x[dd];
               if (c) {
                 ksrc += (x[dd] / l[dd]) * mul;
-                mul *= d->nf;
+                mul *= nf;
                 ys[dd] = x[dd] % l[dd] + 1;
               } else {
                 ys[dd] = x[dd];
@@ -324,6 +323,54 @@ void build_ghost_lists(const su3_lattice* h, const su3_decomp* d, std::vector<in
             lists[par & 1].push_back(make_int4(k, dst, ksrc, src));
           }
   }
+}
+
+int check_decomposition(const char* fn, const int L[4], int ndmpi, int mpifactor, int lbcex, long long* np) {
+  if (ndmpi < 1 || ndmpi > 4) return su3_fail(SU3_EINVAL, "%s: ndmpi %d not in [1, 4]", fn, ndmpi);
+  if (mpifactor < 1) return su3_fail(SU3_EINVAL, "%s: mpifactor %d < 1", fn, mpifactor);
+  if (lbcex != 0 && lbcex != 1) return su3_fail(SU3_EINVAL, "%s: lbcex must be 0 or 1", fn);
+  if (!lbcex && mpifactor > 1)
+    return su3_fail(SU3_EINVAL, "%s: the exchange can be off only for one sublattice (mpifactor 1)", fn);
+  for (int d = 0; d < 4; ++d)
+    if (L[d] < 2 || (L[d] & 1)) return su3_fail(SU3_EINVAL, "%s: extent L%d = %d must be even and >= 2", fn, d, L[d]);
+  if (4LL * L[0] * L[1] * L[2] * L[3] > 0x7fffffffLL) return su3_fail(SU3_EINVAL, "%s: 4*V exceeds 2^31-1", fn);
+  for (int d = 0; d < ndmpi; ++d)
+    if (L[d] % mpifactor || (L[d] / mpifactor) % 2 || L[d] / mpifactor < 2)
+      return su3_fail(SU3_EINVAL, "%s: L%d = %d does not split into %d even parts >= 2", fn, d, L[d], mpifactor);
+  *np = 1;
+  for (int d = 0; d < ndmpi; ++d) *np *= mpifactor;
+  if (*np > 65535) return su3_fail(SU3_EINVAL, "%s: %lld sublattices (at most 65535)", fn, *np);
+  return SU3_OK;
+}
+
+// Sublattice geometry (origin 0): interior extents L/mpifactor in the cut
+// directions, one ghost layer on each side of them.
+void host_sub_geometry(const int L[4], int ndmpi, int mpifactor, SubGeometry& g) {
+  int l[4];
+  long long ext = 1;
+  g.cut = 0;
+  for (int dd = 0; dd < 4; ++dd) {
+    const bool cut = dd < ndmpi;
+    l[dd] = cut ? L[dd] / mpifactor : L[dd];
+    g.e[dd] = l[dd] + (cut ? 2 : 0);
+    g.o[dd] = 0;
+    if (cut) g.cut |= 1 << dd;
+    ext *= g.e[dd];
+  }
+  g.in.L0 = l[0];
+  g.in.L1 = l[1];
+  g.in.L2 = l[2];
+  g.in.L3 = l[3];
+  g.in.hL0 = l[0] / 2;
+  g.in.Vh = (int)((long long)l[0] * l[1] * l[2] * l[3] / 2);
+  g.in.s1 = l[0];
+  g.in.s2 = l[0] * l[1];
+  g.in.s3 = l[0] * l[1] * l[2];
+  g.he0 = g.e[0] / 2;
+  g.L0 = L[0];
+  g.L1 = L[1];
+  g.L2 = L[2];
+  g.Vh = (int)(ext / 2);
 }
 
 }  // namespace
@@ -393,21 +440,12 @@ int su3_decomp_create(int L0, int L1, int L2, int L3, double beta, uint64_t seed
   if (!out) return su3_fail(SU3_EINVAL, "su3_decomp_create: out is NULL");
   *out = nullptr;
   const int L[4] = {L0, L1, L2, L3};
-  if (ndmpi < 1 || ndmpi > 4) return su3_fail(SU3_EINVAL, "su3_decomp_create: ndmpi %d not in [1, 4]", ndmpi);
-  if (mpifactor < 1) return su3_fail(SU3_EINVAL, "su3_decomp_create: mpifactor %d < 1", mpifactor);
-  if (lbcex != 0 && lbcex != 1) return su3_fail(SU3_EINVAL, "su3_decomp_create: lbcex must be 0 or 1");
-  if (!lbcex && mpifactor > 1)
-    return su3_fail(SU3_EINVAL, "su3_decomp_create: the exchange can be off only for one sublattice (mpifactor 1)");
-  for (int d = 0; d < ndmpi; ++d)
-    if (L[d] % mpifactor || (L[d] / mpifactor) % 2 || L[d] / mpifactor < 2)
-      return su3_fail(SU3_EINVAL, "su3_decomp_create: L%d = %d does not split into %d even parts >= 2", d, L[d],
-                      mpifactor);
   long long np = 1;
-  for (int d = 0; d < ndmpi; ++d) np *= mpifactor;
-  if (np > 65535) return su3_fail(SU3_EINVAL, "su3_decomp_create: %lld sublattices (at most 65535)", np);
+  int rc = check_decomposition("su3_decomp_create", L, ndmpi, mpifactor, lbcex, &np);
+  if (rc != SU3_OK) return rc;
 
   su3_handle h = nullptr;
-  int rc = su3_create_ex(L0, L1, L2, L3, beta, seed, start, precision, cuda_stream, &h);
+  rc = su3_create_ex(L0, L1, L2, L3, beta, seed, start, precision, cuda_stream, &h);
   if (rc != SU3_OK) return rc;
   su3_decomp* d = new (std::nothrow) su3_decomp;
   if (!d) {
@@ -425,36 +463,12 @@ int su3_decomp_create(int L0, int L1, int L2, int L3, double beta, uint64_t seed
     return SU3_OK;
   }
   SubGeometry& g = d->geo;
-  int l[4];
-  long long ext = 1;
-  g.cut = 0;
-  for (int dd = 0; dd < 4; ++dd) {
-    const bool cut = dd < ndmpi;
-    l[dd] = cut ? L[dd] / mpifactor : L[dd];
-    g.e[dd] = l[dd] + (cut ? 2 : 0);
-    g.o[dd] = 0;
-    if (cut) g.cut |= 1 << dd;
-    ext *= g.e[dd];
-  }
-  g.in.L0 = l[0];
-  g.in.L1 = l[1];
-  g.in.L2 = l[2];
-  g.in.L3 = l[3];
-  g.in.hL0 = l[0] / 2;
-  g.in.Vh = (int)((long long)l[0] * l[1] * l[2] * l[3] / 2);
-  g.in.s1 = l[0];
-  g.in.s2 = l[0] * l[1];
-  g.in.s3 = l[0] * l[1] * l[2];
-  g.he0 = g.e[0] / 2;
-  g.L0 = L0;
-  g.L1 = L1;
-  g.L2 = L2;
-  g.Vh = (int)(ext / 2);
+  host_sub_geometry(L, ndmpi, mpifactor, g);
   const int ncomp = precision == SU3_FP64 ? kEntriesF64 : kGroupsF32;
   const size_t elem = precision == SU3_FP64 ? sizeof(double2) : sizeof(float4);
   d->sub_elems = (size_t)8 * ncomp * g.Vh;
   std::vector<int4> lists[2];
-  build_ghost_lists(h, d, lists);
+  build_ghost_lists(L, ndmpi, mpifactor, d->np, g, lists);
   cudaError_t e = cudaMalloc(&d->d_sub, d->sub_elems * elem * np);
   for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
     d->nghost[p] = (int)lists[p].size();
@@ -474,6 +488,25 @@ int su3_decomp_create(int L0, int L1, int L2, int L3, double beta, uint64_t seed
   d->subs_current = false;
   d->global_current = true;
   *out = h;
+  return SU3_OK;
+}
+
+int su3_decomp_plan(int L0, int L1, int L2, int L3, int ndmpi, int mpifactor, int lbcex, int* nsub,
+                    long long* halo_links_per_sweep) {
+  const int L[4] = {L0, L1, L2, L3};
+  long long np = 1;
+  const int rc = check_decomposition("su3_decomp_plan", L, ndmpi, mpifactor, lbcex, &np);
+  if (rc != SU3_OK) return rc;
+  long long halo = 0;
+  if (lbcex) {
+    SubGeometry g{};
+    host_sub_geometry(L, ndmpi, mpifactor, g);
+    std::vector<int4> lists[2];
+    build_ghost_lists(L, ndmpi, mpifactor, (int)np, g, lists);
+    halo = 4LL * (long long)(lists[0].size() + lists[1].size());
+  }
+  if (nsub) *nsub = (int)np;
+  if (halo_links_per_sweep) *halo_links_per_sweep = halo;
   return SU3_OK;
 }
 

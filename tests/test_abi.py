@@ -7,6 +7,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 import paper_0904_1179_gb300 as su3
@@ -106,3 +107,28 @@ def test_binding_has_no_fallback_and_no_oracle():
             if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in text and "su3_oracle" not in text, fn
+
+
+def _halo_sites(L, nd, nf):
+    """Ghost cells the staples read: both faces of every cut direction and the
+    x + a - b edge of every ordered pair of cut directions, per sublattice."""
+    l = [L[d] // nf if d < nd else L[d] for d in range(4)]
+    vol = int(np.prod(l))
+    faces = sum(2 * vol // l[d] for d in range(nd))
+    edges = sum(vol // (l[a] * l[b]) for a in range(nd) for b in range(nd) if a != b)
+    return (faces + edges) * nf ** nd
+
+
+@pytest.mark.parametrize("L", [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (8, 4, 12, 8), (32, 32, 32, 32)])
+def test_decomp_plan_matches_closed_form(lib, L):
+    # host-only: the gather lists of the boundary exchange, counted
+    for nd in range(1, 5):
+        for nf in (1, 2, 4):
+            if any(L[d] % nf or (L[d] // nf) % 2 for d in range(nd)):
+                with pytest.raises(su3.Su3Error):
+                    su3.su3_decomp_plan(L, nd, nf)
+                continue
+            nsub, halo = su3.su3_decomp_plan(L, nd, nf)
+            assert nsub == nf ** nd
+            assert halo == 4 * _halo_sites(L, nd, nf), (L, nd, nf)
+    assert su3.su3_decomp_plan(L, 1, 1, 0) == (1, 0)
