@@ -285,19 +285,6 @@ __device__ __forceinline__ int nb_half(const Geometry& g, const Site& s, int nu,
   return (x0 >> 1) + g.hL0 * r;
 }
 
-__device__ __forceinline__ int wrap_step(int x, int d, int L) {
-  x += d;
-  return x < 0 ? x + L : (x >= L ? x - L : x);
-}
-// x + nu-hat - rho-hat with nu, rho known only at run time (no indexed arrays).
-__device__ __forceinline__ int nb_half2_rt(const Geometry& g, const Site& s, int nu, int rho) {
-  const int x0 = wrap_step(s.x0, (nu == 0) - (rho == 0), g.L0);
-  const int x1 = wrap_step(s.x1, (nu == 1) - (rho == 1), g.L1);
-  const int x2 = wrap_step(s.x2, (nu == 2) - (rho == 2), g.L2);
-  const int x3 = wrap_step(s.x3, (nu == 3) - (rho == 3), g.L3);
-  return (x0 >> 1) + g.hL0 * (x1 + g.L1 * (x2 + g.L2 * x3));
-}
-
 // Half index of x + nu-hat - rho-hat for nu != rho.
 __device__ __forceinline__ int nb_half2(const Geometry& g, const Site& s, int nu, int rho) {
   Site t = s;

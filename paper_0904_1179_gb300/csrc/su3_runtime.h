@@ -11,10 +11,7 @@
 // Threads per block of the half-sweep kernels unless set otherwise.
 constexpr int kSu3DefaultThreads = 128;
 // Sites per chunk of the canonical-layout staging buffer (37.7 MB of FP64 links).
-#ifndef SU3_CHUNK_LOG2
-#define SU3_CHUNK_LOG2 16
-#endif
-constexpr long long kChunkSites = 1LL << SU3_CHUNK_LOG2;
+constexpr long long kChunkSites = 1LL << 16;
 
 struct su3_batch;
 struct su3_decomp;

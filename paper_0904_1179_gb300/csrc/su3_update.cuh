@@ -240,30 +240,18 @@ __device__ __forceinline__ UpdateCount update_link_f64(const G& g, double2* U, i
 // SU(3) matrix, so rows 0,1 are multiplied out two rows at a time and row 2
 // is completed.
 // ---------------------------------------------------------------------------
-#ifndef SU3_NU_UNROLL
-#define SU3_NU_UNROLL 4
-#endif
-
 template <int MU, bool CG, typename G, typename S>
 __device__ __forceinline__ pm3 staple_p(const G& g, const float4* U, const S& st, int h, int p,
                                         pm3* Apart = nullptr) {
   const int q = p ^ 1;
   pm3 A = zero_p();
   const int h_pmu = nb_half(g, st, MU, +1);
-#if SU3_NU_UNROLL == 1
-#pragma unroll 1
-#else
 #pragma unroll
-#endif
   for (int nu = 0; nu < 4; ++nu) {
     if (nu == MU) continue;
     const int h_pnu = nb_half(g, st, nu, +1);
     const int h_mnu = nb_half(g, st, nu, -1);
-#if SU3_NU_UNROLL == 1
-    const int h_pmu_mnu = nb_half2_rt(g, st, MU, nu);
-#else
     const int h_pmu_mnu = nb_half2(g, st, MU, nu);
-#endif
     {
       const pm3 a = load_pm3<CG>(U, nu, q, h_pmu, g.Vh);  // U_nu(x+mu)
       pm3 b = load_pm3<CG>(U, MU, q, h_pnu, g.Vh);        // U_mu(x+nu)
