@@ -333,6 +333,47 @@ def test_full_size_32x4_sampled(prec):
         assert unit < (5e-7 if f32 else 1e-13) and det < (5e-7 if f32 else 1e-13)
 
 
+def tiled_config(tile, reps, seed, f32):
+    """An oracle hot start on a small lattice, repeated periodically: a seeded
+    non-trivial configuration of a large lattice without generating every
+    link.  Neighbour wraps of the large lattice still meet different links."""
+    Ut = oracle.hot_start(tile, seed, f32=f32)
+    return np.ascontiguousarray(np.tile(Ut, (reps, reps, reps, reps, 1, 1, 1, 1)))
+
+
+@pytest.mark.parametrize("L,beta,tile", [((48, 48, 48, 48), 5.7, (12, 12, 12, 12)),
+                                         ((64, 64, 64, 64), 6.0, (8, 8, 8, 8))])
+def test_large_lattices_sampled(L, beta, tile):
+    # the precision study's 48^4 and the large-lattice 64^4 workloads at full
+    # size: sampled updated links of two half-sweeps against the oracle
+    reps = L[0] // tile[0]
+    rng = np.random.default_rng(5)
+    for prec in (su3.SU3_FP64, su3.SU3_FP32_MIXED):
+        f32 = prec != su3.SU3_FP64
+        U0 = tiled_config(tile, reps, 21, f32)
+        with su3.Lattice(L, beta, 7, start=su3.SU3_COLD, precision=prec) as lat:
+            for mu, p in ((2, 1), (3, 0)):
+                lat.set_links(U0)
+                lat.sweep_count = 5
+                lat.half_sweep(mu, p)
+                G = flat_links(lat.get_links())
+                # sites on the wrap of every direction, and random ones
+                edge = [s for s in (0, np.prod(L) - 1, L[0] - 1, L[0] * L[1] * L[2] * (L[3] - 1))
+                        if (lambda x: sum(x) % 2)(np.unravel_index(s, L[::-1])) == p]
+                sites = np.concatenate([edge, rng.choice(site_list(L, p), size=300, replace=False)]).astype(np.int64)
+                O, marg = oracle.updated_links(L, beta, 7, 5, mu, sites, U0, f32=f32, with_margins=True)
+                d = np.abs(G[sites, mu] - O).max(axis=(1, 2, 3))
+                if f32:
+                    bad = d > F32_TOL
+                    assert bad.sum() <= 1
+                    if bad.any():
+                        assert (np.nanmin(np.abs(marg[bad]), axis=1) < F32_MARGIN).all()
+                else:
+                    assert d.max() < F64_TOL, d.max()
+                del G
+        del U0
+
+
 # ---------------------------------------------------------------------------
 # statistical agreement over long chains
 # ---------------------------------------------------------------------------
