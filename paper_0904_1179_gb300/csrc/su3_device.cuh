@@ -14,6 +14,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "su3_log_table.cuh"
+
 namespace su3dev {
 
 // ---------------------------------------------------------------------------
@@ -113,6 +115,34 @@ __device__ __forceinline__ uint4 rng_counter(uint32_t site, uint32_t w1, uint64_
 __device__ __forceinline__ double u01_f64(uint32_t a, uint32_t b) {
   const uint64_t x = ((uint64_t)a << 20) | (uint64_t)(b >> 12);
   return __longlong_as_double((long long)(0x3FF0000000000000ull | x)) - (1.0 - 0x1p-53);
+}
+
+// Natural logarithm of a uniform u in (0, 1) (a normal double, as u01_f64
+// makes them), by table-driven argument reduction (P. T. P. Tang, ACM TOMS 16
+// (1990) 378): u = m 2^e with m in [1, 2), F = 1 + j/64 the table point
+// nearest m, r = (m - F)/F with |r| <= 2^-7, and
+//     log u = e ln 2 + log F + log(1 + r),
+// log(1 + r) from its Taylor series to r^7 (truncation 2^-52 relative).  The
+// table (su3_log_table.cuh) holds log F and 1/F rounded to double; the result
+// is within a few ulp of the exact logarithm.  Eleven FP64 operations.
+__device__ __forceinline__ double log_u01(double u) {
+  const long long b = __double_as_longlong(u);
+  const int e = (int)(b >> 52) - 1023;  // u in (0, 1): e in [-53, -1]
+  const long long mb = b & 0x000FFFFFFFFFFFFFLL;
+  const double m = __longlong_as_double(mb | 0x3FF0000000000000LL);             // [1, 2)
+  const int j = (int)((mb + (1LL << 45)) >> 46);                                 // round(64 (m - 1)), 0..64
+  const double F = __longlong_as_double(0x3FF0000000000000LL + ((long long)j << 46));  // 1 + j/64 (2 for j = 64)
+  const double r = (m - F) * __ldg(&kInvF[j]);
+  double p = 1.0 / 7.0;
+  p = fma(p, r, -1.0 / 6.0);
+  p = fma(p, r, 1.0 / 5.0);
+  p = fma(p, r, -1.0 / 4.0);
+  p = fma(p, r, 1.0 / 3.0);
+  p = fma(p, r, -0.5);
+  p = fma(p, r, 1.0);
+  // e as a double without a conversion: 2^52 + 1024 + e from its bits, minus 2^52 + 1024
+  const double ed = __longlong_as_double(0x4330000000000000LL + (long long)(e + 1024)) - 4503599627371520.0;
+  return fma(ed, 0x1.62e42fefa39efp-1, __ldg(&kLogF[j])) + r * p;
 }
 
 // Uniform in [2^-24, 1-2^-24]: 23 bits centred in the bin, exact in float.

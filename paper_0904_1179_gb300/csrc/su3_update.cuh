@@ -196,7 +196,7 @@ __device__ __forceinline__ UpdateCount update_link_f64(const G& g, double2* U, i
       }
       ++cnt.proposed;
       const double c = cospi(2.0 * uu[1]);  // cos(2 pi u1)
-      const double delta = -(log(uu[0]) + c * c * log(uu[2])) * inv_alpha;
+      const double delta = -(log_u01(uu[0]) + c * c * log_u01(uu[2])) * inv_alpha;
       if (uu[3] * uu[3] > 1.0 - 0.5 * delta) continue;
       const double a0 = 1.0 - delta;
       double rho = 1.0 - a0 * a0;
