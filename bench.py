@@ -197,8 +197,9 @@ def time_sweeps(lat, stream, steps, warmup, sweeps_per_step, world, sampler=None
 
 def time_e2e(su3, L, prec, steps, warmup, sweeps_per_step):
     """End to end through the public API with page-locked host buffers: per step, copy the
-    configuration in (su3_links_set), run the sweeps, read the plaquette back, copy the
-    configuration out (su3_links_get)."""
+    configuration in (su3_links_set), run the sweeps -- the last one measuring the plaquette
+    inside the sweep (su3_sweep_measured) -- read the plaquette back, copy the configuration
+    out (su3_links_get)."""
     import numpy as np
     import torch
     shape = su3.links_shape(L)
@@ -208,20 +209,21 @@ def time_e2e(su3, L, prec, steps, warmup, sweeps_per_step):
         lat.get_links(host_in)  # the host-side start configuration
         for _ in range(warmup):
             lat.set_links(host_in)
-            lat.sweep(sweeps_per_step)
-            lat.plaquette()
+            lat.sweep(sweeps_per_step - 1)
+            lat.sweep_measured(1)
             lat.get_links(host_out)
         t0 = time.perf_counter()
         for _ in range(steps):
             lat.set_links(host_in)
-            lat.sweep(sweeps_per_step)
-            lat.plaquette()
+            lat.sweep(sweeps_per_step - 1)
+            lat.sweep_measured(1)
             lat.get_links(host_out)
         dt = time.perf_counter() - t0
     ups = 4 * int(np.prod(L)) * sweeps_per_step * steps / dt
     return {"value": ups, "unit": UNIT, "h2d_bytes_per_step": int(host_in.nbytes),
             "d2h_bytes_per_step": int(host_out.nbytes) + 8, "ms_per_step": dt / steps * 1e3,
-            "step": "su3_links_set(host) + %d sweeps + su3_plaquette + su3_links_get(host)" % sweeps_per_step}
+            "step": "su3_links_set(host) + %d sweeps, the last with the fused plaquette (su3_sweep_measured) "
+                    "+ su3_links_get(host)" % sweeps_per_step}
 
 
 # --- the oracle on every host core -------------------------------------------

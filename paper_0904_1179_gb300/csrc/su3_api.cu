@@ -208,6 +208,7 @@ int su3_transfer(su3_lattice* h, const su3dev::Geometry& g, void* links, double*
   for (long long s0 = 0; s0 < V; s0 += kChunkSites, ++i) {
     const long long n = (V - s0) < kChunkSites ? (V - s0) : kChunkSites;
     const int b = i & 1;
+    cudaStream_t cs = h->copy_stream;
     const size_t bytes = (size_t)n * 72 * sizeof(double);
     ConvArgs a{g, h->precision, s0, n, stage[b], links};
     if (get) {
@@ -215,14 +216,14 @@ int su3_transfer(su3_lattice* h, const su3dev::Geometry& g, void* links, double*
       if (i >= 2) SU3_CUDA(cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0), what);
       SU3_CUDA(su3k_launch_conv(a, false, h->stream), what);
       SU3_CUDA(cudaEventRecord(h->ev_conv[b], h->stream), what);
-      SU3_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_conv[b], 0), what);
-      SU3_CUDA(cudaMemcpyAsync(host + s0 * 72, stage[b], bytes, cudaMemcpyDeviceToHost, h->copy_stream), what);
-      SU3_CUDA(cudaEventRecord(h->ev_copied[b], h->copy_stream), what);
+      SU3_CUDA(cudaStreamWaitEvent(cs, h->ev_conv[b], 0), what);
+      SU3_CUDA(cudaMemcpyAsync(host + s0 * 72, stage[b], bytes, cudaMemcpyDeviceToHost, cs), what);
+      SU3_CUDA(cudaEventRecord(h->ev_copied[b], cs), what);
     } else {
       // stage[b] is free once the conversion of chunk i-2 has read it
-      if (i >= 2) SU3_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_conv[b], 0), what);
-      SU3_CUDA(cudaMemcpyAsync(stage[b], host + s0 * 72, bytes, cudaMemcpyHostToDevice, h->copy_stream), what);
-      SU3_CUDA(cudaEventRecord(h->ev_copied[b], h->copy_stream), what);
+      if (i >= 2) SU3_CUDA(cudaStreamWaitEvent(cs, h->ev_conv[b], 0), what);
+      SU3_CUDA(cudaMemcpyAsync(stage[b], host + s0 * 72, bytes, cudaMemcpyHostToDevice, cs), what);
+      SU3_CUDA(cudaEventRecord(h->ev_copied[b], cs), what);
       SU3_CUDA(cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0), what);
       SU3_CUDA(su3k_launch_conv(a, true, h->stream), what);
       SU3_CUDA(cudaEventRecord(h->ev_conv[b], h->stream), what);
@@ -373,9 +374,16 @@ int su3_sweep_measured(su3_handle h, int nsweeps, double* plaq_out) {
     const uint64_t t0 = h->sweep_host;
     for (int i = 0; i < n; ++i) SU3_CUDA(cudaGraphLaunch(h->graph_meas, h->stream), "su3_sweep_measured: graph launch");
     h->sweep_host += (uint64_t)n;
-    SU3_CUDA(cudaMemcpyAsync(h->h_meas, h->d_meas, (size_t)h->meas_cap * sizeof(double), cudaMemcpyDeviceToHost,
-                             h->stream),
+    // copy back only the n slots just written (two pieces where they wrap)
+    const int first = (int)(t0 % (uint64_t)h->meas_cap);
+    const int n1 = n < h->meas_cap - first ? n : h->meas_cap - first;
+    SU3_CUDA(cudaMemcpyAsync(h->h_meas + first, h->d_meas + first, (size_t)n1 * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream),
              "su3_sweep_measured: copy");
+    if (n > n1)
+      SU3_CUDA(cudaMemcpyAsync(h->h_meas, h->d_meas, (size_t)(n - n1) * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream),
+               "su3_sweep_measured: copy");
     rc = sync(h, "su3_sweep_measured");
     if (rc != SU3_OK) return rc;
     for (int i = 0; i < n; ++i) plaq_out[done + i] = h->h_meas[(t0 + (uint64_t)i) % (uint64_t)h->meas_cap];
