@@ -57,6 +57,26 @@ constexpr int kDefaultThreads = kSu3DefaultThreads;
 // to one warp) when that would leave SMs idle, so that a small lattice's
 // links spread over as many SMs as there are warps (each link's update is a
 // long serial chain, and on the FP64 pipe a few warps saturate an SM).
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms;
+}
+
+// FP64 sweeps of lattices whose half-sweep, at four lanes per link, still
+// gives at most four warps per SM run on k_half_sweep_f64_split: there the
+// update's latency is the bound (GB300: 8^4 1.51x, 8^3x16 1.44x faster).
+// Larger lattices load the FP64 pipe, and the split's idle lanes during the
+// heatbath cost about what its shorter staple chain saves (10^4: 1.04x) or
+// more (12^4: 0.61x).
+bool use_split(int Vh) {
+  const int sms = sm_count();
+  return sms > 0 && 4LL * Vh <= 128LL * sms;
+}
+
 int default_threads(int Vh) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -115,6 +135,7 @@ void release(su3_lattice* h) {
 HalfSweepArgs half_sweep_args(const su3_lattice* h, int parity) {
   HalfSweepArgs a{};
   a.meas = nullptr;
+  a.split = h->split;
   a.geom = h->geom;
   a.key = su3dev::philox_round_keys(h->key);
   a.parity = parity;
@@ -273,6 +294,7 @@ int su3_create_ex(int L0, int L1, int L2, int L3, double beta, uint64_t seed, in
   h->key.k0 = (uint32_t)seed;
   h->key.k1 = (uint32_t)(seed >> 32);
   h->threads = default_threads(h->geom.Vh);
+  h->split = use_split(h->geom.Vh);
 
   cudaError_t e;
   if (cuda_stream) {

@@ -315,6 +315,26 @@ __device__ __forceinline__ int nb_half(const Geometry& g, const Site& s, int nu,
   return (x0 >> 1) + g.hL0 * r;
 }
 
+__device__ __forceinline__ int wrap_coord(int x, int L) { return x < 0 ? x + L : (x >= L ? x - L : x); }
+
+// nb_half and nb_half2 for a direction known only at run time (it differs
+// between the lanes that share one link update): selects, no indexed arrays.
+__device__ __forceinline__ int nb_half_rt(const Geometry& g, const Site& s, int nu, int d) {
+  const int x0 = nu == 0 ? wrap_coord(s.x0 + d, g.L0) : s.x0;
+  const int x1 = nu == 1 ? wrap_coord(s.x1 + d, g.L1) : s.x1;
+  const int x2 = nu == 2 ? wrap_coord(s.x2 + d, g.L2) : s.x2;
+  const int x3 = nu == 3 ? wrap_coord(s.x3 + d, g.L3) : s.x3;
+  return (x0 >> 1) + g.hL0 * (x1 + g.L1 * (x2 + g.L2 * x3));
+}
+
+__device__ __forceinline__ int nb_half2_rt(const Geometry& g, const Site& s, int nu, int rho) {
+  const int x0 = wrap_coord(s.x0 + (nu == 0) - (rho == 0), g.L0);
+  const int x1 = wrap_coord(s.x1 + (nu == 1) - (rho == 1), g.L1);
+  const int x2 = wrap_coord(s.x2 + (nu == 2) - (rho == 2), g.L2);
+  const int x3 = wrap_coord(s.x3 + (nu == 3) - (rho == 3), g.L3);
+  return (x0 >> 1) + g.hL0 * (x1 + g.L1 * (x2 + g.L2 * x3));
+}
+
 // Half index of x + nu-hat - rho-hat for nu != rho.
 __device__ __forceinline__ int nb_half2(const Geometry& g, const Site& s, int nu, int rho) {
   Site t = s;

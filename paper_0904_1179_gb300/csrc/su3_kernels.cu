@@ -72,6 +72,60 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64(HalfSweepAr
   if (MEAS) block_partial(m, args.meas);
 }
 
+// A small lattice's half-sweep has too few links to fill the GPU, and each
+// link's FP64 update is a long dependent chain: the time is its latency.
+// Here four lanes share one link: lanes 0, 1, 2 compute the two staple paths
+// of the first, second and third direction nu != MU at the same time, lane 0
+// gathers them and adds them up in the single-thread order (forward then
+// backward path, nu ascending), so the staple, and everything after it, is
+// bit for bit that of k_half_sweep_f64.  Lane 3 only idles.
+__device__ __forceinline__ mat3<double> shfl_mat(const mat3<double>& m, int src) {
+  mat3<double> r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      r.e[i][k].re = __shfl_sync(0xffffffffu, m.e[i][k].re, src);
+      r.e[i][k].im = __shfl_sync(0xffffffffu, m.e[i][k].im, src);
+    }
+  return r;
+}
+
+template <int MU, bool STATS>
+__global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64_split(HalfSweepArgs args) {
+  const Geometry& g = args.geom;
+  const int p = args.parity;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int link = gid >> 2, part = gid & 3;
+  const bool active = link < g.Vh;
+  const int h = active ? link : 0;  // a group past the end works on site 0 and discards it (shuffles stay converged)
+  const Site st = site_of(g, h, p);
+  double2* U = (double2*)args.links;
+  mat3<double> F = zero3<double>(), B = zero3<double>();
+  if (part < 3) {
+    const int nu = part < MU ? part : part + 1;
+    const int h_pmu = nb_half(g, st, MU, +1);
+    F = forward_path<double, false>(g, U, st, h, p, MU, nu, h_pmu, nb_half_rt(g, st, nu, +1));
+    B = backward_path<double, false>(g, U, p, MU, nu, nb_half_rt(g, st, nu, -1), nb_half2_rt(g, st, MU, nu));
+  }
+  const int lane0 = (threadIdx.x & 31) & ~3;
+  mat3<double> A = zero3<double>();
+  acc_full(A, F);
+  acc_full(A, B);
+#pragma unroll
+  for (int k = 1; k < 3; ++k) {
+    acc_full(A, shfl_mat(F, lane0 + k));
+    acc_full(A, shfl_mat(B, lane0 + k));
+  }
+  UpdateCount c{0, 0};
+  if (part == 0 && active) {
+    const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15, 1};
+    c = heatbath_f64<MU, false, false, false>(g, U, h, p, *args.sweep, (uint32_t)canon(g, st), args.key, uc, A, A,
+                                             nullptr);
+  }
+  count_stats<STATS>(c, args.stats);
+}
+
 template <int MU, bool STATS, bool EFT, bool REPEAT, bool MEAS>
 __global__ void __launch_bounds__(SU3_F32_LB_THREADS, SU3_F32_MINBLOCKS) k_half_sweep_f32(HalfSweepArgs args) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -377,6 +431,14 @@ static cudaError_t launch_half_sweep_mu(const HalfSweepArgs& a, int precision, b
   if (MU > 0 && a.meas) {  // fused plaquette (statistics are not counted in these phases)
     return repeat ? launch_prec<MU, false, true, (MU > 0)>(a, precision, blocks, threads, s)
                   : launch_prec<MU, false, false, (MU > 0)>(a, precision, blocks, threads, s);
+  }
+  if (a.split && precision == 0 && !repeat) {
+    const int sblocks = (4 * a.geom.Vh + threads - 1) / threads;
+    if (stats)
+      k_half_sweep_f64_split<MU, true><<<sblocks, threads, 0, s>>>(a);
+    else
+      k_half_sweep_f64_split<MU, false><<<sblocks, threads, 0, s>>>(a);
+    return cudaGetLastError();
   }
   if (stats)
     return repeat ? launch_prec<MU, true, true, false>(a, precision, blocks, threads, s)

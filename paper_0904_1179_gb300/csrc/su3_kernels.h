@@ -22,6 +22,7 @@ struct HalfSweepArgs {
   void* links;
   unsigned long long* stats;  // [accepted, proposed], used when counting
   double* meas;               // fused plaquette: per-block partial sums of this phase (nullptr: off)
+  int split;                  // FP64 one-hit sweep of a small lattice: four lanes per link (see k_half_sweep_f64_split)
 };
 
 struct InitArgs {

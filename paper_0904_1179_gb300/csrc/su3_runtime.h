@@ -48,6 +48,7 @@ struct su3_lattice {
   int meas_cap = 0;
   int threads = kSu3DefaultThreads;
   int max_tries = 1;  // SU(2) proposals per subgroup (1: one-hit heatbath)
+  bool split = false;  // small FP64 lattice: four lanes per link update
   su3dev::Geometry geom{};
   su3dev::PhiloxKey key{};
   su3_batch* batch = nullptr;    // non-null for a batch of replicas

@@ -58,10 +58,44 @@ struct Store<float, CG> {
 // Apart (optional): receives the sum of the terms with nu < MU.  After the
 // update, Re Tr(U_new Apart) is the sum of the plaquettes of the planes
 // (MU, nu < MU) at x and at x - nu-hat.
+// The two three-link paths of direction nu (nu != mu):
+//   forward  F = U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+,
+//   backward B = U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu).
+// h_pmu is the half index of x + mu-hat.
+template <typename T, bool CG, typename G, typename S>
+__device__ __forceinline__ mat3<T> forward_path(const G& g, const void* U, const S& st, int h, int p, int mu, int nu,
+                                                int h_pmu, int h_pnu) {
+  const int q = p ^ 1;
+  const mat3<T> a = Store<T, CG>::load(U, nu, q, h_pmu, g.Vh);  // U_nu(x+mu)
+  const mat3<T> b = Store<T, CG>::load(U, mu, q, h_pnu, g.Vh);  // U_mu(x+nu)
+  mat3<T> t;
+  mul_nd_rows01(a, b, t);
+  const mat3<T> c = Store<T, CG>::load(U, nu, p, h, g.Vh);  // U_nu(x)
+  mat3<T> f;
+  mul_nd_rows01(t, c, f);
+  complete_row2(f);
+  return f;
+}
+
+template <typename T, bool CG, typename G>
+__device__ __forceinline__ mat3<T> backward_path(const G& g, const void* U, int p, int mu, int nu, int h_mnu,
+                                                 int h_pmu_mnu) {
+  const int q = p ^ 1;
+  const mat3<T> d = Store<T, CG>::load(U, nu, p, h_pmu_mnu, g.Vh);  // U_nu(x+mu-nu)
+  const mat3<T> e = Store<T, CG>::load(U, mu, q, h_mnu, g.Vh);      // U_mu(x-nu)
+  mat3<T> hm;
+  mul_nn_rows01(e, d, hm);
+  complete_row2(hm);
+  const mat3<T> f = Store<T, CG>::load(U, nu, q, h_mnu, g.Vh);  // U_nu(x-nu)
+  mat3<T> b;
+  mul_dn_rows01(hm, f, b);
+  complete_row2(b);
+  return b;
+}
+
 template <typename T, int MU, bool CG, typename G, typename S>
 __device__ __forceinline__ mat3<T> staple(const G& g, const void* U, const S& st, int h, int p,
                                           mat3<T>* Apart = nullptr) {
-  const int q = p ^ 1;
   mat3<T> A = zero3<T>();
   const int h_pmu = nb_half(g, st, MU, +1);
 #pragma unroll
@@ -70,29 +104,8 @@ __device__ __forceinline__ mat3<T> staple(const G& g, const void* U, const S& st
     const int h_pnu = nb_half(g, st, nu, +1);
     const int h_mnu = nb_half(g, st, nu, -1);
     const int h_pmu_mnu = nb_half2(g, st, MU, nu);
-    {
-      const mat3<T> a = Store<T, CG>::load(U, nu, q, h_pmu, g.Vh);  // U_nu(x+mu)
-      const mat3<T> b = Store<T, CG>::load(U, MU, q, h_pnu, g.Vh);  // U_mu(x+nu)
-      mat3<T> t;
-      mul_nd_rows01(a, b, t);
-      const mat3<T> c = Store<T, CG>::load(U, nu, p, h, g.Vh);  // U_nu(x)
-      mat3<T> f;
-      mul_nd_rows01(t, c, f);
-      complete_row2(f);
-      acc_full(A, f);
-    }
-    {
-      const mat3<T> d = Store<T, CG>::load(U, nu, p, h_pmu_mnu, g.Vh);  // U_nu(x+mu-nu)
-      const mat3<T> e = Store<T, CG>::load(U, MU, q, h_mnu, g.Vh);      // U_mu(x-nu)
-      mat3<T> hm;
-      mul_nn_rows01(e, d, hm);
-      complete_row2(hm);
-      const mat3<T> f = Store<T, CG>::load(U, nu, q, h_mnu, g.Vh);  // U_nu(x-nu)
-      mat3<T> b;
-      mul_dn_rows01(hm, f, b);
-      complete_row2(b);
-      acc_full(A, b);
-    }
+    acc_full(A, forward_path<T, CG>(g, U, st, h, p, MU, nu, h_pmu, h_pnu));
+    acc_full(A, backward_path<T, CG>(g, U, p, MU, nu, h_mnu, h_pmu_mnu));
     if (Apart && nu == MU - 1) *Apart = A;
   }
   return A;
@@ -162,15 +175,29 @@ struct UpdateCount {
 // the directions nu < MU (see staple()).
 // G: Geometry (periodic lattice) or SubGeometry (sublattice with ghost
 // layers); h enumerates the sites of parity p, hs is where the site is stored.
+template <int MU, bool CG, bool REPEAT, bool MEAS, typename KEY, typename G>
+__device__ __forceinline__ UpdateCount heatbath_f64(const G& g, double2* U, int h, int p, uint64_t t, uint32_t s,
+                                                    const KEY& key, const UpdateConsts& uc, const mat3<double>& A,
+                                                    const mat3<double>& Apart, double* meas);
+
 template <int MU, bool CG, bool REPEAT, bool MEAS = false, typename KEY, typename G>
 __device__ __forceinline__ UpdateCount update_link_f64(const G& g, double2* U, int h, int p, uint64_t t,
                                                        const KEY& key, const UpdateConsts& uc, double* meas = nullptr) {
-  UpdateCount cnt{0, 0};
   const auto st = site_of(g, h, p);
   const uint32_t s = (uint32_t)canon(g, st);
   h = store_index(g, st, h);
   mat3<double> Apart;
   const mat3<double> A = staple<double, MU, CG>(g, U, st, h, p, MEAS ? &Apart : nullptr);
+  return heatbath_f64<MU, CG, REPEAT, MEAS>(g, U, h, p, t, s, key, uc, A, Apart, meas);
+}
+
+// Everything after the staple: three SU(2) heatbath steps, Gram-Schmidt and
+// the store of link (s, MU) at storage half index h.
+template <int MU, bool CG, bool REPEAT, bool MEAS, typename KEY, typename G>
+__device__ __forceinline__ UpdateCount heatbath_f64(const G& g, double2* U, int h, int p, uint64_t t, uint32_t s,
+                                                    const KEY& key, const UpdateConsts& uc, const mat3<double>& A,
+                                                    const mat3<double>& Apart, double* meas) {
+  UpdateCount cnt{0, 0};
   mat3<double> u = load_f64<CG>(U, MU, p, h, g.Vh);
 #pragma unroll
   for (int sub = 0; sub < 3; ++sub) {
