@@ -20,8 +20,6 @@
 // The random numbers are keyed by the global site, so every link comes out
 // bit for bit as in the undivided lattice; what the emulation adds is the
 // measured cost of the exchange on a GB300.
-#include <cstdarg>
-#include <cstdio>
 #include <new>
 #include <vector>
 
