@@ -619,6 +619,56 @@ def run_table1(args):
     return 0
 
 
+def run_oracle_configs(args):
+    """The oracle timed on the other workloads, in microseconds per link update: one
+    full sweep of 48^4 (beta 5.7) and of 64^4 (beta 6.0) on every host core (spawned
+    processes on disjoint site subsets, as the CPU baseline; the configuration is an
+    oracle hot start of a 12^4 / 8^4 cell repeated), and one sweep of one replica of
+    each lattice size of the 96-replica batch on one core."""
+    import numpy as np
+    import oracle
+    from paper_0904_1179_gb300.workloads import batch_96
+    oracle.build()
+    out = {"mode": "oracle_configs", "unit": "us per link update", "kind": "oracle", "rows": []}
+    for L, beta, cell in (((48, 48, 48, 48), 5.7, 12), ((64, 64, 64, 64), 6.0, 8)):
+        # an oracle hot start on a small cell, repeated: a full hot start of 64^4
+        # would take the oracle longer than the sweep being timed
+        r = L[0] // cell
+        U = np.tile(oracle.hot_start((cell,) * 4, SEED), (r, r, r, r, 1, 1, 1, 1))
+        pool = OraclePool(L, U)
+        del U
+        try:
+            pool.half_sweep(beta, SEED, 0, 0, 0)  # start the workers
+            t0 = time.perf_counter()
+            n = 0
+            for mu in range(4):
+                for p in range(2):
+                    n += pool.half_sweep(beta, SEED, 1, mu, p)
+            dt = time.perf_counter() - t0
+            procs = pool.procs
+        finally:
+            pool.close()
+        out["rows"].append({"lattice": list(L), "beta": beta, "sample": "one sweep", "cores": procs,
+                            "seconds": dt, "core_us_per_update": dt * procs / n * 1e6,
+                            "value": n / dt})
+    dims, betas, seeds = batch_96()
+    seen = {}
+    for L, b, sd in zip(dims, betas, seeds):
+        if tuple(L) in seen:
+            continue
+        U = oracle.hot_start(L, sd, f32=True)
+        t0 = time.perf_counter()
+        oracle.sweep(L, b, sd, 0, 1, U, f32=True)
+        dt = time.perf_counter() - t0
+        n = 4 * int(np.prod(L))
+        seen[tuple(L)] = True
+        out["rows"].append({"lattice": list(L), "beta": b, "sample": "one sweep of the first replica of this size, "
+                            "FP32-mixed reading", "cores": 1, "seconds": dt, "core_us_per_update": dt / n * 1e6,
+                            "value": n / dt})
+    print(json.dumps(out))
+    return 0
+
+
 def run_decomp(args):
     """Table 1's structure on one GPU: each column (8^4 x 512 ... 32^4 x 2 sweeps, FP64,
     beta 5.7) undivided and cut like the paper's rows -- ndmpi = 1 with one sublattice and
@@ -704,6 +754,8 @@ def main():
     ap.add_argument("--chains-therm", type=int, default=500, help="thermalisation sweeps (48^4: 3/5 of it)")
     ap.add_argument("--chains-meas", type=int, default=8000, help="measured sweeps (48^4: 5/16 of it)")
     ap.add_argument("--large", action="store_true", help="64^4 beta 6.0, FP64 vs FP32-mixed")
+    ap.add_argument("--oracle-configs", action="store_true",
+                    help="the oracle's microseconds per update on 48^4, 64^4 and the batch's lattice sizes")
     ap.add_argument("--decomp", action="store_true",
                     help="Table 1's rows on one GPU: the domain decomposition emulated, exchange cost measured")
     ap.add_argument("--table1", action="store_true",
@@ -723,6 +775,8 @@ def main():
         return run_table1(args)
     if args.decomp:
         return run_decomp(args)
+    if args.oracle_configs:
+        return run_oracle_configs(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
