@@ -436,6 +436,8 @@ def run_profile_case(case):
     dims, beta = (DIMS, BETA)
     if case.endswith("_64"):
         dims, beta, case = (64, 64, 64, 64), 6.0, case[:-3]
+    elif case.endswith("_8"):
+        dims, case = (8, 8, 8, 8), case[:-2]
     prec = {"fp64": su3.SU3_FP64, "fp32_mixed": su3.SU3_FP32_MIXED, "fp32_eft": su3.SU3_FP32_EFT}[case]
     with su3.Lattice(dims, beta, SEED, start=su3.SU3_HOT, precision=prec) as lat:
         lat.sweep(3)
@@ -761,7 +763,8 @@ def main():
     ap.add_argument("--table1", action="store_true",
                     help="the paper's Table 1 columns in full (FP64 and FP32-mixed), with the oracle beside them")
     ap.add_argument("--large-sweeps", type=int, default=100)
-    ap.add_argument("--profile", choices=["fp64", "fp32_mixed", "fp32_eft", "batched", "fp64_64", "fp32_mixed_64", "decomp16"],
+    ap.add_argument("--profile", choices=["fp64", "fp32_mixed", "fp32_eft", "batched", "fp64_64", "fp32_mixed_64", "decomp16",
+                             "fp64_8"],
                     help="small case for ncu: create the 32^4 lattice (or the 96-replica batch) and run 3 graphed "
                          "sweeps, nothing else")
     args = ap.parse_args()
