@@ -73,9 +73,12 @@ def peaks():
 # where the kernel changed after its last capture.
 NCU_TRAFFIC = {"fp64": 688.0e6, "fp32_mixed": 225.9e6, "fp32_eft": 226.0e6, "batched": 3.579e9}
 
-# Peak FP64 FMA rate of GB300: 1.006 TFLOP/s measured by an FMA loop at the
-# 2070 MHz maximum SM clock (the nominal figure is 1.25 TFLOP/s).
-FP64_PEAK_TFLOPS = 1.006
+# FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA per
+# clock (1/64 of the 128 FP32 lanes) x 2 flop x 2.070 GHz = 1.2586 TFLOP/s
+# (the nominal 1.25).  An FMA-loop probe reached 1.006 TFLOP/s (0.80 of it);
+# both are reported.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP64_PROBE_TFLOPS = 1.006
 
 
 class ClockSampler:
@@ -838,6 +841,8 @@ def main():
         "gpu_launches_note": "headline timed region: per sweep 8 half-sweep kernels + 1 sweep-counter kernel",
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC["fp64"],
+                     "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flop x 2.070 GHz",
+                     "probe_peak": FP64_PROBE_TFLOPS, "frac_of_probe": achieved_tf / FP64_PROBE_TFLOPS,
                      "kernel": "k_half_sweep_f64", "flop_per_launch": flop_per_launch, "kernel_ms": kernel_ms,
                      "hbm_frac": BYTES_PER_UPDATE["fp64"] * (V // 2) / (kernel_ms * 1e-3) / 1e9 / hbm_peak,
                      "hbm_peak": hbm_peak, "hbm_peak_kind": peak_kind},
