@@ -66,15 +66,16 @@ int sm_count() {
   return sms;
 }
 
-// FP64 sweeps of lattices whose half-sweep, at four lanes per link, still
-// gives at most four warps per SM run on k_half_sweep_f64_split: there the
-// update's latency is the bound (GB300: 8^4 1.51x, 8^3x16 1.44x faster).
-// Larger lattices load the FP64 pipe, and the split's idle lanes during the
-// heatbath cost about what its shorter staple chain saves (10^4: 1.04x) or
-// more (12^4: 0.61x).
-bool use_split(int Vh) {
+// Half-sweeps of small lattices run four lanes per link (k_half_sweep_*_split):
+// there the latency of one update is the bound.  FP64: when the split still
+// gives at most four warps per SM (GB300: 8^4 1.51x, 8^3x16 1.44x faster;
+// beyond that the FP64 pipe is loaded and the idle lanes during the heatbath
+// cost what the shorter staple chain saves: 10^4 1.04x, 12^4 0.61x).  FP32:
+// at most eight warps per SM (8^4 1.35x, 10^4 1.27x; 12^4 would lose: 0.92x).
+bool use_split(int Vh, int precision) {
   const int sms = sm_count();
-  return sms > 0 && 4LL * Vh <= 128LL * sms;
+  const long long warps_per_sm = precision == SU3_FP64 ? 4 : 8;
+  return sms > 0 && 4LL * Vh <= 32LL * warps_per_sm * sms;
 }
 
 int default_threads(int Vh) {
@@ -294,7 +295,7 @@ int su3_create_ex(int L0, int L1, int L2, int L3, double beta, uint64_t seed, in
   h->key.k0 = (uint32_t)seed;
   h->key.k1 = (uint32_t)(seed >> 32);
   h->threads = default_threads(h->geom.Vh);
-  h->split = use_split(h->geom.Vh);
+  h->split = use_split(h->geom.Vh, precision);
 
   cudaError_t e;
   if (cuda_stream) {

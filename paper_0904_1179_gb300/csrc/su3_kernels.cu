@@ -126,6 +126,58 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64_split(HalfS
   count_stats<STATS>(c, args.stats);
 }
 
+// The same four-lane split for FP32 storage: the staple paths on row pairs
+// (pm3: 18 floats) are gathered into lane 0 and added in the single-thread
+// order; no register cap (small lattices leave the SMs nearly empty).
+__device__ __forceinline__ pm3 shfl_pm3(const pm3& m, int src) {
+  pm3 r;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    r.re[k].x = __shfl_sync(0xffffffffu, m.re[k].x, src);
+    r.re[k].y = __shfl_sync(0xffffffffu, m.re[k].y, src);
+    r.im[k].x = __shfl_sync(0xffffffffu, m.im[k].x, src);
+    r.im[k].y = __shfl_sync(0xffffffffu, m.im[k].y, src);
+    r.r2re[k] = __shfl_sync(0xffffffffu, m.r2re[k], src);
+    r.r2im[k] = __shfl_sync(0xffffffffu, m.r2im[k], src);
+  }
+  return r;
+}
+
+template <int MU, bool STATS, bool EFT>
+__global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f32_split(HalfSweepArgs args) {
+  const Geometry& g = args.geom;
+  const int p = args.parity;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int link = gid >> 2, part = gid & 3;
+  const bool active = link < g.Vh;
+  const int h = active ? link : 0;
+  const Site st = site_of(g, h, p);
+  float4* U = (float4*)args.links;
+  pm3 F = zero_p(), B = zero_p();
+  if (part < 3) {
+    const int nu = part < MU ? part : part + 1;
+    const int h_pmu = nb_half(g, st, MU, +1);
+    F = forward_path_p<false>(g, U, h, p, MU, nu, h_pmu, nb_half_rt(g, st, nu, +1));
+    B = backward_path_p<false>(g, U, p, MU, nu, nb_half_rt(g, st, nu, -1), nb_half2_rt(g, st, MU, nu));
+  }
+  const int lane0 = (threadIdx.x & 31) & ~3;
+  pm3 A = zero_p();
+  acc_p(A, F);
+  acc_p(A, B);
+#pragma unroll
+  for (int k = 1; k < 3; ++k) {
+    acc_p(A, shfl_pm3(F, lane0 + k));
+    acc_p(A, shfl_pm3(B, lane0 + k));
+  }
+  UpdateCount c{0, 0};
+  if (part == 0 && active) {
+    const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15, 1};
+    c = heatbath_f32<MU, false, EFT, false, false>(g, U, h, p, *args.sweep, (uint32_t)canon(g, st), args.key, uc, A,
+                                                    A, nullptr);
+  }
+  count_stats<STATS>(c, args.stats);
+}
+
 template <int MU, bool STATS, bool EFT, bool REPEAT, bool MEAS>
 __global__ void __launch_bounds__(SU3_F32_LB_THREADS, SU3_F32_MINBLOCKS) k_half_sweep_f32(HalfSweepArgs args) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -432,12 +484,24 @@ static cudaError_t launch_half_sweep_mu(const HalfSweepArgs& a, int precision, b
     return repeat ? launch_prec<MU, false, true, (MU > 0)>(a, precision, blocks, threads, s)
                   : launch_prec<MU, false, false, (MU > 0)>(a, precision, blocks, threads, s);
   }
-  if (a.split && precision == 0 && !repeat) {
+  if (a.split && !repeat) {
     const int sblocks = (4 * a.geom.Vh + threads - 1) / threads;
-    if (stats)
-      k_half_sweep_f64_split<MU, true><<<sblocks, threads, 0, s>>>(a);
-    else
-      k_half_sweep_f64_split<MU, false><<<sblocks, threads, 0, s>>>(a);
+    if (precision == 0) {
+      if (stats)
+        k_half_sweep_f64_split<MU, true><<<sblocks, threads, 0, s>>>(a);
+      else
+        k_half_sweep_f64_split<MU, false><<<sblocks, threads, 0, s>>>(a);
+    } else if (precision == 2) {
+      if (stats)
+        k_half_sweep_f32_split<MU, true, true><<<sblocks, threads, 0, s>>>(a);
+      else
+        k_half_sweep_f32_split<MU, false, true><<<sblocks, threads, 0, s>>>(a);
+    } else {
+      if (stats)
+        k_half_sweep_f32_split<MU, true, false><<<sblocks, threads, 0, s>>>(a);
+      else
+        k_half_sweep_f32_split<MU, false, false><<<sblocks, threads, 0, s>>>(a);
+    }
     return cudaGetLastError();
   }
   if (stats)

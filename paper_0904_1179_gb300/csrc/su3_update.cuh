@@ -267,10 +267,46 @@ __device__ __forceinline__ UpdateCount heatbath_f64(const G& g, double2* U, int 
 // SU(3) matrix, so rows 0,1 are multiplied out two rows at a time and row 2
 // is completed.
 // ---------------------------------------------------------------------------
+// The two paths of direction nu on row pairs (as forward_path and
+// backward_path above).
+template <bool CG, typename G>
+__device__ __forceinline__ pm3 forward_path_p(const G& g, const float4* U, int h, int p, int mu, int nu, int h_pmu,
+                                              int h_pnu) {
+  const int q = p ^ 1;
+  const pm3 a = load_pm3<CG>(U, nu, q, h_pmu, g.Vh);  // U_nu(x+mu)
+  pm3 b = load_pm3<CG>(U, mu, q, h_pnu, g.Vh);        // U_mu(x+nu)
+  complete_row2_p(b);
+  pm3 t;
+  mul_nd_p(a, b, t);
+  pm3 c = load_pm3<CG>(U, nu, p, h, g.Vh);  // U_nu(x)
+  complete_row2_p(c);
+  pm3 f;
+  mul_nd_p(t, c, f);
+  complete_row2_p(f);
+  return f;
+}
+
+template <bool CG, typename G>
+__device__ __forceinline__ pm3 backward_path_p(const G& g, const float4* U, int p, int mu, int nu, int h_mnu,
+                                               int h_pmu_mnu) {
+  const int q = p ^ 1;
+  pm3 d = load_pm3<CG>(U, nu, p, h_pmu_mnu, g.Vh);  // U_nu(x+mu-nu)
+  complete_row2_p(d);
+  const pm3 e = load_pm3<CG>(U, mu, q, h_mnu, g.Vh);  // U_mu(x-nu)
+  pm3 hm;
+  mul_nn_p(e, d, hm);
+  complete_row2_p(hm);
+  pm3 f = load_pm3<CG>(U, nu, q, h_mnu, g.Vh);  // U_nu(x-nu)
+  complete_row2_p(f);
+  pm3 b;
+  mul_dn_p(hm, f, b);
+  complete_row2_p(b);
+  return b;
+}
+
 template <int MU, bool CG, typename G, typename S>
 __device__ __forceinline__ pm3 staple_p(const G& g, const float4* U, const S& st, int h, int p,
                                         pm3* Apart = nullptr) {
-  const int q = p ^ 1;
   pm3 A = zero_p();
   const int h_pmu = nb_half(g, st, MU, +1);
 #pragma unroll
@@ -279,33 +315,8 @@ __device__ __forceinline__ pm3 staple_p(const G& g, const float4* U, const S& st
     const int h_pnu = nb_half(g, st, nu, +1);
     const int h_mnu = nb_half(g, st, nu, -1);
     const int h_pmu_mnu = nb_half2(g, st, MU, nu);
-    {
-      const pm3 a = load_pm3<CG>(U, nu, q, h_pmu, g.Vh);  // U_nu(x+mu)
-      pm3 b = load_pm3<CG>(U, MU, q, h_pnu, g.Vh);        // U_mu(x+nu)
-      complete_row2_p(b);
-      pm3 t;
-      mul_nd_p(a, b, t);
-      pm3 c = load_pm3<CG>(U, nu, p, h, g.Vh);  // U_nu(x)
-      complete_row2_p(c);
-      pm3 f;
-      mul_nd_p(t, c, f);
-      complete_row2_p(f);
-      acc_p(A, f);
-    }
-    {
-      pm3 d = load_pm3<CG>(U, nu, p, h_pmu_mnu, g.Vh);  // U_nu(x+mu-nu)
-      complete_row2_p(d);
-      const pm3 e = load_pm3<CG>(U, MU, q, h_mnu, g.Vh);  // U_mu(x-nu)
-      pm3 hm;
-      mul_nn_p(e, d, hm);
-      complete_row2_p(hm);
-      pm3 f = load_pm3<CG>(U, nu, q, h_mnu, g.Vh);  // U_nu(x-nu)
-      complete_row2_p(f);
-      pm3 b;
-      mul_dn_p(hm, f, b);
-      complete_row2_p(b);
-      acc_p(A, b);
-    }
+    acc_p(A, forward_path_p<CG>(g, U, h, p, MU, nu, h_pmu, h_pnu));
+    acc_p(A, backward_path_p<CG>(g, U, p, MU, nu, h_mnu, h_pmu_mnu));
     if (Apart && nu == MU - 1) *Apart = A;
   }
   return A;
@@ -325,15 +336,29 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // compensated FP32 sums of FP64-class accuracy (EFT = true).  REPEAT = false
 // compiles the one-hit heatbath without the retry loop.
 // ---------------------------------------------------------------------------
+template <int MU, bool CG, bool EFT, bool REPEAT, bool MEAS, typename KEY, typename G>
+__device__ __forceinline__ UpdateCount heatbath_f32(const G& g, float4* U, int h, int p, uint64_t t, uint32_t s,
+                                                    const KEY& key, const UpdateConsts& uc, const pm3& A,
+                                                    const pm3& Apart, double* meas);
+
 template <int MU, bool CG, bool EFT, bool REPEAT, bool MEAS = false, typename KEY, typename G>
 __device__ __forceinline__ UpdateCount update_link_f32(const G& g, float4* U, int h, int p, uint64_t t,
                                                        const KEY& key, const UpdateConsts& uc, double* meas = nullptr) {
-  UpdateCount cnt{0, 0};
   const auto st = site_of(g, h, p);
   const uint32_t s = (uint32_t)canon(g, st);
   h = store_index(g, st, h);
   pm3 Apart;
   const pm3 A = staple_p<MU, CG>(g, U, st, h, p, MEAS ? &Apart : nullptr);
+  return heatbath_f32<MU, CG, EFT, REPEAT, MEAS>(g, U, h, p, t, s, key, uc, A, Apart, meas);
+}
+
+// Everything after the staple (FP32 storage): three SU(2) heatbath steps,
+// reunitarisation, store.
+template <int MU, bool CG, bool EFT, bool REPEAT, bool MEAS, typename KEY, typename G>
+__device__ __forceinline__ UpdateCount heatbath_f32(const G& g, float4* U, int h, int p, uint64_t t, uint32_t s,
+                                                    const KEY& key, const UpdateConsts& uc, const pm3& A,
+                                                    const pm3& Apart, double* meas) {
+  UpdateCount cnt{0, 0};
   pm3 u = load_pm3<CG>(U, MU, p, h, g.Vh);
   complete_row2_p(u);
   const float inv_beta15 = uc.inv_beta15;
