@@ -140,7 +140,13 @@ SU3_API double su3_plaquette(su3_handle h);
  * layout (n_doubles must equal V*4*18, else SU3_ESIZE).  Synchronises.
  * For SU3_FP32_MIXED, set rounds rows 0 and 1 to FP32 (round to nearest) and
  * ignores row 2; get returns rows 0 and 1 exactly and row 2 computed in FP64
- * as conj(row0 x row1).  Page-locked buffers transfer fastest. */
+ * as conj(row0 x row1).  Page-locked buffers transfer fastest.
+ * The links set must be SU(3) matrices (to the storage precision): the
+ * staple multiplies out rows 0 and 1 of each three-link path and completes
+ * row 2 as conj(row0 x row1), which holds for products of SU(3) matrices
+ * only.  set does not check; every update reunitarises the link it writes
+ * (a link far from unitary, |row|^2 - 1 or <row0,row1> beyond 1e-3, takes a
+ * full FP64 Gram-Schmidt in the FP32 paths). */
 SU3_API int su3_links_get(su3_handle h, double* host, size_t n_doubles);
 SU3_API int su3_links_set(su3_handle h, const double* host, size_t n_doubles);
 

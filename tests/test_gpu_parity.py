@@ -274,6 +274,39 @@ def test_fp32_half_sweeps_match_oracle_reading(L, prec):
     print("fp32 (precision %d) half-sweeps %s: worst |dU| %.2e, flips %d of %d" % (prec, L, worst, flips, total))
 
 
+@pytest.mark.parametrize("prec", [su3.SU3_FP32_MIXED, su3.SU3_FP32_EFT])
+def test_fp32_far_from_unitary_takes_full_gram_schmidt(prec):
+    # the links being updated have rows 0 and 1 stretched by 2 % and 1.5 %
+    # (their staples, from the other links, stay in SU(3)): the
+    # reunitarisation's norm errors exceed 1e-3, so every updated link goes
+    # through the full FP64 Gram-Schmidt branch; the result is still the
+    # oracle's FP32 reading, and unitary to FP32 rounding
+    L = (4, 4, 4, 8)
+    U0 = oracle.hot_start(L, 17, f32=True)
+    pm = parity_mask(L)
+    seed, t = 31, 2
+    with su3.Lattice(L, BETA, seed, start=su3.SU3_COLD, precision=prec) as lat:
+        for mu, p in ((0, 0), (2, 1)):
+            U1 = U0.copy()
+            sel = U1[pm == bool(p), mu]
+            sel[:, 0] *= 1.02
+            sel[:, 1] *= 0.985
+            U1[pm == bool(p), mu] = sel
+            U1 = U1.astype(np.float32).astype(np.float64)
+            lat.set_links(U1)
+            lat.sweep_count = t
+            lat.half_sweep(mu, p)
+            G = flat_links(lat.get_links())
+            sites = site_list(L, p)
+            O, marg = oracle.updated_links(L, BETA, seed, t, mu, sites, U1, f32=True, with_margins=True)
+            d = np.abs(G[sites, mu] - O).max(axis=(1, 2, 3))
+            bad = d > F32_TOL
+            assert bad.sum() <= 1, (bad.sum(), d.max())
+            assert not bad.any() or (np.nanmin(np.abs(marg[bad]), axis=1) < F32_MARGIN).all()
+            unit, det = su3_defects(G[sites, mu])
+            assert unit < 5e-7 and det < 5e-7, (unit, det)
+
+
 def test_fp32_links_stay_su3_and_float():
     L = (8, 8, 8, 8)
     with su3.Lattice(L, BETA, 3, start=su3.SU3_HOT, precision=su3.SU3_FP32_MIXED) as lat:
