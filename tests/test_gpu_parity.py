@@ -177,6 +177,33 @@ def test_fp64_sweep_matches_oracle(L):
         assert abs(lat.plaquette() - plaq[-1]) < 1e-13
 
 
+@pytest.mark.parametrize("beta", [0.2, 50.0])
+def test_extreme_couplings_match_oracle(beta):
+    # strong coupling (alpha ~ 0.1: the Kennedy-Pendleton proposal is often
+    # rejected) and weak coupling (alpha ~ 100): one sweep link by link (FP64)
+    # and one half-sweep against the oracle's FP32 reading
+    L = (4, 4, 4, 6)
+    U0 = oracle.hot_start(L, 8)
+    O = U0.copy()
+    stats, _ = oracle.sweep(L, beta, 12, 0, 1, O)
+    with su3.Lattice(L, beta, 12, start=su3.SU3_COLD) as lat:
+        lat.set_links(U0)
+        lat.set_stats(True)
+        lat.sweep(1)
+        assert np.abs(lat.get_links() - O).max() < F64_TOL
+        assert lat.stats() == stats
+    U32 = oracle.hot_start(L, 8, f32=True)
+    with su3.Lattice(L, beta, 12, start=su3.SU3_COLD, precision=su3.SU3_FP32_MIXED) as lat:
+        lat.set_links(U32)
+        lat.half_sweep(1, 0)
+        G = flat_links(lat.get_links())
+        sites = site_list(L, 0)
+        Of, marg = oracle.updated_links(L, beta, 12, 0, 1, sites, U32, f32=True, with_margins=True)
+        d = np.abs(G[sites, 1] - Of).max(axis=(1, 2, 3))
+        bad = d > F32_TOL
+        assert bad.sum() <= 1 and (not bad.any() or (np.nanmin(np.abs(marg[bad]), axis=1) < F32_MARGIN).all())
+
+
 def test_fp64_cold_start_chain_config0():
     # 4^4, beta 5.7, cold start, Philox seed 1, 20 sweeps, plaquette after each sweep
     L = (4, 4, 4, 4)
