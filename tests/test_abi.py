@@ -132,3 +132,21 @@ def test_decomp_plan_matches_closed_form(lib, L):
             assert nsub == nf ** nd
             assert halo == 4 * _halo_sites(L, nd, nf), (L, nd, nf)
     assert su3.su3_decomp_plan(L, 1, 1, 0) == (1, 0)
+
+
+def test_c_program_on_the_abi(lib, tmp_path):
+    # the header compiles as C, and a C program linked against libsu3.so runs
+    # the calls that need no GPU
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(su3._LIB_PATH)
+    exe = str(tmp_path / "c_abi_host")
+    src = os.path.join(os.path.dirname(__file__), "c_abi_host.c")
+    inc = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", inc, src, "-L", libdir, "-lsu3", "-Wl,-rpath," + libdir,
+                    "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert "c abi ok" in r.stdout
