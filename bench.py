@@ -16,8 +16,9 @@ Multi-GPU: replicas only -- each rank runs its own lattice (weak scaling), no
 collective on the data path; value = all ranks' link updates / slowest rank's
 time.
 
---impl reference times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload (one half-sweep of the 32^4 lattice per step).
+--impl reference times the FP64 CPU oracle on every host core (spawned
+processes on disjoint site subsets) on a bounded sample of the same workload
+(one half-sweep of the 32^4 lattice per step).
 """
 from __future__ import annotations
 
@@ -53,7 +54,8 @@ BYTES_PER_UPDATE = {"fp64": 9 * 18 * 8, "fp32_mixed": 9 * 12 * 4}
 # FP64 floating-point operations per link update of the FP64 kernel as written
 # (staple 6 paths x 2 three-row-pair products + 6 row completions, accumulation,
 # three SU(2) projections and rotations, Gram-Schmidt); transcendental calls
-# are not counted.  See the design notes for the breakdown.
+# are not counted: staple 3 x (348 + 390) = 2214, projections and rotations
+# 864, Gram-Schmidt 130.
 FP64_FLOP_PER_UPDATE = 3208
 
 
