@@ -21,8 +21,8 @@
  *     (Sec. 2.1, paragraph on the boundary exchange cost);
  *   - one timed unit = one SU(3) matrix update (Sec. 2.1, Fig. 1 caption);
  *   - start-configuration creation is separate from the sweeps (Sec. 2).
- * Everything else is silent in the paper and follows the textbook readings
- * listed in the design notes: Wilson action S = beta sum_P (1 - ReTr U_P / 3),
+ * Everything else is silent in the paper and follows these textbook
+ * readings: Wilson action S = beta sum_P (1 - ReTr U_P / 3),
  * Cabibbo-Marinari (Phys. Lett. B119 (1982) 387) over the SU(2) subgroups
  * (0,1), (0,2), (1,2), Kennedy-Pendleton (Phys. Lett. B156 (1985) 393)
  * sampling with one hit, Gram-Schmidt reunitarisation after every update,
