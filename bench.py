@@ -52,11 +52,17 @@ PAPER_TABLE1_SECONDS = [48.2, 48.3, 48.7, 48.9]
 # 9 links moved per update.
 BYTES_PER_UPDATE = {"fp64": 9 * 18 * 8, "fp32_mixed": 9 * 12 * 4}
 # FP64 floating-point operations per link update of the FP64 kernel as written
-# (staple 6 paths x 2 three-row-pair products + 6 row completions, accumulation,
-# three SU(2) projections and rotations, Gram-Schmidt); transcendental calls
-# are not counted: staple 3 x (348 + 390) = 2214, projections and rotations
-# 864, Gram-Schmidt 130.
-FP64_FLOP_PER_UPDATE = 3208
+# (an FMA counts 2; transcendental calls, square roots and divisions are not
+# counted):
+#   staple 2070: 6 paths x 2 products of rows 0,1 (or columns 0,1) = 12 x 144,
+#     first path's row completion 42, 5 accumulations with the row completion
+#     fused in, 60 each;
+#   three SU(2) steps 254 + 254 + 212 = 720: projection 100, |r|^2 and
+#     1/alpha 8, uniforms 6, Kennedy-Pendleton proposal and test 8, a0 and the
+#     direction 8, quaternions 8, SU(2) matrix 32, rotation of rows (i, j) 84
+#     (42 in the last step, whose row 2 is rebuilt by Gram-Schmidt);
+#   Gram-Schmidt 84 and row completion 42.
+FP64_FLOP_PER_UPDATE = 2070 + 720 + 126
 
 
 def peaks():
@@ -73,7 +79,7 @@ def peaks():
 # one ncu capture of each kernel (profiles/*.md; batched: 128 threads x 6 blocks
 # per SM, the autotuner's usual choice); None
 # where the kernel changed after its last capture.
-NCU_TRAFFIC = {"fp64": 688.0e6, "fp32_mixed": 225.9e6, "fp32_eft": 226.0e6, "batched": 3.579e9}
+NCU_TRAFFIC = {"fp64": 688.2e6, "fp32_mixed": 225.5e6, "fp32_eft": 225.6e6, "batched": 3.571e9}
 
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA per
 # clock (1/64 of the 128 FP32 lanes) x 2 flop x 2.070 GHz = 1.2586 TFLOP/s

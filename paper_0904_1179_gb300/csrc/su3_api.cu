@@ -141,8 +141,8 @@ HalfSweepArgs half_sweep_args(const su3_lattice* h, int parity) {
   a.key = su3dev::philox_round_keys(h->key);
   a.parity = parity;
   a.beta = h->beta;
-  a.inv_beta15 = (float)(1.5 / h->beta);
-  a.inv_beta15_f64 = 1.5 / h->beta;
+  a.three_over_beta = (float)(3.0 / h->beta);
+  a.three_over_beta_f64 = 3.0 / h->beta;
   a.max_tries = h->max_tries;
   a.sweep = h->d_sweep;
   a.links = h->links;

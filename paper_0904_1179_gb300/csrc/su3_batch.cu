@@ -45,8 +45,8 @@ struct ReplicaDesc {
   Geometry g;
   PhiloxKey key;
   long long offset;  // first element (double2 or float4) of the replica's link store
-  double inv_beta15_f64;
-  float inv_beta15;
+  double three_over_beta_f64;
+  float three_over_beta;
   int ntiles;  // work items per phase
 };
 
@@ -85,7 +85,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 template <typename T, bool EFT, bool REPEAT>
 __device__ __forceinline__ void update_item(int mu, const ReplicaDesc& rd, void* links, int h, int p, uint64_t t,
                                             int max_tries) {
-  const UpdateConsts uc{rd.inv_beta15_f64, rd.inv_beta15, max_tries};
+  const UpdateConsts uc{rd.three_over_beta_f64, rd.three_over_beta, max_tries};
   if constexpr (std::is_same<T, double>::value) {
     double2* U = (double2*)links + rd.offset;
     switch (mu) {
@@ -276,8 +276,8 @@ int build_schedule(su3_lattice* h) {
     d.key.k0 = (uint32_t)b->seeds[r];
     d.key.k1 = (uint32_t)(b->seeds[r] >> 32);
     d.offset = b->offsets[r];
-    d.inv_beta15_f64 = 1.5 / b->betas[r];
-    d.inv_beta15 = (float)(1.5 / b->betas[r]);
+    d.three_over_beta_f64 = 3.0 / b->betas[r];
+    d.three_over_beta = (float)(3.0 / b->betas[r]);
     d.ntiles = tiles_of(d.g, b->threads);
     reps[r] = d;
   }

@@ -50,8 +50,8 @@ struct DecompArgs {
   int nf, ndmpi;
   PhiloxRoundKeys key;
   int parity;
-  double inv_beta15_f64;
-  float inv_beta15;
+  double three_over_beta_f64;
+  float three_over_beta;
   const uint64_t* sweep;
   void* subs;
   size_t sub_elems;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_decomp_half_sweep_f64(Deco
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   UpdateCount c{0, 0};
   if (h < g.in.Vh) {
-    const UpdateConsts uc{a.inv_beta15_f64, a.inv_beta15, 1};
+    const UpdateConsts uc{a.three_over_beta_f64, a.three_over_beta, 1};
     double2* U = (double2*)a.subs + (size_t)k * a.sub_elems;
     c = update_link_f64<MU, false, false>(g, U, h, a.parity, *a.sweep, a.key, uc);
   }
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kMaxSweepThreads, 4) k_decomp_half_sweep_f32(D
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   UpdateCount c{0, 0};
   if (h < g.in.Vh) {
-    const UpdateConsts uc{a.inv_beta15_f64, a.inv_beta15, 1};
+    const UpdateConsts uc{a.three_over_beta_f64, a.three_over_beta, 1};
     float4* U = (float4*)a.subs + (size_t)k * a.sub_elems;
     c = update_link_f32<MU, false, EFT, false>(g, U, h, a.parity, *a.sweep, a.key, uc);
   }
@@ -224,8 +224,8 @@ DecompArgs decomp_args(const su3_lattice* h, int parity) {
   a.ndmpi = d->ndmpi;
   a.key = philox_round_keys(h->key);
   a.parity = parity;
-  a.inv_beta15_f64 = 1.5 / h->beta;
-  a.inv_beta15 = (float)(1.5 / h->beta);
+  a.three_over_beta_f64 = 3.0 / h->beta;
+  a.three_over_beta = (float)(3.0 / h->beta);
   a.sweep = h->d_sweep;
   a.subs = d->d_sub;
   a.sub_elems = d->sub_elems;

@@ -236,13 +236,14 @@ __device__ __forceinline__ void mul_nd_rows01(const mat3<T>& X, const mat3<T>& Y
     }
 }
 
-// Rows 0,1 of X * Y (Y complete).
+// Columns 0,1 of X * Y (X complete, Y's columns 0,1 used); column 2 of Z is
+// left unset.
 template <typename T>
-__device__ __forceinline__ void mul_nn_rows01(const mat3<T>& X, const mat3<T>& Y, mat3<T>& Z) {
+__device__ __forceinline__ void mul_nn_cols01(const mat3<T>& X, const mat3<T>& Y, mat3<T>& Z) {
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 2; ++k) {
       cx<T> s = mk(T(0), T(0));
 #pragma unroll
       for (int j = 0; j < 3; ++j) s = mac(s, X.e[i][j], Y.e[j][k]);
@@ -250,7 +251,7 @@ __device__ __forceinline__ void mul_nn_rows01(const mat3<T>& X, const mat3<T>& Y
     }
 }
 
-// Rows 0,1 of X^+ * Y (X and Y complete).
+// Rows 0,1 of X^+ * Y (X's columns 0,1 used, Y complete).
 template <typename T>
 __device__ __forceinline__ void mul_dn_rows01(const mat3<T>& X, const mat3<T>& Y, mat3<T>& Z) {
 #pragma unroll
@@ -262,6 +263,25 @@ __device__ __forceinline__ void mul_dn_rows01(const mat3<T>& X, const mat3<T>& Y
       for (int j = 0; j < 3; ++j) s = mac_ca(s, X.e[j][i], Y.e[j][k]);
       Z.e[i][k] = s;
     }
+}
+
+// A += B for an SU(3) matrix B of which only rows 0,1 are set: row 2 of B is
+// formed as conj(row0 x row1) inside the accumulation of A's row 2.
+template <typename T>
+__device__ __forceinline__ void acc_completed(mat3<T>& A, const mat3<T>& B) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    A.e[0][k] = add(A.e[0][k], B.e[0][k]);
+    A.e[1][k] = add(A.e[1][k], B.e[1][k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int a = (k + 1) % 3, b = (k + 2) % 3;
+    // A_2k + conj(v) = conj(conj(A_2k) + v), v = B_0a B_1b - B_0b B_1a
+    cx<T> v = mac(conj(A.e[2][k]), B.e[0][a], B.e[1][b]);
+    v = mac(v, mk(-B.e[0][b].re, -B.e[0][b].im), B.e[1][a]);
+    A.e[2][k] = conj(v);
+  }
 }
 
 template <typename T>

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64(HalfSweepAr
   UpdateCount c{0, 0};
   double m = 0.0;
   if (h < args.geom.Vh) {
-    const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15, args.max_tries};
+    const UpdateConsts uc{args.three_over_beta_f64, args.three_over_beta, args.max_tries};
     c = update_link_f64<MU, false, REPEAT, MEAS>(args.geom, (double2*)args.links, h, args.parity, *args.sweep, args.key,
                                                  uc, &m);
   }
@@ -74,15 +74,16 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64(HalfSweepAr
 
 // A small lattice's half-sweep has too few links to fill the GPU, and each
 // link's FP64 update is a long dependent chain: the time is its latency.
-// Here four lanes share one link: lanes 0, 1, 2 compute the two staple paths
-// of the first, second and third direction nu != MU at the same time, lane 0
-// gathers them and adds them up in the single-thread order (forward then
-// backward path, nu ascending), so the staple, and everything after it, is
-// bit for bit that of k_half_sweep_f64.  Lane 3 only idles.
-__device__ __forceinline__ mat3<double> shfl_mat(const mat3<double>& m, int src) {
+// Here four lanes share one link: lanes 0, 1, 2 compute rows 0,1 of the two
+// staple paths of the first, second and third direction nu != MU at the same
+// time, lane 0 gathers them and adds them up in the single-thread order
+// (forward then backward path, nu ascending, row 2 formed in the
+// accumulation), so the staple, and everything after it, is bit for bit that
+// of k_half_sweep_f64.  Lane 3 only idles.
+__device__ __forceinline__ mat3<double> shfl_rows01(const mat3<double>& m, int src) {
   mat3<double> r;
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       r.e[i][k].re = __shfl_sync(0xffffffffu, m.e[i][k].re, src);
@@ -109,27 +110,28 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64_split(HalfS
     B = backward_path<double, false>(g, U, p, MU, nu, nb_half_rt(g, st, nu, -1), nb_half2_rt(g, st, MU, nu));
   }
   const int lane0 = (threadIdx.x & 31) & ~3;
-  mat3<double> A = zero3<double>();
-  acc_full(A, F);
-  acc_full(A, B);
+  mat3<double> A;
+  init_completed(A, F);
+  acc_completed(A, B);
 #pragma unroll
   for (int k = 1; k < 3; ++k) {
-    acc_full(A, shfl_mat(F, lane0 + k));
-    acc_full(A, shfl_mat(B, lane0 + k));
+    acc_completed(A, shfl_rows01(F, lane0 + k));
+    acc_completed(A, shfl_rows01(B, lane0 + k));
   }
   UpdateCount c{0, 0};
   if (part == 0 && active) {
-    const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15, 1};
+    const UpdateConsts uc{args.three_over_beta_f64, args.three_over_beta, 1};
     c = heatbath_f64<MU, false, false, false>(g, U, h, p, *args.sweep, (uint32_t)canon(g, st), args.key, uc, A, A,
                                              nullptr);
   }
   count_stats<STATS>(c, args.stats);
 }
 
-// The same four-lane split for FP32 storage: the staple paths on row pairs
-// (pm3: 18 floats) are gathered into lane 0 and added in the single-thread
-// order; no register cap (small lattices leave the SMs nearly empty).
-__device__ __forceinline__ pm3 shfl_pm3(const pm3& m, int src) {
+// The same four-lane split for FP32 storage: rows 0,1 of the staple paths on
+// row pairs (12 floats each) are gathered into lane 0 and added in the
+// single-thread order; no register cap (small lattices leave the SMs nearly
+// empty).
+__device__ __forceinline__ pm3 shfl_pm3_rows01(const pm3& m, int src) {
   pm3 r;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -137,8 +139,6 @@ __device__ __forceinline__ pm3 shfl_pm3(const pm3& m, int src) {
     r.re[k].y = __shfl_sync(0xffffffffu, m.re[k].y, src);
     r.im[k].x = __shfl_sync(0xffffffffu, m.im[k].x, src);
     r.im[k].y = __shfl_sync(0xffffffffu, m.im[k].y, src);
-    r.r2re[k] = __shfl_sync(0xffffffffu, m.r2re[k], src);
-    r.r2im[k] = __shfl_sync(0xffffffffu, m.r2im[k], src);
   }
   return r;
 }
@@ -161,17 +161,17 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f32_split(HalfS
     B = backward_path_p<false>(g, U, p, MU, nu, nb_half_rt(g, st, nu, -1), nb_half2_rt(g, st, MU, nu));
   }
   const int lane0 = (threadIdx.x & 31) & ~3;
-  pm3 A = zero_p();
-  acc_p(A, F);
-  acc_p(A, B);
+  pm3 A;
+  init_completed_p(A, F);
+  acc_completed_p(A, B);
 #pragma unroll
   for (int k = 1; k < 3; ++k) {
-    acc_p(A, shfl_pm3(F, lane0 + k));
-    acc_p(A, shfl_pm3(B, lane0 + k));
+    acc_completed_p(A, shfl_pm3_rows01(F, lane0 + k));
+    acc_completed_p(A, shfl_pm3_rows01(B, lane0 + k));
   }
   UpdateCount c{0, 0};
   if (part == 0 && active) {
-    const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15, 1};
+    const UpdateConsts uc{args.three_over_beta_f64, args.three_over_beta, 1};
     c = heatbath_f32<MU, false, EFT, false, false>(g, U, h, p, *args.sweep, (uint32_t)canon(g, st), args.key, uc, A,
                                                     A, nullptr);
   }
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(SU3_F32_LB_THREADS, SU3_F32_MINBLOCKS) k_half_
   UpdateCount c{0, 0};
   double m = 0.0;
   if (h < args.geom.Vh) {
-    const UpdateConsts uc{args.inv_beta15_f64, args.inv_beta15, args.max_tries};
+    const UpdateConsts uc{args.three_over_beta_f64, args.three_over_beta, args.max_tries};
     c = update_link_f32<MU, false, EFT, REPEAT, MEAS>(args.geom, (float4*)args.links, h, args.parity, *args.sweep,
                                                       args.key, uc, &m);
   }

@@ -15,8 +15,8 @@ struct HalfSweepArgs {
   su3dev::PhiloxRoundKeys key;
   int parity;
   double beta;        // FP64 path
-  double inv_beta15_f64;  // FP64 path: 1.5 / beta
-  float inv_beta15;   // FP32 path: 1.5 / beta, so that 1/alpha = inv_beta15 / k
+  double three_over_beta_f64;  // FP64 path: 3 / beta
+  float three_over_beta;       // FP32 path: 3 / beta, so that 1/alpha = 3 / (2 beta k) = three_over_beta / (2k)
   int max_tries;      // SU(2) proposals per subgroup: 1 = one-hit heatbath
   const uint64_t* sweep;  // device sweep counter (RNG position)
   void* links;

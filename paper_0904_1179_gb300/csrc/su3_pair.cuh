@@ -126,13 +126,22 @@ __device__ __forceinline__ void mul_dn_p(const pm3& H, const pm3& F, pm3& Z) {
   }
 }
 
-__device__ __forceinline__ void acc_p(pm3& A, const pm3& B) {
+// A += B for an SU(3) matrix B of which only rows 0,1 are set: row 2 of B,
+// conj(row0 x row1), is formed inside the accumulation of A's row 2.
+__device__ __forceinline__ void acc_completed_p(pm3& A, const pm3& B) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     A.re[k] = add2(A.re[k], B.re[k]);
     A.im[k] = add2(A.im[k], B.im[k]);
-    A.r2re[k] += B.r2re[k];
-    A.r2im[k] += B.r2im[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int a = (k + 1) % 3, b = (k + 2) % 3;
+    // A_2k + conj(v) = conj(conj(A_2k) + v), v = B_0a B_1b - B_0b B_1a
+    cx<float> v = mac(mk(A.r2re[k], -A.r2im[k]), pget(B, 0, a), pget(B, 1, b));
+    v = mac(v, mk(-pre(B, 0, b), -pim(B, 0, b)), pget(B, 1, a));
+    A.r2re[k] = v.re;
+    A.r2im[k] = -v.im;
   }
 }
 

@@ -54,11 +54,14 @@ struct Store<float, CG> {
 // Six-staple sum A for U_mu(x), x = st of parity p:
 //   sum_{nu != mu} U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ + U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu).
 // Each three-link path is an SU(3) matrix, so only its rows 0 and 1 are
-// multiplied out and row 2 is completed as conj(row0 x row1).
+// multiplied out; its row 2, conj(row0 x row1), is formed inside the
+// accumulation of A's row 2 (acc_completed).  The paths are added in the
+// order forward, backward for nu ascending; every kernel that forms a staple
+// keeps this order, so their results agree bit for bit.
 // Apart (optional): receives the sum of the terms with nu < MU.  After the
 // update, Re Tr(U_new Apart) is the sum of the plaquettes of the planes
 // (MU, nu < MU) at x and at x - nu-hat.
-// The two three-link paths of direction nu (nu != mu):
+// The two three-link paths of direction nu (nu != mu), rows 0,1:
 //   forward  F = U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+,
 //   backward B = U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu).
 // h_pmu is the half index of x + mu-hat.
@@ -73,7 +76,6 @@ __device__ __forceinline__ mat3<T> forward_path(const G& g, const void* U, const
   const mat3<T> c = Store<T, CG>::load(U, nu, p, h, g.Vh);  // U_nu(x)
   mat3<T> f;
   mul_nd_rows01(t, c, f);
-  complete_row2(f);
   return f;
 }
 
@@ -83,20 +85,31 @@ __device__ __forceinline__ mat3<T> backward_path(const G& g, const void* U, int 
   const int q = p ^ 1;
   const mat3<T> d = Store<T, CG>::load(U, nu, p, h_pmu_mnu, g.Vh);  // U_nu(x+mu-nu)
   const mat3<T> e = Store<T, CG>::load(U, mu, q, h_mnu, g.Vh);      // U_mu(x-nu)
+  // Rows 0,1 of d^+ e^+ = (e d)^+ are the conjugated columns 0,1 of e d, which
+  // need all three rows of e (stored in full here) but no row-2 completion.
   mat3<T> hm;
-  mul_nn_rows01(e, d, hm);
-  complete_row2(hm);
+  mul_nn_cols01(e, d, hm);
   const mat3<T> f = Store<T, CG>::load(U, nu, q, h_mnu, g.Vh);  // U_nu(x-nu)
   mat3<T> b;
   mul_dn_rows01(hm, f, b);
-  complete_row2(b);
   return b;
+}
+
+// A = F (rows 0,1 given, row 2 completed): the first term of a staple.
+template <typename T>
+__device__ __forceinline__ void init_completed(mat3<T>& A, const mat3<T>& F) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    A.e[0][k] = F.e[0][k];
+    A.e[1][k] = F.e[1][k];
+  }
+  complete_row2(A);
 }
 
 template <typename T, int MU, bool CG, typename G, typename S>
 __device__ __forceinline__ mat3<T> staple(const G& g, const void* U, const S& st, int h, int p,
                                           mat3<T>* Apart = nullptr) {
-  mat3<T> A = zero3<T>();
+  mat3<T> A;
   const int h_pmu = nb_half(g, st, MU, +1);
 #pragma unroll
   for (int nu = 0; nu < 4; ++nu) {
@@ -104,16 +117,22 @@ __device__ __forceinline__ mat3<T> staple(const G& g, const void* U, const S& st
     const int h_pnu = nb_half(g, st, nu, +1);
     const int h_mnu = nb_half(g, st, nu, -1);
     const int h_pmu_mnu = nb_half2(g, st, MU, nu);
-    acc_full(A, forward_path<T, CG>(g, U, st, h, p, MU, nu, h_pmu, h_pnu));
-    acc_full(A, backward_path<T, CG>(g, U, p, MU, nu, h_mnu, h_pmu_mnu));
+    const mat3<T> F = forward_path<T, CG>(g, U, st, h, p, MU, nu, h_pmu, h_pnu);
+    if (nu == (MU == 0 ? 1 : 0)) {
+      init_completed(A, F);
+    } else {
+      acc_completed(A, F);
+    }
+    acc_completed(A, backward_path<T, CG>(g, U, p, MU, nu, h_mnu, h_pmu_mnu));
     if (Apart && nu == MU - 1) *Apart = A;
   }
   return A;
 }
 
 
-// 2x2 block of W = U A in rows/columns (i, j), projected on the SU(2) direction:
-// r = (Re(W_ii+W_jj), Im(W_ij+W_ji), Re(W_ij-W_ji), Im(W_ii-W_jj)) / 2.
+// 2x2 block of W = U A in rows/columns (i, j), projected on the SU(2) direction,
+// returned as 2r = (Re(W_ii+W_jj), Im(W_ij+W_ji), Re(W_ij-W_ji), Im(W_ii-W_jj)):
+// the factor 1/2 of r cancels in r/|r| and is folded into 1/alpha.
 template <typename T>
 __device__ __forceinline__ void su2_projection(const mat3<T>& u, const mat3<T>& A, int i, int j, T r[4]) {
   cx<T> wii = mk(T(0), T(0)), wij = wii, wji = wii, wjj = wii;
@@ -124,16 +143,17 @@ __device__ __forceinline__ void su2_projection(const mat3<T>& u, const mat3<T>& 
     wji = mac(wji, u.e[j][c], A.e[c][i]);
     wjj = mac(wjj, u.e[j][c], A.e[c][j]);
   }
-  r[0] = T(0.5) * (wii.re + wjj.re);
-  r[1] = T(0.5) * (wij.im + wji.im);
-  r[2] = T(0.5) * (wij.re - wji.re);
-  r[3] = T(0.5) * (wii.im - wjj.im);
+  r[0] = wii.re + wjj.re;
+  r[1] = wij.im + wji.im;
+  r[2] = wij.re - wji.re;
+  r[3] = wii.im - wjj.im;
 }
 
 // rows (i, j) of u <- R rows (i, j), R = Y V^+ with Y = m(a), V = m(v),
 // m(q) = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]].
+// rows_j = false leaves row j unchanged (its new value is not needed).
 template <typename T>
-__device__ __forceinline__ void apply_su2(mat3<T>& u, int i, int j, const T a[4], const T v[4]) {
+__device__ __forceinline__ void apply_su2(mat3<T>& u, int i, int j, const T a[4], const T v[4], bool rows_j = true) {
   const cx<T> y00 = mk(a[0], a[3]), y01 = mk(a[2], a[1]);
   const cx<T> v00 = mk(v[0], v[3]), v01 = mk(v[2], v[1]), v10 = mk(-v[2], v[1]), v11 = mk(v[0], -v[3]);
   // (V^+)_{pq} = conj(V_{qp}); a product of two matrices of this SU(2) form
@@ -146,7 +166,7 @@ __device__ __forceinline__ void apply_su2(mat3<T>& u, int i, int j, const T a[4]
   for (int c = 0; c < 3; ++c) {
     const cx<T> ui = u.e[i][c], uj = u.e[j][c];
     u.e[i][c] = mac(mul(R00, ui), R01, uj);
-    u.e[j][c] = mac(mul(R10, ui), R11, uj);
+    if (rows_j) u.e[j][c] = mac(mul(R10, ui), R11, uj);
   }
 }
 
@@ -156,8 +176,8 @@ __device__ __forceinline__ int subrow_j(int sub) { return sub == 0 ? 1 : 2; }
 
 // Parameters of one link update that do not vary across the links of a lattice.
 struct UpdateConsts {
-  double inv_beta15_f64;  // 1.5 / beta: 1/alpha = 3/(2 beta k) = inv_beta15 / k
-  float inv_beta15;
+  double three_over_beta_f64;  // 3 / beta: 1/alpha = 3 / (2 beta k) = three_over_beta / (2k)
+  float three_over_beta;
   int max_tries;  // 1: one-hit heatbath; > 1: repeat until accepted, at most this many proposals
 };
 
@@ -202,15 +222,15 @@ __device__ __forceinline__ UpdateCount heatbath_f64(const G& g, double2* U, int 
 #pragma unroll
   for (int sub = 0; sub < 3; ++sub) {
     const int i = subrow_i(sub), j = subrow_j(sub);
-    double r[4];
+    double r[4];  // 2r
     su2_projection(u, A, i, j, r);
-    const double kk = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
+    const double kk = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];  // (2k)^2
     if (!(kk > 0.0)) {  // k = 0: degenerate staple (measure zero), leave the subgroup
       ++cnt.proposed;
       continue;
     }
-    const double ik = rsqrt(kk);
-    const double inv_alpha = uc.inv_beta15_f64 * ik;  // 1/alpha = 3 / (2 beta k)
+    const double ik = rsqrt(kk);                           // 1 / (2k)
+    const double inv_alpha = uc.three_over_beta_f64 * ik;  // 1/alpha = 3 / (2 beta k)
     const int ntries = REPEAT ? uc.max_tries : 1;
     for (int tr = 0; tr < ntries; ++tr) {
       double uu[6];
@@ -234,8 +254,9 @@ __device__ __forceinline__ UpdateCount heatbath_f64(const G& g, double2* U, int 
       double sphi, cphi;
       sincospi(2.0 * uu[5], &sphi, &cphi);  // angle 2 pi u5
       const double a[4] = {a0, rho * sn * cphi, rho * sn * sphi, rho * ct};
-      const double v[4] = {r[0] * ik, r[1] * ik, r[2] * ik, r[3] * ik};
-      apply_su2(u, i, j, a, v);
+      const double v[4] = {r[0] * ik, r[1] * ik, r[2] * ik, r[3] * ik};  // r / k
+      // Row 2 leaves the last subgroup unused: reunitarisation rebuilds it.
+      apply_su2(u, i, j, a, v, sub < 2);
       ++cnt.accepted;
       break;
     }
@@ -267,8 +288,8 @@ __device__ __forceinline__ UpdateCount heatbath_f64(const G& g, double2* U, int 
 // SU(3) matrix, so rows 0,1 are multiplied out two rows at a time and row 2
 // is completed.
 // ---------------------------------------------------------------------------
-// The two paths of direction nu on row pairs (as forward_path and
-// backward_path above).
+// The two paths of direction nu on row pairs, rows 0,1 (as forward_path and
+// backward_path above), added to the staple in the same order.
 template <bool CG, typename G>
 __device__ __forceinline__ pm3 forward_path_p(const G& g, const float4* U, int h, int p, int mu, int nu, int h_pmu,
                                               int h_pnu) {
@@ -282,7 +303,6 @@ __device__ __forceinline__ pm3 forward_path_p(const G& g, const float4* U, int h
   complete_row2_p(c);
   pm3 f;
   mul_nd_p(t, c, f);
-  complete_row2_p(f);
   return f;
 }
 
@@ -300,14 +320,23 @@ __device__ __forceinline__ pm3 backward_path_p(const G& g, const float4* U, int 
   complete_row2_p(f);
   pm3 b;
   mul_dn_p(hm, f, b);
-  complete_row2_p(b);
   return b;
+}
+
+// A = F (rows 0,1 given, row 2 completed): the first term of a staple.
+__device__ __forceinline__ void init_completed_p(pm3& A, const pm3& F) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    A.re[k] = F.re[k];
+    A.im[k] = F.im[k];
+  }
+  complete_row2_p(A);
 }
 
 template <int MU, bool CG, typename G, typename S>
 __device__ __forceinline__ pm3 staple_p(const G& g, const float4* U, const S& st, int h, int p,
                                         pm3* Apart = nullptr) {
-  pm3 A = zero_p();
+  pm3 A;
   const int h_pmu = nb_half(g, st, MU, +1);
 #pragma unroll
   for (int nu = 0; nu < 4; ++nu) {
@@ -315,8 +344,13 @@ __device__ __forceinline__ pm3 staple_p(const G& g, const float4* U, const S& st
     const int h_pnu = nb_half(g, st, nu, +1);
     const int h_mnu = nb_half(g, st, nu, -1);
     const int h_pmu_mnu = nb_half2(g, st, MU, nu);
-    acc_p(A, forward_path_p<CG>(g, U, h, p, MU, nu, h_pmu, h_pnu));
-    acc_p(A, backward_path_p<CG>(g, U, p, MU, nu, h_mnu, h_pmu_mnu));
+    const pm3 F = forward_path_p<CG>(g, U, h, p, MU, nu, h_pmu, h_pnu);
+    if (nu == (MU == 0 ? 1 : 0)) {
+      init_completed_p(A, F);
+    } else {
+      acc_completed_p(A, F);
+    }
+    acc_completed_p(A, backward_path_p<CG>(g, U, p, MU, nu, h_mnu, h_pmu_mnu));
     if (Apart && nu == MU - 1) *Apart = A;
   }
   return A;
@@ -361,7 +395,7 @@ __device__ __forceinline__ UpdateCount heatbath_f32(const G& g, float4* U, int h
   UpdateCount cnt{0, 0};
   pm3 u = load_pm3<CG>(U, MU, p, h, g.Vh);
   complete_row2_p(u);
-  const float inv_beta15 = uc.inv_beta15;
+  const float three_over_beta = uc.three_over_beta;
 #pragma unroll
   for (int sub = 0; sub < 3; ++sub) {
     const int i = subrow_i(sub), j = subrow_j(sub);
@@ -401,15 +435,15 @@ __device__ __forceinline__ UpdateCount heatbath_f32(const G& g, float4* U, int h
         wjj = mac(wjj, pget(u, j, c), pget(A, c, j));
       }
     }
-    const float r[4] = {0.5f * (wii.re + wjj.re), 0.5f * (wij.im + wji.im), 0.5f * (wij.re - wji.re),
-                        0.5f * (wii.im - wjj.im)};
-    const float kk = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
-    if (!(kk > 1e-30f)) {  // degenerate staple (measure zero): leave the subgroup
+    // 2r, as in su2_projection
+    const float r[4] = {wii.re + wjj.re, wij.im + wji.im, wij.re - wji.re, wii.im - wjj.im};
+    const float kk = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];  // (2k)^2
+    if (!(kk > 4e-30f)) {  // degenerate staple (measure zero): leave the subgroup
       ++cnt.proposed;
       continue;
     }
-    const float ik = rsqrtf(kk);
-    const float ia = inv_beta15 * ik;  // 1/alpha = 3 / (2 beta k)
+    const float ik = rsqrtf(kk);             // 1 / (2k)
+    const float ia = three_over_beta * ik;  // 1/alpha = 3 / (2 beta k)
     bool acc = false;
     float a[4];
     const int ntries = REPEAT ? uc.max_tries : 1;
@@ -452,7 +486,8 @@ __device__ __forceinline__ UpdateCount heatbath_f32(const G& g, float4* U, int h
       for (int c = 0; c < 3; ++c) {
         const cx<float> ui = pget(u, i, c), uj = pget(u, j, c);
         pset(u, i, c, mac(mul(R00, ui), R01, uj));
-        pset(u, j, c, mac(mul(R10, ui), R11, uj));
+        // row 2 leaves the last subgroup unused: reunitarisation rebuilds it
+        if (sub < 2) pset(u, j, c, mac(mul(R10, ui), R11, uj));
       }
     }
     ++cnt.accepted;
