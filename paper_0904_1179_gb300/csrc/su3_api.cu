@@ -283,15 +283,7 @@ int su3_create_ex(int L0, int L1, int L2, int L3, double beta, uint64_t seed, in
   h->beta = beta;
   h->seed = seed;
   h->precision = precision;
-  h->geom.L0 = L0;
-  h->geom.L1 = L1;
-  h->geom.L2 = L2;
-  h->geom.L3 = L3;
-  h->geom.hL0 = L0 / 2;
-  h->geom.Vh = (int)(V / 2);
-  h->geom.s1 = L0;
-  h->geom.s2 = L0 * L1;
-  h->geom.s3 = L0 * L1 * L2;
+  h->geom = su3dev::make_geometry(L0, L1, L2, L3);
   h->key.k0 = (uint32_t)seed;
   h->key.k1 = (uint32_t)(seed >> 32);
   h->threads = default_threads(h->geom.Vh);

@@ -432,16 +432,7 @@ int su3_batch_create(int n, const int (*dims)[4], const double* betas, const uin
       su3_release_handle(h);
       return su3_fail(SU3_EINVAL, "su3_batch_create: replica %d: beta must be finite and > 0", r);
     }
-    Geometry g{};
-    g.L0 = dims[r][0];
-    g.L1 = dims[r][1];
-    g.L2 = dims[r][2];
-    g.L3 = dims[r][3];
-    g.hL0 = g.L0 / 2;
-    g.Vh = (int)(V / 2);
-    g.s1 = g.L0;
-    g.s2 = g.L0 * g.L1;
-    g.s3 = g.L0 * g.L1 * g.L2;
+    const Geometry g = make_geometry(dims[r][0], dims[r][1], dims[r][2], dims[r][3]);
     b->geoms.push_back(g);
     b->betas.push_back(betas[r]);
     b->seeds.push_back(seeds[r]);

@@ -355,15 +355,7 @@ void host_sub_geometry(const int L[4], int ndmpi, int mpifactor, SubGeometry& g)
     if (cut) g.cut |= 1 << dd;
     ext *= g.e[dd];
   }
-  g.in.L0 = l[0];
-  g.in.L1 = l[1];
-  g.in.L2 = l[2];
-  g.in.L3 = l[3];
-  g.in.hL0 = l[0] / 2;
-  g.in.Vh = (int)((long long)l[0] * l[1] * l[2] * l[3] / 2);
-  g.in.s1 = l[0];
-  g.in.s2 = l[0] * l[1];
-  g.in.s3 = l[0] * l[1] * l[2];
+  g.in = make_geometry(l[0], l[1], l[2], l[3]);
   g.he0 = g.e[0] / 2;
   g.L0 = L[0];
   g.L1 = L[1];

@@ -42,12 +42,52 @@ constexpr uint32_t kPhiloxWeylB = 0xBB67AE85u;
 constexpr uint32_t kTagUpdate = 0u;
 constexpr uint32_t kTagHotStart = 1u;
 
+// Division of n in [0, 2^31) by a fixed d >= 1 as a multiply and a shift:
+// with s = ceil(log2 d) and m = ceil(2^(31+s) / d) < 2^32,
+// floor(n m / 2^(31+s)) = floor(n / d) exactly, because the excess
+// n (m d - 2^(31+s)) / (d 2^(31+s)) is below 2^-s <= 1/d (Granlund and
+// Montgomery, PLDI 1994).
+struct Divisor {
+  uint32_t m;
+  int shift;  // 31 + s
+};
+
+__host__ inline Divisor make_divisor(uint32_t d) {
+  int s = 0;
+  while ((1ull << s) < d) ++s;
+  const unsigned long long two = 1ull << (31 + s);
+  return Divisor{(uint32_t)((two + d - 1) / d), 31 + s};
+}
+
+__device__ __forceinline__ int udiv(int n, const Divisor& d) {
+  return (int)(((unsigned long long)(uint32_t)n * d.m) >> d.shift);
+}
+
 struct Geometry {
   int L0, L1, L2, L3;
   int hL0;      // L0 / 2
   int Vh;       // V / 2
   int s1, s2, s3;  // strides of x1, x2, x3 in the canonical index: L0, L0*L1, L0*L1*L2
+  Divisor div_hL0, div_L1, div_L2;
 };
+
+// Geometry of a periodic L0 x L1 x L2 x L3 lattice (L0 even, V/2 < 2^31).
+__host__ inline Geometry make_geometry(int L0, int L1, int L2, int L3) {
+  Geometry g{};
+  g.L0 = L0;
+  g.L1 = L1;
+  g.L2 = L2;
+  g.L3 = L3;
+  g.hL0 = L0 / 2;
+  g.Vh = (int)((long long)L0 * L1 * L2 * L3 / 2);
+  g.s1 = L0;
+  g.s2 = L0 * L1;
+  g.s3 = L0 * L1 * L2;
+  g.div_hL0 = make_divisor((uint32_t)g.hL0);
+  g.div_L1 = make_divisor((uint32_t)L1);
+  g.div_L2 = make_divisor((uint32_t)L2);
+  return g;
+}
 
 struct PhiloxKey {
   uint32_t k0, k1;
@@ -303,12 +343,12 @@ struct Site {
 
 __device__ __forceinline__ Site site_of(const Geometry& g, int h, int p) {
   Site st;
-  const int r = h / g.hL0;
+  const int r = udiv(h, g.div_hL0);
   const int x0e = 2 * (h - r * g.hL0);
   st.r = r;
-  const int q = r / g.L1;
+  const int q = udiv(r, g.div_L1);
   st.x1 = r - q * g.L1;
-  st.x3 = q / g.L2;
+  st.x3 = udiv(q, g.div_L2);
   st.x2 = q - st.x3 * g.L2;
   st.x0 = x0e + ((p + st.x1 + st.x2 + st.x3) & 1);
   return st;

@@ -160,16 +160,7 @@ extern "C" SU3_API int su3_plaquette_noalloc(const void* links, int L0, int L1, 
   double* scratch = nullptr;
   const int rc = scratch_address(&scratch);
   if (rc != SU3_OK) return rc;
-  Geometry g{};
-  g.L0 = L0;
-  g.L1 = L1;
-  g.L2 = L2;
-  g.L3 = L3;
-  g.hL0 = L0 / 2;
-  g.Vh = (int)(V / 2);
-  g.s1 = L0;
-  g.s2 = L0 * L1;
-  g.s3 = L0 * L1 * L2;
+  const Geometry g = make_geometry(L0, L1, L2, L3);
   const int blocks = (int)((V + kThreads - 1) / kThreads);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (precision == SU3_FP64)
