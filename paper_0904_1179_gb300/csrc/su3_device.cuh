@@ -69,6 +69,10 @@ struct Geometry {
   int Vh;       // V / 2
   int s1, s2, s3;  // strides of x1, x2, x3 in the canonical index: L0, L0*L1, L0*L1*L2
   Divisor div_hL0, div_L1, div_L2;
+  // Half-index steps: hs[nu] = change of h for x_nu + 1 (nu >= 1), and
+  // wrap[nu] = (L_nu - 1) hs[nu], the change when x_nu wraps from L_nu - 1 to
+  // 0 (with the sign reversed); wrap[0] = L0/2 - 1 for x0.
+  int hs[4], wrap[4];
 };
 
 // Geometry of a periodic L0 x L1 x L2 x L3 lattice (L0 even, V/2 < 2^31).
@@ -86,6 +90,14 @@ __host__ inline Geometry make_geometry(int L0, int L1, int L2, int L3) {
   g.div_hL0 = make_divisor((uint32_t)g.hL0);
   g.div_L1 = make_divisor((uint32_t)L1);
   g.div_L2 = make_divisor((uint32_t)L2);
+  g.hs[0] = 0;
+  g.hs[1] = g.hL0;
+  g.hs[2] = g.hL0 * L1;
+  g.hs[3] = g.hL0 * L1 * L2;
+  g.wrap[0] = g.hL0 - 1;
+  g.wrap[1] = (L1 - 1) * g.hs[1];
+  g.wrap[2] = (L2 - 1) * g.hs[2];
+  g.wrap[3] = (L3 - 1) * g.hs[3];
   return g;
 }
 
@@ -339,6 +351,7 @@ __device__ __forceinline__ void acc_full(mat3<T>& A, const mat3<T>& B) {
 struct Site {
   int x0, x1, x2, x3;
   int r;  // x1 + L1*(x2 + L2*x3)
+  int h;  // half index (x0 >> 1) + hL0 * r
 };
 
 __device__ __forceinline__ Site site_of(const Geometry& g, int h, int p) {
@@ -351,28 +364,30 @@ __device__ __forceinline__ Site site_of(const Geometry& g, int h, int p) {
   st.x3 = udiv(q, g.div_L2);
   st.x2 = q - st.x3 * g.L2;
   st.x0 = x0e + ((p + st.x1 + st.x2 + st.x3) & 1);
+  st.h = h;
   return st;
 }
 
 __device__ __forceinline__ int canon(const Geometry& g, const Site& s) { return s.x0 + g.L0 * s.r; }
 
+// The half index is separable, h = (x0 >> 1) + hs1 x1 + hs2 x2 + hs3 x3, so
+// a step of d = +1 or -1 along nu changes it by an offset that depends only
+// on x_nu: +-hs[nu], or the wrap offset at the boundary; along x0 the step
+// changes x0 >> 1 by 0 or d, depending on the parity of x0.
+__device__ __forceinline__ int nb_offset(const Geometry& g, const Site& s, int nu, int d) {
+  if (nu == 0) {
+    if (d > 0) return s.x0 == g.L0 - 1 ? -g.wrap[0] : (s.x0 & 1);
+    return s.x0 == 0 ? g.wrap[0] : (s.x0 & 1) - 1;
+  }
+  const int x = nu == 1 ? s.x1 : (nu == 2 ? s.x2 : s.x3);
+  const int L = nu == 1 ? g.L1 : (nu == 2 ? g.L2 : g.L3);
+  if (d > 0) return x == L - 1 ? -g.wrap[nu] : g.hs[nu];
+  return x == 0 ? g.wrap[nu] : -g.hs[nu];
+}
+
 // Half index of the neighbour x + d*nu-hat (d = +1 or -1), periodic.
 __device__ __forceinline__ int nb_half(const Geometry& g, const Site& s, int nu, int d) {
-  int x0 = s.x0, r = s.r;
-  if (nu == 0) {
-    x0 += d;
-    x0 = x0 < 0 ? x0 + g.L0 : (x0 >= g.L0 ? x0 - g.L0 : x0);
-  } else if (nu == 1) {
-    const int x = s.x1 + d;
-    r += (x < 0 ? g.L1 - 1 : (x >= g.L1 ? 1 - g.L1 : d));
-  } else if (nu == 2) {
-    const int x = s.x2 + d;
-    r += g.L1 * (x < 0 ? g.L2 - 1 : (x >= g.L2 ? 1 - g.L2 : d));
-  } else {
-    const int x = s.x3 + d;
-    r += g.L1 * g.L2 * (x < 0 ? g.L3 - 1 : (x >= g.L3 ? 1 - g.L3 : d));
-  }
-  return (x0 >> 1) + g.hL0 * r;
+  return s.h + nb_offset(g, s, nu, d);
 }
 
 __device__ __forceinline__ int wrap_coord(int x, int L) { return x < 0 ? x + L : (x >= L ? x - L : x); }
@@ -397,15 +412,7 @@ __device__ __forceinline__ int nb_half2_rt(const Geometry& g, const Site& s, int
 
 // Half index of x + nu-hat - rho-hat for nu != rho.
 __device__ __forceinline__ int nb_half2(const Geometry& g, const Site& s, int nu, int rho) {
-  Site t = s;
-  int* xs[4] = {&t.x0, &t.x1, &t.x2, &t.x3};
-  const int Ls[4] = {g.L0, g.L1, g.L2, g.L3};
-  int v = *xs[nu] + 1;
-  *xs[nu] = v >= Ls[nu] ? v - Ls[nu] : v;
-  v = *xs[rho] - 1;
-  *xs[rho] = v < 0 ? v + Ls[rho] : v;
-  t.r = t.x1 + g.L1 * (t.x2 + g.L2 * t.x3);
-  return (t.x0 >> 1) + g.hL0 * t.r;
+  return s.h + nb_offset(g, s, nu, +1) + nb_offset(g, s, rho, -1);
 }
 
 // Storage half index of the thread's own site (the plain lattice stores the
