@@ -79,7 +79,7 @@ def peaks():
 # one ncu capture of each kernel (profiles/*.md; batched: 128 threads x 6 blocks
 # per SM, the autotuner's usual choice); None
 # where the kernel changed after its last capture.
-NCU_TRAFFIC = {"fp64": 688.2e6, "fp32_mixed": 225.5e6, "fp32_eft": 225.6e6, "batched": 3.571e9}
+NCU_TRAFFIC = {"fp64": 687.8e6, "fp32_mixed": 226.7e6, "fp32_eft": 226.8e6, "batched": 3.460e9}
 
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA per
 # clock (1/64 of the 128 FP32 lanes) x 2 flop x 2.070 GHz = 1.2586 TFLOP/s
