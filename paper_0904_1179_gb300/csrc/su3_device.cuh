@@ -59,7 +59,7 @@ __host__ inline Divisor make_divisor(uint32_t d) {
   return Divisor{(uint32_t)((two + d - 1) / d), 31 + s};
 }
 
-__device__ __forceinline__ int udiv(int n, const Divisor& d) {
+__host__ __device__ __forceinline__ int udiv(int n, const Divisor& d) {
   return (int)(((unsigned long long)(uint32_t)n * d.m) >> d.shift);
 }
 
@@ -354,7 +354,7 @@ struct Site {
   int h;  // half index (x0 >> 1) + hL0 * r
 };
 
-__device__ __forceinline__ Site site_of(const Geometry& g, int h, int p) {
+__host__ __device__ __forceinline__ Site site_of(const Geometry& g, int h, int p) {
   Site st;
   const int r = udiv(h, g.div_hL0);
   const int x0e = 2 * (h - r * g.hL0);
@@ -368,13 +368,13 @@ __device__ __forceinline__ Site site_of(const Geometry& g, int h, int p) {
   return st;
 }
 
-__device__ __forceinline__ int canon(const Geometry& g, const Site& s) { return s.x0 + g.L0 * s.r; }
+__host__ __device__ __forceinline__ int canon(const Geometry& g, const Site& s) { return s.x0 + g.L0 * s.r; }
 
 // The half index is separable, h = (x0 >> 1) + hs1 x1 + hs2 x2 + hs3 x3, so
 // a step of d = +1 or -1 along nu changes it by an offset that depends only
 // on x_nu: +-hs[nu], or the wrap offset at the boundary; along x0 the step
 // changes x0 >> 1 by 0 or d, depending on the parity of x0.
-__device__ __forceinline__ int nb_offset(const Geometry& g, const Site& s, int nu, int d) {
+__host__ __device__ __forceinline__ int nb_offset(const Geometry& g, const Site& s, int nu, int d) {
   if (nu == 0) {
     if (d > 0) return s.x0 == g.L0 - 1 ? -g.wrap[0] : (s.x0 & 1);
     return s.x0 == 0 ? g.wrap[0] : (s.x0 & 1) - 1;
@@ -386,7 +386,7 @@ __device__ __forceinline__ int nb_offset(const Geometry& g, const Site& s, int n
 }
 
 // Half index of the neighbour x + d*nu-hat (d = +1 or -1), periodic.
-__device__ __forceinline__ int nb_half(const Geometry& g, const Site& s, int nu, int d) {
+__host__ __device__ __forceinline__ int nb_half(const Geometry& g, const Site& s, int nu, int d) {
   return s.h + nb_offset(g, s, nu, d);
 }
 
@@ -411,7 +411,7 @@ __device__ __forceinline__ int nb_half2_rt(const Geometry& g, const Site& s, int
 }
 
 // Half index of x + nu-hat - rho-hat for nu != rho.
-__device__ __forceinline__ int nb_half2(const Geometry& g, const Site& s, int nu, int rho) {
+__host__ __device__ __forceinline__ int nb_half2(const Geometry& g, const Site& s, int nu, int rho) {
   return s.h + nb_offset(g, s, nu, +1) + nb_offset(g, s, rho, -1);
 }
 
