@@ -336,14 +336,6 @@ __device__ __forceinline__ void acc_completed(mat3<T>& A, const mat3<T>& B) {
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void acc_full(mat3<T>& A, const mat3<T>& B) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) A.e[i][k] = add(A.e[i][k], B.e[i][k]);
-}
-
 // ---------------------------------------------------------------------------
 // Checkerboard geometry.  A thread owns half index h and parity p; its site
 // has x0 = 2*(h mod hL0) + ((p + x1 + x2 + x3) & 1).
