@@ -300,6 +300,26 @@ class OraclePool:
         os.remove(self.path)
 
 
+def host_cpu_model():
+    """Host CPU model as the OS reports it (lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline_sample(f32):
     """The oracle as it stands on the same 32^4 workload: on every host core (spawned
     processes on disjoint site subsets of each half-sweep, two full sweeps), and on one
@@ -324,7 +344,7 @@ def cpu_baseline_sample(f32):
     oracle.sweep(DIMS, BETA, SEED, 0, 1, U, f32=f32)
     dt = time.perf_counter() - t0
     one = 4 * 32 ** 4 / dt
-    return {"value": n / dt_all, "unit": UNIT, "cores": procs, "kind": "oracle",
+    return {"value": n / dt_all, "unit": UNIT, "cores": procs, "kind": "oracle", "cpu_model": host_cpu_model(),
             "sample": "two full sweeps (2*4*32^4 link updates) of the 32^4 beta=5.7 hot-start lattice, %s, "
                       "%d single-thread processes on disjoint site subsets of each half-sweep, %.1f s"
                       % ("FP32-mixed reading" if f32 else "FP64", procs, dt_all),
@@ -366,6 +386,7 @@ def run_reference(args):
                                    "one half-sweep (V/2 link updates) of the FP64 CPU oracle",
                        "lattice": list(DIMS), "beta": BETA},
             "cpu_baseline": {"value": ups, "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "cpu_model": host_cpu_model(),
                              "sample": "one checkerboard half-sweep of the 32^4 lattice per step, %d single-thread "
                                        "processes on disjoint site subsets" % procs},
             "e2e": {"value": ups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
