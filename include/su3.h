@@ -182,6 +182,17 @@ SU3_API int su3_info(su3_handle h, int dims[4], double* beta, uint64_t* seed, in
  * random numbers are keyed by its site. */
 SU3_API int su3_set_block_size(su3_handle h, int threads);
 
+/* Threads per link update of the one-hit half-sweep (an implementation
+ * choice; the paper has none): 0 = automatic (the default), 1 = one thread
+ * per link (FP64 and single-site FP32 stores) or per pair of links (FP32
+ * stores in the site-paired layout, L3 a multiple of 4), 4 = four lanes per
+ * link, which share the staple's paths (for small lattices, whose half-sweep
+ * leaves the GPU mostly idle).  Results do not depend on it: every form adds
+ * the staple in the same order and rounds every step identically.  Phases
+ * that measure the plaquette and the repeat-until-accepted heatbath always
+ * take the one-thread form.  Not for batch or decomposed handles: SU3_EINVAL. */
+SU3_API int su3_set_lanes(su3_handle h, int lanes);
+
 /* ---------------------------------------------------------------------------
  * Domain decomposition emulated on one device (Sec. 2.1, Eq. (MPInp), Tables
  * 1 and 2): the first ndmpi directions are cut into mpifactor parts each,
@@ -307,7 +318,8 @@ SU3_API int su3_status(su3_handle h);
  *     half-lattice structure of arrays indexed by h = s/2 (s the canonical
  *     site index; each parity holds one site of every pair 2h, 2h+1):
  *       SU3_FP64:       double2 [4 mu][2 parity][9 entries row*3+col][V/2]
- *       SU3_FP32_MIXED: float4  [4 mu][2 parity][3 columns k][V/2], rows 0
+ *       SU3_FP32_MIXED, SU3_FP32_EFT (the same store):
+ *                       float4  [4 mu][2 parity][3 columns k][V/2], rows 0
  *                       and 1 only: column k = (re u0k, re u1k, im u0k,
  *                       im u1k); row 2 is conj(row0 x row1).
  *   out: device pointer to one double that receives the mean plaquette, as
@@ -321,10 +333,13 @@ SU3_API int su3_status(su3_handle h);
  * calls share the one array: calls that overlap on the GPU (on different
  * streams, or from several host threads) race and return wrong results.  The
  * first call on each device looks up the array's device address with that
- * device current (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Errors: SU3_EINVAL (NULL pointer, odd or < 2 extent, bad
- * precision), SU3_ESIZE (too many sites), SU3_ECUDA (lookup or launch
- * failed); su3_last_error() describes them. */
+ * device current (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  The cache remembers the CUDA context it was
+ * filled in: after the context is destroyed and created again
+ * (cudaDeviceReset) the next call looks the address up again, so make that
+ * call, too, outside a capture.  Errors: SU3_EINVAL (NULL pointer, odd or
+ * < 2 extent, bad precision), SU3_ESIZE (too many sites), SU3_ECUDA (lookup
+ * or launch failed); su3_last_error() describes them. */
 SU3_API int su3_plaquette_noalloc(const void* links, int L0, int L1, int L2, int L3, int precision, double* out,
                                   void* cuda_stream);
 

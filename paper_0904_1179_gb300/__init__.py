@@ -21,7 +21,7 @@ __all__ = [
     "su3_create", "su3_create_ex", "su3_destroy", "su3_sweep", "su3_sweep_measured", "su3_half_sweep", "su3_plaquette",
     "su3_decomp_create", "su3_decomp_plan", "su3_decomp_info",
     "su3_links_get", "su3_links_set", "su3_sweep_count", "su3_set_sweep_count", "su3_set_stats", "su3_stats",
-    "su3_info", "su3_set_block_size", "su3_set_heatbath", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
+    "su3_info", "su3_set_block_size", "su3_set_lanes", "su3_set_heatbath", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
     "su3_batch_links_get", "su3_batch_links_set", "su3_batch_size", "su3_batch_config", "su3_batch_get_config",
     "su3_batch_autotune", "su3_batch_debug", "su3_status", "Batch", "su3_plaquette_noalloc", "su3_last_error", "su3_version", "Lattice", "links_shape", "EXPORTS",
 ]
@@ -69,6 +69,7 @@ EXPORTS = [
     ("su3_stats", ctypes.c_int, [_h, _pu64, _pu64]),
     ("su3_info", ctypes.c_int, [_h, _pi, _pd, _pu64, _pi]),
     ("su3_set_block_size", ctypes.c_int, [_h, ctypes.c_int]),
+    ("su3_set_lanes", ctypes.c_int, [_h, ctypes.c_int]),
     ("su3_set_heatbath", ctypes.c_int, [_h, ctypes.c_int]),
     ("su3_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _pd, _pu64, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(_h)]),
@@ -244,6 +245,11 @@ def su3_info(h):
 
 def su3_set_block_size(h, threads):
     _check(load_library().su3_set_block_size(h, threads))
+
+
+def su3_set_lanes(h, lanes):
+    """0: automatic; 1: one thread per link (or link pair); 4: four lanes per link."""
+    _check(load_library().su3_set_lanes(h, int(lanes)))
 
 
 def su3_set_heatbath(h, max_tries):
@@ -480,6 +486,9 @@ class Lattice:
 
     def set_block_size(self, threads):
         su3_set_block_size(self.handle, threads)
+
+    def set_lanes(self, lanes):
+        su3_set_lanes(self.handle, lanes)
 
     def set_heatbath(self, max_tries):
         su3_set_heatbath(self.handle, max_tries)

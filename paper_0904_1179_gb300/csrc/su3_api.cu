@@ -137,6 +137,8 @@ HalfSweepArgs half_sweep_args(const su3_lattice* h, int parity) {
   HalfSweepArgs a{};
   a.meas = nullptr;
   a.split = h->split;
+  a.pairs = h->pairs;
+  a.pgeom = h->pgeom;
   a.geom = h->geom;
   a.key = su3dev::philox_round_keys(h->key);
   a.parity = parity;
@@ -156,7 +158,7 @@ HalfSweepArgs half_sweep_args(const su3_lattice* h, int parity) {
 // plaquette of the updated configuration once, and a last kernel sums them
 // into the ring slot of this sweep.
 int enqueue_sweep_body(su3_lattice* h, bool measured) {
-  const int blocks = (h->geom.Vh + h->threads - 1) / h->threads;
+  const int blocks = su3k_half_sweep_blocks(half_sweep_args(h, 1), h->precision, h->threads);
   for (int mu = 0; mu < 4; ++mu)
     for (int p = 0; p < 2; ++p) {
       HalfSweepArgs a = half_sweep_args(h, p);
@@ -221,7 +223,8 @@ int ensure_transfer(su3_lattice* h, const char* what) {
 
 }  // namespace
 
-int su3_transfer(su3_lattice* h, const su3dev::Geometry& g, void* links, double* host, bool get, const char* what) {
+int su3_transfer(su3_lattice* h, const su3dev::Geometry& g, void* links, bool pairs, double* host, bool get,
+                 const char* what) {
   int rc = ensure_transfer(h, what);
   if (rc != SU3_OK) return rc;
   const long long V = 2LL * g.Vh;
@@ -232,7 +235,7 @@ int su3_transfer(su3_lattice* h, const su3dev::Geometry& g, void* links, double*
     const int b = i & 1;
     cudaStream_t cs = h->copy_stream;
     const size_t bytes = (size_t)n * 72 * sizeof(double);
-    ConvArgs a{g, h->precision, s0, n, stage[b], links};
+    ConvArgs a{g, h->precision, s0, n, stage[b], links, pairs ? 1 : 0};
     if (get) {
       // stage[b] is free once the copy-out of chunk i-2 has finished
       if (i >= 2) SU3_CUDA(cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0), what);
@@ -284,10 +287,19 @@ int su3_create_ex(int L0, int L1, int L2, int L3, double beta, uint64_t seed, in
   h->seed = seed;
   h->precision = precision;
   h->geom = su3dev::make_geometry(L0, L1, L2, L3);
+  h->pairs = precision != SU3_FP64 && su3_fp32_pairs(L3);
+  if (h->pairs) h->pgeom = su3dev::make_geometry(L0, L1, L2, L3 / 2);
   h->key.k0 = (uint32_t)seed;
   h->key.k1 = (uint32_t)(seed >> 32);
-  h->threads = default_threads(h->geom.Vh);
+  h->threads = default_threads(h->pairs ? h->pgeom.Vh : h->geom.Vh);
   h->split = use_split(h->geom.Vh, precision);
+  {
+    const cudaError_t ep = su3k_prepare();
+    if (ep != cudaSuccess) {
+      delete h;
+      return cuda_fail(ep, "su3_create: kernel attributes");
+    }
+  }
 
   cudaError_t e;
   if (cuda_stream) {
@@ -322,7 +334,7 @@ int su3_create_ex(int L0, int L1, int L2, int L3, double beta, uint64_t seed, in
     rc = cuda_fail(e, "su3_create: memset");
   }
   if (rc == SU3_OK) {
-    InitArgs ia{h->geom, su3dev::philox_round_keys(h->key), precision, h->links};
+    InitArgs ia{h->geom, su3dev::philox_round_keys(h->key), precision, h->links, h->pairs ? 1 : 0};
     e = su3k_launch_init(ia, start == SU3_HOT, h->stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "su3_create: start configuration");
   }
@@ -365,7 +377,7 @@ int su3_sweep_measured(su3_handle h, int nsweeps, double* plaq_out) {
   if (h->stats_on) return fail(SU3_EINVAL, "su3_sweep_measured: disable acceptance statistics first");
   if (su3_decomp_active(h)) return fail(SU3_EINVAL, "su3_sweep_measured: not available on a decomposed lattice");
   if (nsweeps == 0) return SU3_OK;
-  const int blocks = (h->geom.Vh + h->threads - 1) / h->threads;
+  const int blocks = su3k_half_sweep_blocks(half_sweep_args(h, 1), h->precision, h->threads);
   if (h->meas_blocks != blocks || !h->d_meas) {
     SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_sweep_measured");
     if (h->graph_meas) {
@@ -423,7 +435,7 @@ double su3_plaquette(su3_handle h) {
     return NAN;
   }
   if (su3_decomp_sync_global(h) != SU3_OK) return NAN;
-  PlaqArgs a{h->geom, h->links, h->d_partials};
+  PlaqArgs a{h->geom, h->links, h->d_partials, h->pairs ? 1 : 0};
   cudaError_t e = su3k_launch_plaquette(a, h->precision, h->d_plaq, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_plaq, h->d_plaq, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -440,14 +452,14 @@ int su3_links_get(su3_handle h, double* host, size_t n_doubles) {
   if (n_doubles != (size_t)h->V * 72) return fail(SU3_ESIZE, "su3_links_get: n = %zu, expected %lld", n_doubles, h->V * 72);
   const int rc = su3_decomp_sync_global(h);
   if (rc != SU3_OK) return rc;
-  return su3_transfer(h, h->geom, h->links, host, true, "su3_links_get");
+  return su3_transfer(h, h->geom, h->links, h->pairs, host, true, "su3_links_get");
 }
 
 int su3_links_set(su3_handle h, const double* host, size_t n_doubles) {
   if (!h || !host) return fail(SU3_EINVAL, "su3_links_set: NULL argument");
   if (is_batch(h)) return fail(SU3_EINVAL, "su3_links_set: batch handle (use the su3_batch_* calls)");
   if (n_doubles != (size_t)h->V * 72) return fail(SU3_ESIZE, "su3_links_set: n = %zu, expected %lld", n_doubles, h->V * 72);
-  const int rc = su3_transfer(h, h->geom, h->links, const_cast<double*>(host), false, "su3_links_set");
+  const int rc = su3_transfer(h, h->geom, h->links, h->pairs, const_cast<double*>(host), false, "su3_links_set");
   if (rc == SU3_OK) su3_decomp_global_written(h);
   return rc;
 }
@@ -510,10 +522,24 @@ int su3_set_heatbath(su3_handle h, int max_tries) {
   return SU3_OK;
 }
 
+int su3_set_lanes(su3_handle h, int lanes) {
+  if (!h) return fail(SU3_EINVAL, "su3_set_lanes: NULL handle");
+  if (is_batch(h) || su3_decomp_active(h))
+    return fail(SU3_EINVAL, "su3_set_lanes: not for batch or decomposed handles");
+  if (lanes != 0 && lanes != 1 && lanes != 4) return fail(SU3_EINVAL, "su3_set_lanes: lanes %d not 0, 1 or 4", lanes);
+  const bool split = lanes == 0 ? use_split(h->geom.Vh, h->precision) : lanes == 4;
+  if (split != h->split) {
+    SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_set_lanes");
+    drop_graphs(h);
+    h->split = split;
+  }
+  return SU3_OK;
+}
+
 int su3_set_block_size(su3_handle h, int threads) {
   if (!h) return fail(SU3_EINVAL, "su3_set_block_size: NULL handle");
   if (is_batch(h)) return fail(SU3_EINVAL, "su3_set_block_size: batch handle (use the su3_batch_* calls)");
-  if (threads == 0) threads = default_threads(h->geom.Vh);
+  if (threads == 0) threads = default_threads(h->pairs ? h->pgeom.Vh : h->geom.Vh);
   if (threads < 32 || threads > kMaxSweepThreads || (threads & 31))
     return fail(SU3_EINVAL, "su3_set_block_size: %d is not a multiple of 32 in [32, %d]", threads, kMaxSweepThreads);
   if (threads != h->threads) {

@@ -483,7 +483,8 @@ int su3_batch_create(int n, const int (*dims)[4], const double* betas, const uin
     rc = su3_cuda_fail(e, "su3_batch_create: memset");
   for (int r = 0; r < n && rc == SU3_OK; ++r) {
     PhiloxKey k{(uint32_t)seeds[r], (uint32_t)(seeds[r] >> 32)};
-    InitArgs ia{b->geoms[r], philox_round_keys(k), precision, (char*)h->links + b->offsets[r] * b->elem_bytes};
+    // replicas keep one site per FP32 column group (the persistent kernel runs the single-site update)
+    InitArgs ia{b->geoms[r], philox_round_keys(k), precision, (char*)h->links + b->offsets[r] * b->elem_bytes, 0};
     e = su3k_launch_init(ia, start == SU3_HOT, h->stream);
     if (e != cudaSuccess) rc = su3_cuda_fail(e, "su3_batch_create: start configuration");
   }
@@ -527,7 +528,7 @@ int su3_batch_plaquettes(su3_handle h, double* out_n) {
   su3_batch* b = batch_of(h);
   if (!b || !out_n) return fail(SU3_EINVAL, "su3_batch_plaquettes: not a batch handle or NULL output");
   for (int r = 0; r < b->n; ++r) {
-    PlaqArgs a{b->geoms[r], (const char*)h->links + b->offsets[r] * b->elem_bytes, h->d_partials};
+    PlaqArgs a{b->geoms[r], (const char*)h->links + b->offsets[r] * b->elem_bytes, h->d_partials, 0};
     SU3_CUDA(su3k_launch_plaquette(a, h->precision, b->d_plaq_n + r, h->stream), "su3_batch_plaquettes");
   }
   SU3_CUDA(cudaMemcpyAsync(b->h_plaq_n, b->d_plaq_n, (size_t)b->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
@@ -547,7 +548,7 @@ static int batch_links(su3_handle h, int replica, double* host, size_t n_doubles
   const long long V = 2LL * g.Vh;
   if (n_doubles != (size_t)V * 72) return su3_fail(SU3_ESIZE, "%s: n = %zu, expected %lld", what, n_doubles, V * 72);
   void* base = (char*)h->links + b->offsets[replica] * b->elem_bytes;
-  const int rc = su3_transfer(h, g, base, host, get, what);
+  const int rc = su3_transfer(h, g, base, false, host, get, what);
   if (rc != SU3_OK) return rc;
   return check_status(h, what);
 }

@@ -150,6 +150,39 @@ __global__ void k_decomp_move(SubGeometry base, int nf, int ndmpi, E* global, in
   }
 }
 
+// The same move for an FP32 global store in the site-paired layout
+// (su3_sitepair.cuh; the sublattice stores keep one site per column group).
+template <bool TO_SUBS>
+__global__ void k_decomp_move_f32_pairs(SubGeometry base, int nf, int ndmpi, float4* global, int Vh_global,
+                                        float4* subs, size_t sub_elems) {
+  const int k = blockIdx.y, p = blockIdx.z;
+  const SubGeometry g = sub_geometry(base, nf, ndmpi, k);
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= g.in.Vh) return;
+  const SubSite st = site_of(g, h, p);
+  const int hg = st.s >> 1;
+  const int hs = store_index(g, st, h);
+  float4* sub = subs + (size_t)k * sub_elems;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    float r[12];
+    if (TO_SUBS) {
+      load_pair_site(global, mu, p, hg, Vh_global / 2, r);
+      store_f32_rows01(sub, mu, p, hs, g.Vh, r);
+    } else {
+      const mat3<float> m = load_f32_rows01(sub, mu, p, hs, g.Vh);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        r[2 * c] = m.e[0][c].re;
+        r[2 * c + 1] = m.e[0][c].im;
+        r[6 + 2 * c] = m.e[1][c].re;
+        r[6 + 2 * c + 1] = m.e[1][c].im;
+      }
+      store_pair_site(global, mu, p, hg, Vh_global / 2, r);
+    }
+  }
+}
+
 template <int MU>
 cudaError_t launch_update_mu(const DecompArgs& a, int precision, bool stats, int threads, int np, cudaStream_t s) {
   const dim3 grid((a.g.in.Vh + threads - 1) / threads, np);
@@ -205,6 +238,13 @@ cudaError_t launch_move(const su3_lattice* h, bool to_subs) {
     else
       k_decomp_move<double2, kEntriesF64, false><<<grid, threads, 0, h->stream>>>(
           d->geo, d->nf, d->ndmpi, (double2*)h->links, h->geom.Vh, (double2*)d->d_sub, d->sub_elems);
+  } else if (h->pairs) {
+    if (to_subs)
+      k_decomp_move_f32_pairs<true><<<grid, threads, 0, h->stream>>>(d->geo, d->nf, d->ndmpi, (float4*)h->links,
+                                                                      h->geom.Vh, (float4*)d->d_sub, d->sub_elems);
+    else
+      k_decomp_move_f32_pairs<false><<<grid, threads, 0, h->stream>>>(d->geo, d->nf, d->ndmpi, (float4*)h->links,
+                                                                       h->geom.Vh, (float4*)d->d_sub, d->sub_elems);
   } else {
     if (to_subs)
       k_decomp_move<float4, kGroupsF32, true><<<grid, threads, 0, h->stream>>>(

@@ -229,6 +229,13 @@ template <typename T>
 __device__ __forceinline__ cx<T> mul(cx<T> a, cx<T> b) {
   return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
 }
+// FP32 product with every rounding step written out (no contraction left to
+// the compiler), so that the single-site and the site-paired FP32 updates
+// (su3_sitepair.cuh) round identically: re = fma(-a.im, b.im, a.re b.re),
+// im = fma(a.im, b.re, a.re b.im).
+__device__ __forceinline__ cx<float> mul(cx<float> a, cx<float> b) {
+  return mk(__fmaf_rn(-a.im, b.im, __fmul_rn(a.re, b.re)), __fmaf_rn(a.im, b.re, __fmul_rn(a.re, b.im)));
+}
 // acc + a*b
 template <typename T>
 __device__ __forceinline__ cx<T> mac(cx<T> acc, cx<T> a, cx<T> b) {
@@ -635,7 +642,7 @@ __device__ __forceinline__ void reunitarise_f32(const cx<float> a[3], const cx<f
     const float inv_n0 = 1.0f - e0;  // 1/n0 to O(e0^2)
     cr = dr * inv_n0;
     ci = di * inv_n0;
-    e1 = ((h1 - 1.0f) + l1) - (cr * dr + ci * di);
+    e1 = ((h1 - 1.0f) + l1) - __fmaf_rn(ci, di, __fmul_rn(cr, dr));
   } else {
     double n0 = 0.0, n1 = 0.0, dre = 0.0, dim = 0.0;
 #pragma unroll
@@ -652,7 +659,7 @@ __device__ __forceinline__ void reunitarise_f32(const cx<float> a[3], const cx<f
     const float inv_n0 = 1.0f - e0;  // 1/n0 to O(e0^2)
     cr = dr * inv_n0;
     ci = di * inv_n0;
-    e1 = (float)(n1 - 1.0) - (cr * dr + ci * di);
+    e1 = (float)(n1 - 1.0) - __fmaf_rn(ci, di, __fmul_rn(cr, dr));
   }
   if (fabsf(e0) < 1e-3f && fabsf(e1) < 1e-3f && fabsf(dr) < 1e-3f && fabsf(di) < 1e-3f) {
     const float s0 = e0 * fmaf(0.375f, e0, -0.5f);

@@ -12,6 +12,7 @@
 #include "su3_kernels.h"
 
 #include "su3_device.cuh"
+#include "su3_sitepair.cuh"
 #include "su3_update.cuh"
 
 using namespace su3dev;
@@ -143,7 +144,7 @@ __device__ __forceinline__ pm3 shfl_pm3_rows01(const pm3& m, int src) {
   return r;
 }
 
-template <int MU, bool STATS, bool EFT>
+template <int MU, bool STATS, bool EFT, bool PAIRS>
 __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f32_split(HalfSweepArgs args) {
   const Geometry& g = args.geom;
   const int p = args.parity;
@@ -157,8 +158,8 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f32_split(HalfS
   if (part < 3) {
     const int nu = part < MU ? part : part + 1;
     const int h_pmu = nb_half(g, st, MU, +1);
-    F = forward_path_p<false>(g, U, h, p, MU, nu, h_pmu, nb_half_rt(g, st, nu, +1));
-    B = backward_path_p<false>(g, U, p, MU, nu, nb_half_rt(g, st, nu, -1), nb_half2_rt(g, st, MU, nu));
+    F = forward_path_p<false, PAIRS>(g, U, h, p, MU, nu, h_pmu, nb_half_rt(g, st, nu, +1));
+    B = backward_path_p<false, PAIRS>(g, U, p, MU, nu, nb_half_rt(g, st, nu, -1), nb_half2_rt(g, st, MU, nu));
   }
   const int lane0 = (threadIdx.x & 31) & ~3;
   pm3 A;
@@ -172,8 +173,8 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f32_split(HalfS
   UpdateCount c{0, 0};
   if (part == 0 && active) {
     const UpdateConsts uc{args.three_over_beta_f64, args.three_over_beta, 1};
-    c = heatbath_f32<MU, false, EFT, false, false>(g, U, h, p, *args.sweep, (uint32_t)canon(g, st), args.key, uc, A,
-                                                    A, nullptr);
+    c = heatbath_f32_on<MU, EFT, false, false, PAIRS>(g, U, h, p, *args.sweep, (uint32_t)canon(g, st), args.key, uc, A,
+                                                       A, nullptr, load_pm3_l<false, PAIRS>(U, MU, p, h, g.Vh), true);
   }
   count_stats<STATS>(c, args.stats);
 }
@@ -227,7 +228,7 @@ __global__ void k_cold_start(InitArgs args) {
     store_f64((double2*)args.links, mu, p, h, g.Vh, m);
   } else {
     float o[12] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f};
-    store_f32_rows01((float4*)args.links, mu, p, h, g.Vh, o);
+    store_f32_rows01_any((float4*)args.links, mu, p, h, g.Vh, args.pairs, o);
   }
 }
 
@@ -277,7 +278,7 @@ __global__ void k_hot_start(InitArgs args) {
       o[6 + 2 * k] = (float)r1[k].re;
       o[6 + 2 * k + 1] = (float)r1[k].im;
     }
-    store_f32_rows01((float4*)args.links, mu, p, h, g.Vh, o);
+    store_f32_rows01_any((float4*)args.links, mu, p, h, g.Vh, args.pairs, o);
   }
 }
 
@@ -286,29 +287,29 @@ __global__ void k_hot_start(InitArgs args) {
 // block reduction into partials[blockIdx.x], then one block sums the partials.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ mat3<T> load_any(const void* U, int mu, int p, int h, int Vh);
+__device__ __forceinline__ mat3<T> load_any(const void* U, int mu, int p, int h, int Vh, bool pairs);
 template <>
-__device__ __forceinline__ mat3<double> load_any<double>(const void* U, int mu, int p, int h, int Vh) {
+__device__ __forceinline__ mat3<double> load_any<double>(const void* U, int mu, int p, int h, int Vh, bool) {
   return load_f64((const double2*)U, mu, p, h, Vh);
 }
 template <>
-__device__ __forceinline__ mat3<float> load_any<float>(const void* U, int mu, int p, int h, int Vh) {
-  return load_f32((const float4*)U, mu, p, h, Vh);
+__device__ __forceinline__ mat3<float> load_any<float>(const void* U, int mu, int p, int h, int Vh, bool pairs) {
+  return load_f32_any((const float4*)U, mu, p, h, Vh, pairs);
 }
 
 // Re Tr(X Y^+) with X = U_mu(x) U_nu(x+mu), Y = U_nu(x) U_mu(x+nu).
 template <typename T>
-__device__ __forceinline__ double plaq_site(const Geometry& g, const void* U, const Site& st, int h, int p) {
+__device__ __forceinline__ double plaq_site(const Geometry& g, const void* U, const Site& st, int h, int p, bool pairs) {
   const int q = p ^ 1;
   double sum = 0.0;
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu)
 #pragma unroll
     for (int nu = mu + 1; nu < 4; ++nu) {
-      const mat3<T> a = load_any<T>(U, mu, p, h, g.Vh);
-      const mat3<T> b = load_any<T>(U, nu, q, nb_half(g, st, mu, +1), g.Vh);
-      const mat3<T> c = load_any<T>(U, nu, p, h, g.Vh);
-      const mat3<T> d = load_any<T>(U, mu, q, nb_half(g, st, nu, +1), g.Vh);
+      const mat3<T> a = load_any<T>(U, mu, p, h, g.Vh, pairs);
+      const mat3<T> b = load_any<T>(U, nu, q, nb_half(g, st, mu, +1), g.Vh, pairs);
+      const mat3<T> c = load_any<T>(U, nu, p, h, g.Vh, pairs);
+      const mat3<T> d = load_any<T>(U, mu, q, nb_half(g, st, nu, +1), g.Vh, pairs);
       T tr = T(0);
 #pragma unroll
       for (int i = 0; i < 3; ++i)
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(256) k_plaquette_partial(PlaqArgs args) {
     const int p = idx >= g.Vh ? 1 : 0;
     const int h = idx - p * g.Vh;
     const Site st = site_of(g, h, p);
-    v = plaq_site<T>(g, args.links, st, h, p);
+    v = plaq_site<T>(g, args.links, st, h, p, args.pairs != 0);
   }
   __shared__ double red[32];
 #pragma unroll
@@ -401,7 +402,7 @@ __global__ void k_canon_to_store(ConvArgs args) {
     float o[12];
 #pragma unroll
     for (int c = 0; c < 12; ++c) o[c] = (float)src[c];
-    store_f32_rows01((float4*)args.links, mu, p, h, g.Vh, o);
+    store_f32_rows01_any((float4*)args.links, mu, p, h, g.Vh, args.pairs, o);
   }
 }
 
@@ -426,7 +427,7 @@ __global__ void k_store_to_canon(ConvArgs args) {
       dst[2 * c + 1] = m.e[c / 3][c % 3].im;
     }
   } else {
-    const mat3<float> m = load_f32_rows01((const float4*)args.links, mu, p, h, g.Vh);
+    const mat3<float> m = load_f32_rows01_any((const float4*)args.links, mu, p, h, g.Vh, args.pairs);
     cx<double> a[3], b[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -476,10 +477,22 @@ static cudaError_t launch_prec(const HalfSweepArgs& a, int precision, int blocks
   return launch_f32<MU, STATS, false, REPEAT, MEAS>(a, blocks, threads, s);
 }
 
+template <int MU, bool STATS, bool EFT>
+static void launch_f32_split(const HalfSweepArgs& a, int blocks, int threads, cudaStream_t s) {
+  if (a.pairs)
+    k_half_sweep_f32_split<MU, STATS, EFT, true><<<blocks, threads, 0, s>>>(a);
+  else
+    k_half_sweep_f32_split<MU, STATS, EFT, false><<<blocks, threads, 0, s>>>(a);
+}
+
 template <int MU>
 static cudaError_t launch_half_sweep_mu(const HalfSweepArgs& a, int precision, bool stats, int threads, cudaStream_t s) {
   const int blocks = (a.geom.Vh + threads - 1) / threads;
   const bool repeat = a.max_tries > 1;
+  // FP32 in the site-paired layout: the paired kernel, except for the
+  // four-lane form of small lattices
+  if (precision != 0 && a.pairs && !(a.split && !repeat && !(MU > 0 && a.meas)))
+    return su3k_launch_half_sweep_pair(a, MU, precision == 2, stats, threads, s);
   if (MU > 0 && a.meas) {  // fused plaquette (statistics are not counted in these phases)
     return repeat ? launch_prec<MU, false, true, (MU > 0)>(a, precision, blocks, threads, s)
                   : launch_prec<MU, false, false, (MU > 0)>(a, precision, blocks, threads, s);
@@ -493,14 +506,14 @@ static cudaError_t launch_half_sweep_mu(const HalfSweepArgs& a, int precision, b
         k_half_sweep_f64_split<MU, false><<<sblocks, threads, 0, s>>>(a);
     } else if (precision == 2) {
       if (stats)
-        k_half_sweep_f32_split<MU, true, true><<<sblocks, threads, 0, s>>>(a);
+        launch_f32_split<MU, true, true>(a, sblocks, threads, s);
       else
-        k_half_sweep_f32_split<MU, false, true><<<sblocks, threads, 0, s>>>(a);
+        launch_f32_split<MU, false, true>(a, sblocks, threads, s);
     } else {
       if (stats)
-        k_half_sweep_f32_split<MU, true, false><<<sblocks, threads, 0, s>>>(a);
+        launch_f32_split<MU, true, false>(a, sblocks, threads, s);
       else
-        k_half_sweep_f32_split<MU, false, false><<<sblocks, threads, 0, s>>>(a);
+        launch_f32_split<MU, false, false>(a, sblocks, threads, s);
     }
     return cudaGetLastError();
   }
@@ -518,6 +531,11 @@ cudaError_t su3k_launch_half_sweep(const HalfSweepArgs& a, int mu, int precision
     case 2: return launch_half_sweep_mu<2>(a, precision, stats, threads, s);
     default: return launch_half_sweep_mu<3>(a, precision, stats, threads, s);
   }
+}
+
+int su3k_half_sweep_blocks(const HalfSweepArgs& a, int precision, int threads) {
+  const int n = (precision != 0 && a.pairs) ? a.pgeom.Vh : a.geom.Vh;
+  return (n + threads - 1) / threads;
 }
 
 cudaError_t su3k_launch_increment(uint64_t* counter, uint64_t n, cudaStream_t s) {

@@ -23,6 +23,8 @@ struct HalfSweepArgs {
   unsigned long long* stats;  // [accepted, proposed], used when counting
   double* meas;               // fused plaquette: per-block partial sums of this phase (nullptr: off)
   int split;                  // FP64 one-hit sweep of a small lattice: four lanes per link (see k_half_sweep_f64_split)
+  int pairs;                  // FP32 store in the site-paired layout (L3 a multiple of 4; su3_sitepair.cuh)
+  su3dev::Geometry pgeom;     // the pair lattice L0 x L1 x L2 x L3/2 (pairs only)
 };
 
 struct InitArgs {
@@ -30,12 +32,14 @@ struct InitArgs {
   su3dev::PhiloxRoundKeys key;
   int precision;
   void* links;
+  int pairs;  // FP32 store in the site-paired layout
 };
 
 struct PlaqArgs {
   su3dev::Geometry geom;
   const void* links;
   double* partials;
+  int pairs;  // FP32 store in the site-paired layout
 };
 
 struct ConvArgs {
@@ -44,9 +48,24 @@ struct ConvArgs {
   long long s_begin, n_sites;
   double* canon;  // device staging buffer, canonical layout of the chunk
   void* links;
+  int pairs;  // FP32 store in the site-paired layout
 };
 
+// Whether an FP32 store of an L0 x L1 x L2 x L3 lattice uses the site-paired
+// layout (su3_sitepair.cuh): L3 a multiple of 4.
+inline bool su3_fp32_pairs(int L3) { return L3 % 4 == 0; }
+
 cudaError_t su3k_launch_half_sweep(const HalfSweepArgs& a, int mu, int precision, bool stats, int threads, cudaStream_t s);
+// Blocks of one half-sweep launch (the partial sums of the fused plaquette
+// come one per block).
+int su3k_half_sweep_blocks(const HalfSweepArgs& a, int precision, int threads);
+// The site-paired FP32 half-sweep (su3_kernels_pair.cu): one thread per pair
+// of links, the staple's loads staged through shared memory.
+cudaError_t su3k_launch_half_sweep_pair(const HalfSweepArgs& a, int mu, bool eft, bool stats, int threads, cudaStream_t s);
+// Dynamic shared memory per thread of the site-paired half-sweep, and the
+// kernel attributes it needs (set once, before any stream capture).
+constexpr int kPairRingBytesPerThread = 3 * 7 * 16;
+cudaError_t su3k_prepare();
 cudaError_t su3k_launch_increment(uint64_t* counter, uint64_t n, cudaStream_t s);
 // Sum the nparts fused-plaquette partials of one sweep (fixed order) into
 // out[*sweep % cap] * scale.

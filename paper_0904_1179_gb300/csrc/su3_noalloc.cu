@@ -9,7 +9,10 @@
 // them the reduction's scratch -- one partial sum per thread block -- lives in
 // a fixed file-scope device array instead of a handle's cudaMalloc'd buffer.
 // Every GPU that loads libsu3 holds this array (512 KiB) until the process
-// exits.
+// exits.  The kernels are the library's plaquette kernels (su3_kernels.cu),
+// launched with that array as their partial-sum buffer.
+#include <cuda.h>
+
 #include <cstdio>
 #include <mutex>
 
@@ -21,100 +24,32 @@ using namespace su3dev;
 
 namespace {
 
-constexpr int kThreads = 256;  // sites per block of the partial-sum kernel
-// One FP64 partial per block: 65,536 blocks of 256 sites covers lattices up to
-// 2^24 sites (64^4).
+// One FP64 partial per block of the plaquette kernel (256 sites): 65,536
+// partials cover lattices up to 2^24 sites (64^4).
 constexpr int kMaxPartials = 1 << 16;
-constexpr long long kMaxSites = (long long)kMaxPartials * kThreads;
+constexpr long long kMaxSites = (long long)kMaxPartials * 256;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_plaq_scratch[kMaxPartials];
 
+// Device address of the array per device ordinal, with the identity of the
+// CUDA context it was looked up in: a context that was torn down and created
+// again (cudaDeviceReset) loads the module afresh, possibly at another
+// address, so the address is looked up again when the context changes.
+struct ScratchEntry {
+  double* addr;
+  unsigned long long ctx_id;
+  bool ctx_known;
+};
+
 std::mutex g_setup_mutex;
-double* g_scratch_addr[kMaxDevices] = {};
+ScratchEntry g_scratch[kMaxDevices] = {};
 
-template <typename T>
-__device__ __forceinline__ mat3<T> load_link(const void* U, int mu, int p, int h, int Vh);
-template <>
-__device__ __forceinline__ mat3<double> load_link<double>(const void* U, int mu, int p, int h, int Vh) {
-  return load_f64((const double2*)U, mu, p, h, Vh);
-}
-template <>
-__device__ __forceinline__ mat3<float> load_link<float>(const void* U, int mu, int p, int h, int Vh) {
-  return load_f32((const float4*)U, mu, p, h, Vh);
-}
-
-// Sum over the six planes at one site of Re Tr(X Y^+), X = U_mu(x) U_nu(x+mu), Y = U_nu(x) U_mu(x+nu).
-template <typename T>
-__device__ __forceinline__ double site_plaquettes(const Geometry& g, const void* U, const Site& st, int h, int p) {
-  const int q = p ^ 1;
-  double sum = 0.0;
-#pragma unroll
-  for (int mu = 0; mu < 4; ++mu)
-#pragma unroll
-    for (int nu = mu + 1; nu < 4; ++nu) {
-      const mat3<T> a = load_link<T>(U, mu, p, h, g.Vh);
-      const mat3<T> b = load_link<T>(U, nu, q, nb_half(g, st, mu, +1), g.Vh);
-      const mat3<T> c = load_link<T>(U, nu, p, h, g.Vh);
-      const mat3<T> d = load_link<T>(U, mu, q, nb_half(g, st, nu, +1), g.Vh);
-      T tr = T(0);
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          cx<T> x = mk(T(0), T(0)), y = x;
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            x = mac(x, a.e[i][j], b.e[j][k]);
-            y = mac(y, c.e[i][j], d.e[j][k]);
-          }
-          tr = fma(x.re, y.re, tr);
-          tr = fma(x.im, y.im, tr);
-        }
-      sum += (double)tr;
-    }
-  return sum;
-}
-
-// Block b writes partials[b]; every entry read by the final kernel is written
-// first in the same call, so nothing in the scratch has to start at zero.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_noalloc_partial(Geometry g, const void* U, double* partials) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // over 2 * Vh: (parity, h)
-  double v = 0.0;
-  if (idx < 2 * g.Vh) {
-    const int p = idx >= g.Vh ? 1 : 0;
-    const int h = idx - p * g.Vh;
-    v = site_plaquettes<T>(g, U, site_of(g, h, p), h, p);
-  }
-  __shared__ double red[kThreads / 32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double w = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    if (threadIdx.x == 0) partials[blockIdx.x] = w;
-  }
-}
-
-__global__ void __launch_bounds__(1024) k_noalloc_final(const double* partials, int n, double scale, double* out) {
-  __shared__ double red[32];
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v += partials[i];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double w = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    if (threadIdx.x == 0) *out = w * scale;
-  }
-}
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+bool g_entry_resolved = false;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
 
 int fail(int code, const char* msg) {
   char m[256];
@@ -122,22 +57,52 @@ int fail(int code, const char* msg) {
   return su3_internal_fail(code, m);
 }
 
+// Unique id of the calling thread's current context (false if there is none
+// or the driver cannot tell).  The driver calls are resolved through the
+// runtime, so libsu3 does not link the driver library.  Called with
+// g_setup_mutex held.
+bool current_context_id(unsigned long long* id) {
+  if (!g_entry_resolved) {
+    g_entry_resolved = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get_current = (CtxGetCurrentFn)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get_id = (CtxGetIdFn)f;
+  }
+  if (!g_ctx_get_current || !g_ctx_get_id) return false;
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return g_ctx_get_id(ctx, id) == CUDA_SUCCESS;
+}
+
 // Device address of the scratch array on the current device.  The host-side
 // name g_plaq_scratch is only a stand-in for the symbol, so the address is
-// looked up once per device with that device current and then cached.
+// looked up with the device current (cudaGetSymbolAddress) on the first call
+// in each context and cached.
 int scratch_address(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(SU3_ECUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(SU3_ECUDA, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  ScratchEntry& ent = g_scratch[dev];
+  unsigned long long id = 0;
+  const bool have_id = current_context_id(&id);
+  if (!ent.addr || (have_id && ent.ctx_known && id != ent.ctx_id)) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_plaq_scratch);
     if (e != cudaSuccess || !p) return fail(SU3_ECUDA, e != cudaSuccess ? cudaGetErrorString(e) : "null symbol address");
-    g_scratch_addr[dev] = (double*)p;
+    ent.addr = (double*)p;
+    // the lookup binds the runtime's context if none was current before
+    ent.ctx_known = have_id || current_context_id(&id);
+    ent.ctx_id = id;
   }
-  *out = g_scratch_addr[dev];
+  *out = ent.addr;
   return SU3_OK;
 }
 
@@ -149,28 +114,29 @@ extern "C" SU3_API int su3_plaquette_noalloc(const void* links, int L0, int L1, 
   const int L[4] = {L0, L1, L2, L3};
   for (int mu = 0; mu < 4; ++mu)
     if (L[mu] < 2 || (L[mu] & 1)) return fail(SU3_EINVAL, "every extent must be even and >= 2");
-  if (precision != SU3_FP64 && precision != SU3_FP32_MIXED) return fail(SU3_EINVAL, "bad precision");
-  const long long V = (long long)L0 * L1 * L2 * L3;
-  if (V > kMaxSites) {
-    char m[160];
-    snprintf(m, sizeof m, "lattice of %lld sites exceeds the fixed scratch of %d partial sums (at most %lld sites, 64^4)",
-             V, kMaxPartials, kMaxSites);
-    return fail(SU3_ESIZE, m);
+  if (precision != SU3_FP64 && precision != SU3_FP32_MIXED && precision != SU3_FP32_EFT)
+    return fail(SU3_EINVAL, "bad precision");
+  // the site count, one factor at a time, so that no product can overflow
+  long long V = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    V *= L[mu];
+    if (V > kMaxSites) {
+      char m[160];
+      snprintf(m, sizeof m, "lattice of more than %lld sites exceeds the fixed scratch of %d partial sums (64^4)",
+               kMaxSites, kMaxPartials);
+      return fail(SU3_ESIZE, m);
+    }
   }
+  const Geometry g = make_geometry(L0, L1, L2, L3);
+  if (su3k_plaquette_blocks(g) > kMaxPartials) return fail(SU3_ESIZE, "more partial sums than the fixed scratch holds");
   double* scratch = nullptr;
   const int rc = scratch_address(&scratch);
   if (rc != SU3_OK) return rc;
-  const Geometry g = make_geometry(L0, L1, L2, L3);
-  const int blocks = (int)((V + kThreads - 1) / kThreads);
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  if (precision == SU3_FP64)
-    k_noalloc_partial<double><<<blocks, kThreads, 0, s>>>(g, links, scratch);
-  else
-    k_noalloc_partial<float><<<blocks, kThreads, 0, s>>>(g, links, scratch);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(SU3_ECUDA, cudaGetErrorString(e));
-  k_noalloc_final<<<1, 1024, 0, s>>>(scratch, blocks, 1.0 / (3.0 * 6.0 * (double)V), out);
-  e = cudaGetLastError();
+  // SU3_FP32_MIXED and SU3_FP32_EFT share the FP32 two-row store, site-paired when L3 is a multiple of 4
+  const int pairs = precision != SU3_FP64 && su3_fp32_pairs(L3) ? 1 : 0;
+  const cudaError_t e = su3k_launch_plaquette(PlaqArgs{g, links, scratch, pairs},
+                                              precision == SU3_FP64 ? SU3_FP64 : SU3_FP32_MIXED, out,
+                                              (cudaStream_t)cuda_stream);
   if (e != cudaSuccess) return fail(SU3_ECUDA, cudaGetErrorString(e));
   return SU3_OK;
 }

@@ -49,7 +49,9 @@ struct su3_lattice {
   int threads = kSu3DefaultThreads;
   int max_tries = 1;  // SU(2) proposals per subgroup (1: one-hit heatbath)
   bool split = false;  // small FP64 lattice: four lanes per link update
+  bool pairs = false;  // FP32 store in the site-paired layout (L3 a multiple of 4)
   su3dev::Geometry geom{};
+  su3dev::Geometry pgeom{};  // pair lattice L0 x L1 x L2 x L3/2 (pairs only)
   su3dev::PhiloxKey key{};
   su3_batch* batch = nullptr;    // non-null for a batch of replicas
   su3_decomp* decomp = nullptr;  // non-null for a decomposed lattice (su3_decomp_create)
@@ -63,7 +65,8 @@ int su3_sync(su3_lattice* h, const char* what);
 // buffer in the canonical layout, chunk by chunk: host<->device copies on a
 // second stream overlap the layout conversions on the handle's stream.
 // Synchronises.
-int su3_transfer(su3_lattice* h, const su3dev::Geometry& g, void* links, double* host, bool get, const char* what);
+int su3_transfer(su3_lattice* h, const su3dev::Geometry& g, void* links, bool pairs, double* host, bool get,
+                 const char* what);
 // Free a handle and everything it owns (batch part included).
 void su3_release_handle(su3_lattice* h);
 // Free the batch part of a handle (defined in su3_batch.cu).

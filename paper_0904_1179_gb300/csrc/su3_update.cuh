@@ -51,6 +51,54 @@ struct Store<float, CG> {
   }
 };
 
+// The FP32 stores come in two layouts: one site per float4 column group (the
+// single-site layout) and the site-paired layout of su3_sitepair.cuh, which
+// stores the sites x and x + (L3/2) e3 of a lattice whose L3 is a multiple of
+// 4 side by side.  Single-site code reads and writes the latter one site at a
+// time (PAIRS = true); Vh is the full lattice's half volume in both.
+template <bool CG, bool PAIRS>
+__device__ __forceinline__ pm3 load_pm3_l(const float4* __restrict__ U, int mu, int p, int h, int Vh) {
+  if constexpr (PAIRS) {
+    const int Vp = Vh / 2;
+    const int half = h >= Vp ? 1 : 0;
+    const float* b = (const float*)(U + link_base(mu, p, Vp, 6) + (h - half * Vp)) + half;
+    pm3 m;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float* e0 = b + (size_t)4 * k * Vp;        // entry (row 0, column k)
+      const float* e1 = b + (size_t)4 * (3 + k) * Vp;  // entry (row 1, column k)
+      m.re[k] = make_float2(CG ? __ldcg(e0) : __ldg(e0), CG ? __ldcg(e1) : __ldg(e1));
+      m.im[k] = make_float2(CG ? __ldcg(e0 + 2) : __ldg(e0 + 2), CG ? __ldcg(e1 + 2) : __ldg(e1 + 2));
+    }
+    return m;
+  } else {
+    return load_pm3<CG>(U, mu, p, h, Vh);
+  }
+}
+
+// Single-site access to a site-paired store: rows 0,1 of site h's link (mu, p)
+// as 12 floats, row 0 then row 1, (re, im) per column (as store_f32_rows01
+// takes them); Vp = V/4 pairs per (mu, parity), pair h mod Vp, member h / Vp.
+__device__ __forceinline__ void load_pair_site(const float4* __restrict__ U, int mu, int p, int h, int Vp, float r[12]) {
+  const int half = h >= Vp ? 1 : 0;
+  const float* b = (const float*)(U + link_base(mu, p, Vp, 6) + (h - half * Vp)) + half;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    r[6 * (e / 3) + 2 * (e % 3)] = __ldg(b + (size_t)4 * e * Vp);
+    r[6 * (e / 3) + 2 * (e % 3) + 1] = __ldg(b + (size_t)4 * e * Vp + 2);
+  }
+}
+
+__device__ __forceinline__ void store_pair_site(float4* U, int mu, int p, int h, int Vp, const float r[12]) {
+  const int half = h >= Vp ? 1 : 0;
+  float* b = (float*)(U + link_base(mu, p, Vp, 6) + (h - half * Vp)) + half;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    b[(size_t)4 * e * Vp] = r[6 * (e / 3) + 2 * (e % 3)];
+    b[(size_t)4 * e * Vp + 2] = r[6 * (e / 3) + 2 * (e % 3) + 1];
+  }
+}
+
 // Six-staple sum A for U_mu(x), x = st of parity p:
 //   sum_{nu != mu} U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ + U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu).
 // Each three-link path is an SU(3) matrix, so only its rows 0 and 1 are
@@ -290,33 +338,33 @@ __device__ __forceinline__ UpdateCount heatbath_f64(const G& g, double2* U, int 
 // ---------------------------------------------------------------------------
 // The two paths of direction nu on row pairs, rows 0,1 (as forward_path and
 // backward_path above), added to the staple in the same order.
-template <bool CG, typename G>
+template <bool CG, bool PAIRS = false, typename G>
 __device__ __forceinline__ pm3 forward_path_p(const G& g, const float4* U, int h, int p, int mu, int nu, int h_pmu,
                                               int h_pnu) {
   const int q = p ^ 1;
-  const pm3 a = load_pm3<CG>(U, nu, q, h_pmu, g.Vh);  // U_nu(x+mu)
-  pm3 b = load_pm3<CG>(U, mu, q, h_pnu, g.Vh);        // U_mu(x+nu)
+  const pm3 a = load_pm3_l<CG, PAIRS>(U, nu, q, h_pmu, g.Vh);  // U_nu(x+mu)
+  pm3 b = load_pm3_l<CG, PAIRS>(U, mu, q, h_pnu, g.Vh);        // U_mu(x+nu)
   complete_row2_p(b);
   pm3 t;
   mul_nd_p(a, b, t);
-  pm3 c = load_pm3<CG>(U, nu, p, h, g.Vh);  // U_nu(x)
+  pm3 c = load_pm3_l<CG, PAIRS>(U, nu, p, h, g.Vh);  // U_nu(x)
   complete_row2_p(c);
   pm3 f;
   mul_nd_p(t, c, f);
   return f;
 }
 
-template <bool CG, typename G>
+template <bool CG, bool PAIRS = false, typename G>
 __device__ __forceinline__ pm3 backward_path_p(const G& g, const float4* U, int p, int mu, int nu, int h_mnu,
                                                int h_pmu_mnu) {
   const int q = p ^ 1;
-  pm3 d = load_pm3<CG>(U, nu, p, h_pmu_mnu, g.Vh);  // U_nu(x+mu-nu)
+  pm3 d = load_pm3_l<CG, PAIRS>(U, nu, p, h_pmu_mnu, g.Vh);  // U_nu(x+mu-nu)
   complete_row2_p(d);
-  const pm3 e = load_pm3<CG>(U, mu, q, h_mnu, g.Vh);  // U_mu(x-nu)
+  const pm3 e = load_pm3_l<CG, PAIRS>(U, mu, q, h_mnu, g.Vh);  // U_mu(x-nu)
   pm3 hm;
   mul_nn_p(e, d, hm);
   complete_row2_p(hm);
-  pm3 f = load_pm3<CG>(U, nu, q, h_mnu, g.Vh);  // U_nu(x-nu)
+  pm3 f = load_pm3_l<CG, PAIRS>(U, nu, q, h_mnu, g.Vh);  // U_nu(x-nu)
   complete_row2_p(f);
   pm3 b;
   mul_dn_p(hm, f, b);
@@ -356,6 +404,23 @@ __device__ __forceinline__ pm3 staple_p(const G& g, const float4* U, const S& st
   return A;
 }
 
+// ---------------------------------------------------------------------------
+// cp.async: 16-byte copies from global to shared memory that do not pass
+// through registers, tracked in commit groups per thread.
+// ---------------------------------------------------------------------------
+template <bool CG>
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const float4* gsrc) {
+  if (CG)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // The hardware square root (about 1 ulp): the FP32 heatbath needs no
 // correctly rounded one.
 __device__ __forceinline__ float sqrt_approx(float x) {
@@ -388,12 +453,26 @@ __device__ __forceinline__ UpdateCount update_link_f32(const G& g, float4* U, in
 
 // Everything after the staple (FP32 storage): three SU(2) heatbath steps,
 // reunitarisation, store.
+template <int MU, bool EFT, bool REPEAT, bool MEAS, bool PAIRS = false, typename KEY, typename G>
+__device__ __forceinline__ UpdateCount heatbath_f32_on(const G& g, float4* U, int h, int p, uint64_t t, uint32_t s,
+                                                       const KEY& key, const UpdateConsts& uc, const pm3& A,
+                                                       const pm3& Apart, double* meas, pm3 u, bool store);
+
 template <int MU, bool CG, bool EFT, bool REPEAT, bool MEAS, typename KEY, typename G>
 __device__ __forceinline__ UpdateCount heatbath_f32(const G& g, float4* U, int h, int p, uint64_t t, uint32_t s,
                                                     const KEY& key, const UpdateConsts& uc, const pm3& A,
                                                     const pm3& Apart, double* meas) {
+  return heatbath_f32_on<MU, EFT, REPEAT, MEAS>(g, U, h, p, t, s, key, uc, A, Apart, meas,
+                                                 load_pm3<CG>(U, MU, p, h, g.Vh), true);
+}
+
+// The same with the link's own rows 0,1 given (u); store = false computes
+// everything but writes nothing (a lane that only keeps its warp converged).
+template <int MU, bool EFT, bool REPEAT, bool MEAS, bool PAIRS, typename KEY, typename G>
+__device__ __forceinline__ UpdateCount heatbath_f32_on(const G& g, float4* U, int h, int p, uint64_t t, uint32_t s,
+                                                       const KEY& key, const UpdateConsts& uc, const pm3& A,
+                                                       const pm3& Apart, double* meas, pm3 u, bool store) {
   UpdateCount cnt{0, 0};
-  pm3 u = load_pm3<CG>(U, MU, p, h, g.Vh);
   complete_row2_p(u);
   const float three_over_beta = uc.three_over_beta;
 #pragma unroll
@@ -437,7 +516,7 @@ __device__ __forceinline__ UpdateCount heatbath_f32(const G& g, float4* U, int h
     }
     // 2r, as in su2_projection
     const float r[4] = {wii.re + wjj.re, wij.im + wji.im, wij.re - wji.re, wii.im - wjj.im};
-    const float kk = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];  // (2k)^2
+    const float kk = __fmaf_rn(r[3], r[3], __fmaf_rn(r[2], r[2], __fmaf_rn(r[1], r[1], __fmul_rn(r[0], r[0]))));  // (2k)^2
     if (!(kk > 4e-30f)) {  // degenerate staple (measure zero): leave the subgroup
       ++cnt.proposed;
       continue;
@@ -454,11 +533,11 @@ __device__ __forceinline__ UpdateCount heatbath_f32(const G& g, float4* U, int h
       ++cnt.proposed;
       const float u0 = u01_f32(w0.x), u1 = u01_f32(w0.y), u2 = u01_f32(w0.z), u3 = u01_f32(w0.w);
       const float cc = __cosf(fmaf(6.2831853f, u1, -3.14159265f));  // -cos(2 pi u1); only its square is used
-      const float delta = -(__logf(u0) + cc * cc * __logf(u2)) * ia;
-      if (u3 * u3 > 1.0f - 0.5f * delta) continue;
+      const float delta = __fmul_rn(-__fmaf_rn(__fmul_rn(cc, cc), __logf(u2), __logf(u0)), ia);
+      if (__fmul_rn(u3, u3) > __fmaf_rn(-0.5f, delta, 1.0f)) continue;
       const float u4 = u01_f32(w1.x), u5 = u01_f32(w1.y);
       const float rho = sqrt_approx(fmaxf(0.0f, delta * (2.0f - delta)));  // sqrt(1 - a0^2)
-      const float ct = 1.0f - 2.0f * u4;
+      const float ct = __fmaf_rn(-2.0f, u4, 1.0f);
       const float sn = 2.0f * sqrt_approx(u4 * (1.0f - u4));  // sqrt(1 - ct^2)
       float sphi, cphi;
       __sincosf(fmaf(6.2831853f, u5, -3.14159265f), &sphi, &cphi);  // angle 2 pi u5 - pi
@@ -500,7 +579,12 @@ __device__ __forceinline__ UpdateCount heatbath_f32(const G& g, float4* U, int h
   }
   float o[12];
   reunitarise_f32<EFT>(r0, r1, o);
-  store_f32_rows01(U, MU, p, h, g.Vh, o);
+  if (store) {
+    if (PAIRS)
+      store_pair_site(U, MU, p, h, g.Vh / 2, o);
+    else
+      store_f32_rows01(U, MU, p, h, g.Vh, o);
+  }
   if (MEAS) {
     // the stored link, row 2 completed, against A_<
     mat3<float> un;

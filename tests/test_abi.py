@@ -95,6 +95,7 @@ def test_null_handle_calls(lib):
     assert lib.su3_links_set(None, None, 0) == su3.SU3_EINVAL
     assert lib.su3_set_sweep_count(None, 0) == su3.SU3_EINVAL
     assert lib.su3_set_block_size(None, 64) == su3.SU3_EINVAL
+    assert lib.su3_set_lanes(None, 1) == su3.SU3_EINVAL
     v = lib.su3_plaquette(None)
     assert v != v
 

@@ -303,6 +303,68 @@ def test_fp32_half_sweeps_match_oracle_reading(L, prec):
     print("fp32 (precision %d) half-sweeps %s: worst |dU| %.2e, flips %d of %d" % (prec, L, worst, flips, total))
 
 
+# The same lattice updated by the four-lane kernel and by the one-thread kernel
+# (one thread per link pair where L3 is a multiple of 4, per link otherwise),
+# each checked against the oracle's FP32 reading, and against each other: both
+# add the staple in the same order and round every step identically.
+@pytest.mark.parametrize("prec", [su3.SU3_FP32_MIXED, su3.SU3_FP32_EFT])
+@pytest.mark.parametrize("L", [(8, 8, 8, 8), (6, 4, 10, 8), (10, 14, 6, 10)])
+def test_fp32_four_lane_and_one_lane_kernels_match_oracle_reading(L, prec):
+    seed, t = 41, 3
+    U0 = oracle.hot_start(L, 9, f32=True)
+    oracle.sweep(L, BETA, 4, 0, 1, U0, f32=True)
+    flips = total = 0
+    with su3.Lattice(L, BETA, seed, start=su3.SU3_COLD, precision=prec) as lat:
+        for mu in range(4):
+            for p in range(2):
+                got = {}
+                for lanes in (4, 1):
+                    lat.set_lanes(lanes)
+                    lat.set_links(U0)
+                    lat.sweep_count = t
+                    lat.half_sweep(mu, p)
+                    got[lanes] = lat.get_links()
+                assert np.array_equal(got[4], got[1]), (mu, p)
+                sites = site_list(L, p)
+                O, marg = oracle.updated_links(L, BETA, seed, t, mu, sites, U0, f32=True, with_margins=True)
+                d = np.abs(flat_links(got[1])[sites, mu] - O).max(axis=(1, 2, 3))
+                bad = d > F32_TOL
+                if bad.any():
+                    assert (np.nanmin(np.abs(marg[bad]), axis=1) < F32_MARGIN).all(), (mu, p, d[bad])
+                flips += int(bad.sum())
+                total += sites.size
+        lat.set_lanes(0)
+    assert flips <= max(2, total // 2000), (flips, total)
+
+
+def test_lanes_setting_validated():
+    with su3.Lattice((4, 4, 4, 4), BETA, 1, start=su3.SU3_COLD) as lat:
+        for bad in (-1, 2, 3, 8):
+            with pytest.raises(su3.Su3Error):
+                lat.set_lanes(bad)
+        lat.set_lanes(4)
+        lat.set_lanes(0)
+    with su3.Batch([(4, 4, 4, 4)], [BETA], [1], start=su3.SU3_COLD) as b:
+        with pytest.raises(su3.Su3Error):
+            su3.su3_set_lanes(b.handle, 1)
+
+
+# The FP32 fused plaquette (taken inside the odd-site updates of mu = 1, 2, 3)
+# against the oracle's plaquette of the configuration the sweep produced, in
+# the oracle's FP32 reading (row 2 rebuilt from the stored rows): the bound is
+# the FP32 rounding of the staple terms, ~1e-7 per plaquette.
+@pytest.mark.parametrize("prec", [su3.SU3_FP32_MIXED, su3.SU3_FP32_EFT])
+@pytest.mark.parametrize("L", [(8, 8, 8, 16), (6, 4, 10, 6), (4, 4, 4, 4)])
+def test_fp32_fused_plaquette_matches_oracle(L, prec):
+    U0 = oracle.hot_start(L, 13, f32=True)
+    with su3.Lattice(L, BETA, 6, start=su3.SU3_COLD, precision=prec) as lat:
+        lat.set_links(U0)
+        for _ in range(3):
+            got = lat.sweep_measured(1)[0]
+            ref = oracle.plaquette(L, lat.get_links(), f32=True)
+            assert abs(got - ref) < 2e-6, (got, ref)
+
+
 @pytest.mark.parametrize("prec", [su3.SU3_FP32_MIXED, su3.SU3_FP32_EFT])
 def test_fp32_far_from_unitary_takes_full_gram_schmidt(prec):
     # the links being updated have rows 0 and 1 stretched by 2 % and 1.5 %

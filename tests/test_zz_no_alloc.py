@@ -2,11 +2,13 @@
 memory (for example code running under CUDA stream capture, or runtimes that
 only hand out memory from their own pool).  The entry point keeps its scratch
 in a fixed device array instead of allocating; this test checks, through the C
-ABI, that it returns what the allocating su3_plaquette returns, on two calls in
-a row.  The file is named to be collected last."""
+ABI, that it returns what the allocating su3_plaquette returns and what the
+oracle computes for the same configuration, on two calls in a row.  The file
+is named to be collected last."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_0904_1179_gb300 as su3
 from paper_0904_1179_gb300 import build as su3_build
 
@@ -24,6 +26,16 @@ def device_layout(U, L, precision):
         for p in (0, 1):
             sel = flat[parity == bool(p)].reshape(V // 2, 4, 9, 2)
             soa[:, p] = sel.transpose(1, 2, 0, 3)
+    elif L[3] % 4 == 0:
+        # site pairs (h, h + V/4): entry e = 3 row + col of pair j holds
+        # (re u(h), re u(h + V/4), im u(h), im u(h + V/4))
+        Vp = V // 4
+        soa = np.empty((4, 2, 6, Vp, 4), dtype=np.float32)
+        for p in (0, 1):
+            rows01 = flat[parity == bool(p)][:, :, :2]  # (h, mu, row, col, re/im)
+            a, b = rows01[:Vp], rows01[Vp:]
+            quad = np.stack([a[..., 0], b[..., 0], a[..., 1], b[..., 1]], axis=-1)  # (j, mu, row, col, 4)
+            soa[:, p] = quad.transpose(1, 2, 3, 0, 4).reshape(4, 6, Vp, 4).astype(np.float32)
     else:
         soa = np.empty((4, 2, 3, V // 2, 4), dtype=np.float32)
         for p in (0, 1):
@@ -33,11 +45,20 @@ def device_layout(U, L, precision):
     return np.ascontiguousarray(soa)
 
 
-@pytest.mark.parametrize("precision,tol", [(su3.SU3_FP64, 1e-13), (su3.SU3_FP32_MIXED, 1e-12)])
-def test_noalloc_plaquette_matches_allocating_entry_point(precision, tol):
+# tolerances against the allocating entry point (same kernels, same order:
+# equal up to the summation of the partials) and against the oracle (FP64:
+# rounding order; FP32 stores: the FP32 rounding of the plaquette products,
+# ~1e-7 per plaquette)
+# (8, 6, 4, 10): FP32 stores one site per column group; (8, 6, 4, 8): L3 a
+# multiple of 4, FP32 stores site pairs
+@pytest.mark.parametrize("L", [(8, 6, 4, 10), (8, 6, 4, 8)])
+@pytest.mark.parametrize("precision,tol,tol_oracle", [(su3.SU3_FP64, 1e-13, 1e-13),
+                                                      (su3.SU3_FP32_MIXED, 1e-12, 2e-6),
+                                                      (su3.SU3_FP32_EFT, 1e-12, 2e-6)])
+def test_noalloc_plaquette_matches_allocating_entry_point(L, precision, tol, tol_oracle):
     torch = pytest.importorskip("torch")
     su3_build.build()
-    L = (8, 6, 4, 10)
+    oracle.build()
     stream = torch.cuda.current_stream()
     out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
     expect = []
@@ -45,10 +66,14 @@ def test_noalloc_plaquette_matches_allocating_entry_point(precision, tol):
         for call in range(2):  # two calls in a row, on two different configurations
             lat.sweep(2)
             expect.append(lat.plaquette())
-            dev = torch.from_numpy(device_layout(lat.get_links(), L, precision)).cuda()
+            U = lat.get_links()
+            dev = torch.from_numpy(device_layout(U, L, precision)).cuda()
             su3.su3_plaquette_noalloc(dev.data_ptr(), L, precision, out[call:].data_ptr(), stream.cuda_stream)
             torch.cuda.synchronize()
-            assert abs(out[call].item() - expect[call]) < tol, (call, out[call].item(), expect[call])
+            got = out[call].item()
+            assert abs(got - expect[call]) < tol, (call, got, expect[call])
+            ref = oracle.plaquette(L, U, f32=precision != su3.SU3_FP64)
+            assert abs(got - ref) < tol_oracle, (call, got, ref)
     assert expect[0] != expect[1]
 
 
@@ -59,3 +84,8 @@ def test_noalloc_rejects_oversized_lattice():
     with pytest.raises(su3.Su3Error) as e:
         su3.su3_plaquette_noalloc(links.data_ptr(), (66, 64, 64, 64), su3.SU3_FP64, out.data_ptr())
     assert e.value.code == -5 and "64^4" in str(e.value)
+    # extents whose product overflows 64-bit integers are rejected the same way
+    with pytest.raises(su3.Su3Error) as e:
+        su3.su3_plaquette_noalloc(links.data_ptr(), (1 << 30, 1 << 30, 1 << 30, 1 << 30), su3.SU3_FP32_EFT,
+                                  out.data_ptr())
+    assert e.value.code == -5
