@@ -613,6 +613,23 @@ __device__ __forceinline__ void dot2(const float* x, const float* y, int n, floa
   }
 }
 
+// The FP64 value of an FP32 number, built from its bits on the integer pipe
+// (the FP64 pipe, 1/64 of the FP32 rate on this GPU, is kept for the sums):
+// sign, exponent rebiased by 1023 - 127 = 896, the 23 mantissa bits moved to
+// the top of the 52.  Exact for every finite x: a subnormal is first scaled
+// by 2^64 in FP32 (exact) and the scale taken off the exponent; zero keeps
+// its sign.
+__device__ __forceinline__ double f32_to_f64_bits(float x) {
+  const uint32_t ux = (uint32_t)__float_as_int(x);
+  const bool sub = (ux & 0x7F800000u) == 0u;
+  const uint32_t u = sub ? (uint32_t)__float_as_int(x * 0x1p64f) : ux;
+  const uint32_t mag = u & 0x7FFFFFFFu;
+  const uint32_t ebias = sub ? (896u - 64u) << 20 : 896u << 20;
+  const uint32_t hi = (u & 0x80000000u) | (mag == 0u ? 0u : (mag >> 3) + ebias);
+  const uint32_t lo = u << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // EFT = false: the coefficients n0, n1, d are FP64 sums of the exact FP32
 // products (FP64 pipe).  EFT = true: the same sums as compensated FP32 dot
 // products (TwoProd by FMA, TwoSum), about 2^-47 relative -- FP64-class
@@ -647,7 +664,8 @@ __device__ __forceinline__ void reunitarise_f32(const cx<float> a[3], const cx<f
     double n0 = 0.0, n1 = 0.0, dre = 0.0, dim = 0.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const double ar = a[k].re, ai = a[k].im, br = b[k].re, bi = b[k].im;
+      const double ar = f32_to_f64_bits(a[k].re), ai = f32_to_f64_bits(a[k].im);
+      const double br = f32_to_f64_bits(b[k].re), bi = f32_to_f64_bits(b[k].im);
       n0 = fma(ar, ar, fma(ai, ai, n0));
       n1 = fma(br, br, fma(bi, bi, n1));
       dre = fma(ar, br, fma(ai, bi, dre));

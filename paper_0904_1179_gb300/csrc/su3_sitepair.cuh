@@ -480,8 +480,8 @@ __device__ __forceinline__ void reunitarise_q(const float2 a_re[3], const float2
       n0[m] = n1[m] = dre[m] = dim[m] = 0.0;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const double ar = m ? a_re[k].y : a_re[k].x, ai = m ? a_im[k].y : a_im[k].x;
-        const double br = m ? b_re[k].y : b_re[k].x, bi = m ? b_im[k].y : b_im[k].x;
+        const double ar = f32_to_f64_bits(m ? a_re[k].y : a_re[k].x), ai = f32_to_f64_bits(m ? a_im[k].y : a_im[k].x);
+        const double br = f32_to_f64_bits(m ? b_re[k].y : b_re[k].x), bi = f32_to_f64_bits(m ? b_im[k].y : b_im[k].x);
         n0[m] = fma(ar, ar, fma(ai, ai, n0[m]));
         n1[m] = fma(br, br, fma(bi, bi, n1[m]));
         dre[m] = fma(ar, br, fma(ai, bi, dre[m]));
