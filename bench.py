@@ -75,11 +75,34 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one ncu capture of each kernel (profiles/*.md; batched: 128 threads x 6 blocks
-# per SM, the autotuner's usual choice); None
-# where the kernel changed after its last capture.
-NCU_TRAFFIC = {"fp64": 687.8e6, "fp32_mixed": 226.7e6, "fp32_eft": 226.8e6, "batched": 3.460e9}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel of each line, from one ncu capture: the bytes, the command
+# that captured them, and the SHA-256 of the kernel sources (every
+# paper_0904_1179_gb300/csrc/*.cu and *.cuh, sorted by name) at capture time.
+# A line reports the figure only while the sources still hash the same;
+# otherwise its traffic is null and the line says why.
+NCU_TRAFFIC = {}
+
+
+def kernel_sources_sha():
+    import hashlib
+    d = os.path.join(ROOT, "paper_0904_1179_gb300", "csrc")
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(d)):
+        if fn.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, fn), "rb") as f:
+                h.update(fn.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def traffic_of(variant):
+    """(bytes or None, provenance) of a line's ncu DRAM traffic figure."""
+    rec = NCU_TRAFFIC.get(variant)
+    if rec is None:
+        return None, "no ncu capture recorded for this kernel"
+    if rec["sources_sha256"] != kernel_sources_sha():
+        return None, "kernel sources changed since the ncu capture (%s)" % rec["capture"]
+    return rec["bytes"], "ncu capture: %s; kernel sources sha256 %s" % (rec["capture"], rec["sources_sha256"][:16])
 
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA per
 # clock (1/64 of the 128 FP32 lanes) x 2 flop x 2.070 GHz = 1.2586 TFLOP/s
@@ -409,6 +432,7 @@ def variant_fp32(su3, stream, steps, warmup, world, hbm_peak, peak_kind, precisi
     achieved = BYTES_PER_UPDATE["fp32_mixed"] * (V // 2) / (kernel_ms * 1e-3) / 1e9
     gs = ("Gram-Schmidt coefficients as compensated FP32 sums (error-free transformations, ~2^-47)" if eft
           else "FP64 Gram-Schmidt coefficients")
+    traffic, provenance = traffic_of("fp32_eft" if eft else "fp32_mixed")
     return {"workload": "32^4 beta=5.7 hot start seed 7, FP32-mixed (12-real FP32 links, FP32 staple and "
                         "heatbath, %s), 2 sweeps/step" % gs,
             "value": ups, "unit": UNIT, "ms_per_step": total_ms / steps,
@@ -416,7 +440,8 @@ def variant_fp32(su3, stream, steps, warmup, world, hbm_peak, peak_kind, precisi
             "plaquette_after": plaq,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "peak_kind": peak_kind,
-                         "traffic": NCU_TRAFFIC["fp32_eft" if eft else "fp32_mixed"],
+                         "traffic": traffic, "traffic_source": provenance,
+                         "kernel": "k_half_sweep_f32_pair (site-paired FP32 half-sweep)",
                          "bytes_per_launch": BYTES_PER_UPDATE["fp32_mixed"] * (V // 2),
                          "kernel_ms": kernel_ms}}
 
@@ -458,10 +483,11 @@ def variant_measured(su3, stream, steps, warmup, precision):
 
 def run_profile_case(case):
     import paper_0904_1179_gb300 as su3
-    if case == "batched":
+    if case in ("batched", "batched_eft"):
         from paper_0904_1179_gb300.workloads import batch_96
         dims, betas, seeds = batch_96()
-        with su3.Batch(dims, betas, seeds, start=su3.SU3_HOT, precision=su3.SU3_FP32_MIXED) as b:
+        prec = su3.SU3_FP32_EFT if case == "batched_eft" else su3.SU3_FP32_MIXED
+        with su3.Batch(dims, betas, seeds, start=su3.SU3_HOT, precision=prec) as b:
             b.config(128, 6, 0)  # the autotuner's usual choice on GB300
             b.sweep(3)
             p = b.plaquettes()
@@ -476,6 +502,10 @@ def run_profile_case(case):
     dims, beta = (DIMS, BETA)
     if case.endswith("_64"):
         dims, beta, case = (64, 64, 64, 64), 6.0, case[:-3]
+    elif case.endswith("_64s"):  # 64^3 x 16: the x3 lines of 64^4 in 805 MB (FP32)
+        dims, beta, case = (64, 64, 64, 16), 6.0, case[:-4]
+    elif case.endswith("_48"):
+        dims, case = (48, 48, 48, 48), case[:-3]
     elif case.endswith("_8"):
         dims, case = (8, 8, 8, 8), case[:-2]
     prec = {"fp64": su3.SU3_FP64, "fp32_mixed": su3.SU3_FP32_MIXED, "fp32_eft": su3.SU3_FP32_EFT}[case]
@@ -506,12 +536,14 @@ def variant_batched_eft(su3, stream, steps, warmup, hbm_peak, peak_kind):
         b.status()
         sweep_ms = e0.elapsed_time(e1) / steps
     achieved = BYTES_PER_UPDATE["fp32_mixed"] * ups / (sweep_ms * 1e-3) / 1e9
+    traffic, provenance = traffic_of("batched_eft")
     return {"workload": "the 96 replicas of variant 'batched' in FP32-EFT", "value": ups / (sweep_ms * 1e-3),
             "unit": UNIT, "ms_per_step": sweep_ms, "dtype": "f32 (compensated-f32 reunitarisation)",
             "autotuned": {"threads": cfg[0], "blocks_per_sm": cfg[1], "window": cfg[2]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": None,
-                         "kernel_ms": sweep_ms}}
+                         "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": traffic,
+                         "traffic_source": provenance, "kernel": "k_batch_sweep",
+                         "bytes_per_launch": BYTES_PER_UPDATE["fp32_mixed"] * ups, "kernel_ms": sweep_ms}}
 
 
 def variant_batched(su3, stream, steps, warmup, hbm_peak, peak_kind):
@@ -557,13 +589,15 @@ def variant_batched(su3, stream, steps, warmup, hbm_peak, peak_kind):
             lat.close()
     sweep_ms = total_ms / steps
     achieved = BYTES_PER_UPDATE["fp32_mixed"] * ups / (sweep_ms * 1e-3) / 1e9
+    traffic, provenance = traffic_of("batched")
     return {"workload": "96 replicas (32x 8^4, 32x 12^4, 16x 16^4, 16x 8^3x16), beta in [5.5, 6.2], hot starts "
                         "seed 1000+r, FP32-mixed; step = 1 sweep of every replica = one persistent launch",
             "value": value, "unit": UNIT, "ms_per_step": sweep_ms, "dtype": "f32 (f64 reunitarisation)",
             "updates_per_step": ups, "autotuned": {"threads": cfg[0], "blocks_per_sm": cfg[1], "window": cfg[2]},
             "one_by_one": {"value": one_by_one, "unit": UNIT, "speedup": value / one_by_one},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": NCU_TRAFFIC["batched"],
+                         "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": traffic,
+                         "traffic_source": provenance, "kernel": "k_batch_sweep",
                          "bytes_per_launch": BYTES_PER_UPDATE["fp32_mixed"] * ups, "kernel_ms": sweep_ms,
                          "note": "one launch = one sweep of all replicas; duration includes the counter reset"}}
 
@@ -745,7 +779,10 @@ def run_decomp(args):
     beta 5.7) undivided and cut like the paper's rows -- ndmpi = 1 with one sublattice and
     the boundary exchange on ("1"), then np = 2, 4, 8, 16 (ndmpi 1..4, mpifactor 2).  CUDA
     events around the n sweeps of each run (sweep graph built and sublattices filled by one
-    sweep beforehand)."""
+    sweep beforehand).  Each row's time is given against the undivided lattice in its
+    one-thread-per-update form (vs_plain) and against the "1F" row (vs_1F): one sublattice
+    with the exchange off runs the same sublattice kernel as the cut rows, so vs_1F is the
+    cost of the cut and the exchange alone."""
     import numpy as np
     import torch
     import paper_0904_1179_gb300 as su3
@@ -759,10 +796,12 @@ def run_decomp(args):
         V = int(np.prod(L))
         col = {"lattice": list(L), "sweeps": n, "rows": {}}
         for prec, pname in precs:
-            base = None
+            base = base1f = None
             for name, dec in rows:
                 with su3.Lattice(L, BETA, HEADLINE_SEED, start=su3.SU3_HOT, precision=prec, decomp=dec,
                                  stream=stream.cuda_stream) as lat:
+                    if dec is None:
+                        lat.set_lanes(1)  # the sublattices run one thread per update too
                     lat.sweep(1)
                     torch.cuda.synchronize()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -774,17 +813,21 @@ def run_decomp(args):
                     info = lat.decomp_info()
                 if base is None:
                     base = sec
+                if name == "1F":
+                    base1f = sec
                 link_bytes = 144 if prec == su3.SU3_FP64 else 48
                 col["rows"].setdefault(name, {})[pname] = {
                     "seconds": sec, "value": 4 * V * n / sec, "vs_plain": sec / base,
+                    "vs_1F": sec / base1f if base1f else None,
                     "np": info[3], "halo_links_per_sweep": info[4],
                     "halo_bytes_per_sweep": 2 * info[4] * link_bytes}
         out.append(col)
     print(json.dumps({"mode": "decomp", "unit": UNIT, "beta": BETA, "columns": out,
-                      "note": "rows as in Table 1: plain = single-lattice kernels; 1F = one sublattice, "
+                      "note": "rows as in Table 1: plain = the undivided lattice, one thread per update "
+                              "(FP32: per link pair where L3 is a multiple of 4); 1F = one sublattice, "
                               "exchange off; 1 = one sublattice exchanging with itself; 2..16 = np sublattices "
-                              "(ndmpi 1..4, mpifactor 2); halo bytes count the read and the write of every "
-                              "copied link"}))
+                              "(ndmpi 1..4, mpifactor 2); vs_1F compares runs of the same sublattice kernel; "
+                              "halo bytes count the read and the write of every copied link"}))
     return 0
 
 
@@ -832,8 +875,8 @@ def main():
     ap.add_argument("--table1", action="store_true",
                     help="the paper's Table 1 columns in full (FP64 and FP32-mixed), with the oracle beside them")
     ap.add_argument("--large-sweeps", type=int, default=100)
-    ap.add_argument("--profile", choices=["fp64", "fp32_mixed", "fp32_eft", "batched", "fp64_64", "fp32_mixed_64", "decomp16",
-                             "fp64_8"],
+    ap.add_argument("--profile", choices=["fp64", "fp32_mixed", "fp32_eft", "batched", "batched_eft", "fp64_64", "fp32_mixed_64", "decomp16",
+                             "fp64_8", "fp32_mixed_64s", "fp32_eft_64s", "fp32_mixed_48", "fp32_eft_48"],
                     help="small case for ncu: create the 32^4 lattice (or the 96-replica batch) and run 3 graphed "
                          "sweeps, nothing else")
     args = ap.parse_args()
@@ -907,7 +950,8 @@ def main():
         "gpu_launches": args.steps * SWEEPS_PER_STEP * 9,
         "gpu_launches_note": "headline timed region: per sweep 8 half-sweep kernels + 1 sweep-counter kernel",
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC["fp64"],
+                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic_of("fp64")[0],
+                     "traffic_source": traffic_of("fp64")[1],
                      "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flop x 2.070 GHz",
                      "probe_peak": FP64_PROBE_TFLOPS, "frac_of_probe": achieved_tf / FP64_PROBE_TFLOPS,
                      "kernel": "k_half_sweep_f64", "flop_per_launch": flop_per_launch, "kernel_ms": kernel_ms,

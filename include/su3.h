@@ -168,7 +168,8 @@ SU3_API int su3_stats(su3_handle h, uint64_t* accepted, uint64_t* proposed);
  * max_tries > 1 is the repeat-until-accepted heatbath of its non-MPI program:
  * up to max_tries Kennedy-Pendleton proposals per subgroup, proposal n drawn
  * from counter word mu | sub<<2 | call<<4 | n<<6 (proposal 0 is the one-hit
- * draw).  1 <= max_tries <= 2^20.  Valid for single lattices and batches. */
+ * draw).  1 <= max_tries <= 2^20.  Valid for single lattices, decomposed
+ * lattices and batches. */
 SU3_API int su3_set_heatbath(su3_handle h, int max_tries);
 
 /* Lattice properties of a handle. */
@@ -204,9 +205,11 @@ SU3_API int su3_set_lanes(su3_handle h, int lanes);
  * copied into the ghost cells that the neighbours' staples read (the
  * boundary exchange, Appendix A Eq. (mscb18)), by one gather launch over all
  * sublattices.  lbcex = 0 (only with mpifactor 1) is the paper's "exchange
- * off" run: plain periodic wrap, the single-lattice kernels.  Results are bit
- * for bit those of su3_create_ex with the same arguments: the random numbers
- * are keyed by the global site.
+ * off" run: one sublattice covering the lattice, no direction cut, periodic
+ * wrap inside it, no ghost layers and no exchange -- the same sublattice
+ * kernel as the cut runs, so it is their like-for-like baseline.  Results are
+ * bit for bit those of su3_create_ex with the same arguments: the random
+ * numbers are keyed by the global site.
  * ------------------------------------------------------------------------- */
 
 /* Create a decomposed lattice.  Arguments as for su3_create_ex plus
@@ -215,11 +218,12 @@ SU3_API int su3_set_lanes(su3_handle h, int lanes);
  *     into even parts of at least 2 sites;
  *   lbcex: 1 = boundary exchange on, 0 = off (mpifactor 1 only).
  * The handle accepts every single-lattice call: su3_sweep and su3_half_sweep
- * run the decomposed sweep; su3_plaquette, su3_links_get and su3_links_set
- * first gather the sublattices into (or scatter them from) the handle's
- * global store.  Not available on it: su3_sweep_measured, and max_tries > 1
- * in su3_set_heatbath (SU3_EINVAL).  Errors: SU3_EINVAL (arguments),
- * SU3_ENOMEM / SU3_ECUDA (allocation). */
+ * run the decomposed sweep; su3_sweep_measured fuses the plaquette into the
+ * sublattice updates exactly as into the undivided ones; su3_set_heatbath
+ * applies to the sublattice updates; su3_plaquette, su3_links_get and
+ * su3_links_set first gather the sublattices into (or scatter them from) the
+ * handle's global store.  su3_set_lanes is not available on it (SU3_EINVAL).
+ * Errors: SU3_EINVAL (arguments), SU3_ENOMEM / SU3_ECUDA (allocation). */
 SU3_API int su3_decomp_create(int L0, int L1, int L2, int L3, double beta, uint64_t seed, int start, int precision,
                               int ndmpi, int mpifactor, int lbcex, void* cuda_stream, su3_handle* out);
 
@@ -342,6 +346,17 @@ SU3_API int su3_status(su3_handle h);
  * or launch failed); su3_last_error() describes them. */
 SU3_API int su3_plaquette_noalloc(const void* links, int L0, int L1, int L2, int L3, int precision, double* out,
                                   void* cuda_stream);
+
+/* Bounds-checked builds only (libsu3_bounds.so, compiled with
+ * -DSU3_BOUNDS_CHECK; an implementation aid, the paper has none): every link
+ * load and store of every kernel -- single lattices, batch replicas,
+ * sublattices with their ghost layers, the staging copies -- checks its
+ * direction, parity and index against the extent of the store it addresses;
+ * an access out of range is skipped and recorded, never trapped.  *status
+ * receives 0 if no access was out of range since the last clear, else 1;
+ * clear != 0 resets it.  Synchronous.  SU3_EINVAL in the product build (no
+ * checks compiled in) or for a NULL status. */
+SU3_API int su3_bounds_status(unsigned int* status, int clear);
 
 /* Description of the last failure on the calling thread ("" if none). */
 SU3_API const char* su3_last_error(void);

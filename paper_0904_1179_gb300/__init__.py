@@ -21,7 +21,7 @@ __all__ = [
     "su3_create", "su3_create_ex", "su3_destroy", "su3_sweep", "su3_sweep_measured", "su3_half_sweep", "su3_plaquette",
     "su3_decomp_create", "su3_decomp_plan", "su3_decomp_info",
     "su3_links_get", "su3_links_set", "su3_sweep_count", "su3_set_sweep_count", "su3_set_stats", "su3_stats",
-    "su3_info", "su3_set_block_size", "su3_set_lanes", "su3_set_heatbath", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
+    "su3_info", "su3_set_block_size", "su3_set_lanes", "su3_bounds_status", "use_library", "su3_set_heatbath", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
     "su3_batch_links_get", "su3_batch_links_set", "su3_batch_size", "su3_batch_config", "su3_batch_get_config",
     "su3_batch_autotune", "su3_batch_debug", "su3_status", "Batch", "su3_plaquette_noalloc", "su3_last_error", "su3_version", "Lattice", "links_shape", "EXPORTS",
 ]
@@ -70,6 +70,7 @@ EXPORTS = [
     ("su3_info", ctypes.c_int, [_h, _pi, _pd, _pu64, _pi]),
     ("su3_set_block_size", ctypes.c_int, [_h, ctypes.c_int]),
     ("su3_set_lanes", ctypes.c_int, [_h, ctypes.c_int]),
+    ("su3_bounds_status", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint), ctypes.c_int]),
     ("su3_set_heatbath", ctypes.c_int, [_h, ctypes.c_int]),
     ("su3_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _pd, _pu64, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(_h)]),
@@ -98,6 +99,16 @@ class Su3Error(RuntimeError):
 
 def library_path() -> str:
     return _LIB_PATH
+
+
+def use_library(path):
+    """Use another build of the library (e.g. the bounds-checked libsu3_bounds.so) in
+    this process; call before the first use of any su3_* function."""
+    global _LIB_PATH
+    with _lock:
+        if _lib is not None and os.path.abspath(path) != os.path.abspath(_LIB_PATH):
+            raise RuntimeError("libsu3 is already loaded from %s" % _LIB_PATH)
+        _LIB_PATH = os.path.abspath(path)
 
 
 def load_library():
@@ -250,6 +261,13 @@ def su3_set_block_size(h, threads):
 def su3_set_lanes(h, lanes):
     """0: automatic; 1: one thread per link (or link pair); 4: four lanes per link."""
     _check(load_library().su3_set_lanes(h, int(lanes)))
+
+
+def su3_bounds_status(clear=False):
+    """Bounds-checked build only: 1 if a link access was out of range since the last clear, else 0."""
+    v = ctypes.c_uint(0)
+    _check(load_library().su3_bounds_status(ctypes.byref(v), int(bool(clear))))
+    return v.value
 
 
 def su3_set_heatbath(h, max_tries):

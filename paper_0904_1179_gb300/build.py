@@ -2,6 +2,11 @@
 
 Each .cu translation unit under csrc/ compiles in parallel to an object in
 _build/, then nvcc links them into paper_0904_1179_gb300/libsu3.so.
+
+build(bounds_check=True) makes the bounds-checked variant libsu3_bounds.so
+(objects in _build_bounds/, compiled with -DSU3_BOUNDS_CHECK): every link
+access of every kernel checks its index against its store's extent and
+records, never traps, an access out of range (su3_bounds_status).
 """
 from __future__ import annotations
 
@@ -17,6 +22,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsu3.so")
+BUILD_BOUNDS = os.path.join(HERE, "_build_bounds")
+LIB_BOUNDS = os.path.join(HERE, "libsu3_bounds.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
@@ -38,15 +45,15 @@ def _deps():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps() + [os.path.abspath(__file__)])
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra, build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     cmd = [nvcc()] + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -56,25 +63,31 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile every csrc/*.cu for sm_103a and link libsu3.so; returns its path."""
-    if not force and not extra and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), bounds_check: bool = False) -> str:
+    """Compile every csrc/*.cu for sm_103a and link libsu3.so (or, with
+    bounds_check, libsu3_bounds.so); returns its path."""
+    lib, build_dir = (LIB_BOUNDS, BUILD_BOUNDS) if bounds_check else (LIB, BUILD)
+    if bounds_check:
+        extra = list(extra) + ["-DSU3_BOUNDS_CHECK"]
+    if not force and (bounds_check or not extra) and up_to_date(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB + ".tmp%d" % os.getpid()
+        objs = list(ex.map(lambda s: _compile(s, extra, build_dir), srcs))
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stdout + r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    extra = sys.argv[1:]
-    print(build(force=True, verbose=True, extra=extra))
+    args = sys.argv[1:]
+    checked = "--bounds-check" in args
+    extra = [a for a in args if a != "--bounds-check"]
+    print(build(force=True, verbose=True, extra=extra, bounds_check=checked))

@@ -139,6 +139,7 @@ HalfSweepArgs half_sweep_args(const su3_lattice* h, int parity) {
   a.split = h->split;
   a.pairs = h->pairs;
   a.pgeom = h->pgeom;
+  a.tile2 = h->pairs ? su3k_pair_tile2(h->pgeom, h->threads) : 0;
   a.geom = h->geom;
   a.key = su3dev::philox_round_keys(h->key);
   a.parity = parity;
@@ -375,15 +376,16 @@ int su3_sweep_measured(su3_handle h, int nsweeps, double* plaq_out) {
   if (is_batch(h)) return fail(SU3_EINVAL, "su3_sweep_measured: batch handle (use su3_batch_plaquettes)");
   if (nsweeps < 0 || (nsweeps > 0 && !plaq_out)) return fail(SU3_EINVAL, "su3_sweep_measured: bad nsweeps or NULL out");
   if (h->stats_on) return fail(SU3_EINVAL, "su3_sweep_measured: disable acceptance statistics first");
-  if (su3_decomp_active(h)) return fail(SU3_EINVAL, "su3_sweep_measured: not available on a decomposed lattice");
   if (nsweeps == 0) return SU3_OK;
-  const int blocks = su3k_half_sweep_blocks(half_sweep_args(h, 1), h->precision, h->threads);
+  const bool dec = su3_decomp_active(h);
+  const int blocks = dec ? su3_decomp_meas_blocks(h) : su3k_half_sweep_blocks(half_sweep_args(h, 1), h->precision, h->threads);
   if (h->meas_blocks != blocks || !h->d_meas) {
     SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_sweep_measured");
     if (h->graph_meas) {
       cudaGraphExecDestroy(h->graph_meas);
       h->graph_meas = nullptr;
     }
+    if (h->decomp) su3_decomp_invalidate(h->decomp);  // its graphs hold the old partials buffer
     cudaFree(h->d_meas_parts);
     h->d_meas_parts = nullptr;
     SU3_CUDA(cudaMalloc(&h->d_meas_parts, (size_t)3 * blocks * sizeof(double)), "su3_sweep_measured: partials");
@@ -394,12 +396,14 @@ int su3_sweep_measured(su3_handle h, int nsweeps, double* plaq_out) {
       SU3_CUDA(cudaMallocHost(&h->h_meas, (size_t)h->meas_cap * sizeof(double)), "su3_sweep_measured: ring");
     }
   }
-  int rc = ensure_graph(h, true);
+  cudaGraphExec_t exec = nullptr;
+  int rc = dec ? su3_decomp_sweep_measured_graph(h, &exec) : ensure_graph(h, true);
   if (rc != SU3_OK) return rc;
+  if (!dec) exec = h->graph_meas;
   for (int done = 0; done < nsweeps;) {
     const int n = (nsweeps - done) < h->meas_cap ? (nsweeps - done) : h->meas_cap;
     const uint64_t t0 = h->sweep_host;
-    for (int i = 0; i < n; ++i) SU3_CUDA(cudaGraphLaunch(h->graph_meas, h->stream), "su3_sweep_measured: graph launch");
+    for (int i = 0; i < n; ++i) SU3_CUDA(cudaGraphLaunch(exec, h->stream), "su3_sweep_measured: graph launch");
     h->sweep_host += (uint64_t)n;
     // copy back only the n slots just written (two pieces where they wrap)
     const int first = (int)(t0 % (uint64_t)h->meas_cap);
@@ -511,15 +515,32 @@ int su3_set_heatbath(su3_handle h, int max_tries) {
   if (!h) return fail(SU3_EINVAL, "su3_set_heatbath: NULL handle");
   if (max_tries < 1 || max_tries > kMaxHeatbathTries)
     return fail(SU3_EINVAL, "su3_set_heatbath: max_tries %d not in [1, %d]", max_tries, kMaxHeatbathTries);
-  if (max_tries > 1 && su3_decomp_active(h))
-    return fail(SU3_EINVAL, "su3_set_heatbath: a decomposed lattice runs the one-hit heatbath only");
   if (max_tries != h->max_tries) {
     SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_set_heatbath");
     drop_graphs(h);
     if (h->batch) su3_batch_invalidate(h->batch);
+    if (h->decomp) su3_decomp_invalidate(h->decomp);
     h->max_tries = max_tries;
   }
   return SU3_OK;
+}
+
+int su3_bounds_status(unsigned int* status, int clear) {
+  if (!status) return fail(SU3_EINVAL, "su3_bounds_status: NULL status");
+  *status = 0u;
+#ifdef SU3_BOUNDS_CHECK
+  cudaError_t (*const tus[4])(unsigned int*, bool) = {su3k_bounds_status_kernels, su3k_bounds_status_pair,
+                                                        su3k_bounds_status_batch, su3k_bounds_status_decomp};
+  for (auto f : tus) {
+    unsigned int v = 0u;
+    SU3_CUDA(f(&v, clear != 0), "su3_bounds_status");
+    *status |= v;
+  }
+  return SU3_OK;
+#else
+  (void)clear;
+  return fail(SU3_EINVAL, "su3_bounds_status: this library was built without bounds checks");
+#endif
 }
 
 int su3_set_lanes(su3_handle h, int lanes) {

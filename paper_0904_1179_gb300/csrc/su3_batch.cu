@@ -205,6 +205,8 @@ std::map<std::string, std::vector<int>> g_tune_cache;  // key -> {threads, block
 
 }  // namespace
 
+SU3_BOUNDS_STATUS_FN(su3k_bounds_status_batch)
+
 struct su3_batch {
   int n = 0;
   std::vector<Geometry> geoms;

@@ -4,9 +4,9 @@
 // lattice into mpifactor parts each; every sublattice lives in its own MPI
 // process and, between checkerboard steps, sends the boundary links its
 // neighbours need (Appendix A: the checkerboard link storage of a face,
-// Eq. (mscb18)).  With np = 1 the switch lbcex turns that exchange off (plain
-// periodic wrap) or on (the sublattice exchanges with itself), the "1F" and
-// "1" rows of Tables 1 and 2.
+// Eq. (mscb18)).  With np = 1 the switch lbcex turns that exchange off (one
+// sublattice with periodic wrap inside it) or on (the sublattice exchanges
+// with itself), the "1F" and "1" rows of Tables 1 and 2.
 //
 // Here all np sublattices live on one GPU, each in its own extended-box store
 // with a ghost layer on both sides of every cut direction.  One sweep is, for
@@ -32,13 +32,14 @@ using namespace su3dev;
 
 struct su3_decomp {
   int ndmpi = 0, nf = 1, np = 1, lbcex = 1;
-  bool active = false;         // false: np = 1 with the exchange off -- the plain lattice
+  bool active = false;         // true once the sublattice stores exist
   SubGeometry geo{};           // sublattice geometry, origin 0
   size_t sub_elems = 0;        // double2 (FP64) or float4 (FP32) elements per sublattice store
   void* d_sub = nullptr;       // np stores
   int4* d_ghost[2] = {nullptr, nullptr};  // gather lists per parity: {dst sub, dst half, src sub, src half}
   int nghost[2] = {0, 0};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // indexed by stats_on
+  cudaGraphExec_t graph_meas = nullptr;            // sweep with the fused plaquette
   bool subs_current = false;   // sublattice stores hold the configuration
   bool global_current = true;  // the handle's global store holds it
 };
@@ -56,6 +57,9 @@ struct DecompArgs {
   void* subs;
   size_t sub_elems;
   unsigned long long* stats;
+  int count_stats;   // accumulate acceptance statistics
+  int max_tries;     // SU(2) proposals per subgroup (1: one-hit heatbath)
+  double* meas;      // fused plaquette: one partial per block of this phase (nullptr: off)
 };
 
 // Origin of sublattice k (index k = k0 + nf*(k1 + nf*...) over the cut directions).
@@ -70,53 +74,76 @@ __device__ __forceinline__ SubGeometry sub_geometry(const SubGeometry& base, int
   return g;
 }
 
-template <bool STATS>
 __device__ __forceinline__ void count_stats_d(UpdateCount c, unsigned long long* stats) {
-  if (STATS) {
-    const int acc = __reduce_add_sync(0xffffffffu, c.accepted);
-    const int prop = __reduce_add_sync(0xffffffffu, c.proposed);
-    if ((threadIdx.x & 31) == 0) {
-      atomicAdd(&stats[0], (unsigned long long)acc);
-      atomicAdd(&stats[1], (unsigned long long)prop);
-    }
+  const int acc = __reduce_add_sync(0xffffffffu, c.accepted);
+  const int prop = __reduce_add_sync(0xffffffffu, c.proposed);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&stats[0], (unsigned long long)acc);
+    atomicAdd(&stats[1], (unsigned long long)prop);
   }
 }
 
-template <int MU, bool STATS>
+// Block sum of one value per thread into out[block index over the 2D grid], fixed order.
+__device__ __forceinline__ void block_partial_d(double v, double* out) {
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) out[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = w;
+  }
+}
+
+// REPEAT: repeat-until-accepted heatbath (a.max_tries proposals at most).
+// MEAS: the fused plaquette of the odd-site phases of mu = 1, 2, 3, as in the
+// undivided kernels (every link of A_< is final; the ghosts were refreshed by
+// the exchanges after the phases before).
+template <int MU, bool REPEAT, bool MEAS>
 __global__ void __launch_bounds__(kMaxSweepThreads) k_decomp_half_sweep_f64(DecompArgs a) {
   const int k = blockIdx.y;
   const SubGeometry g = sub_geometry(a.g, a.nf, a.ndmpi, k);
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   UpdateCount c{0, 0};
+  double m = 0.0;
   if (h < g.in.Vh) {
-    const UpdateConsts uc{a.three_over_beta_f64, a.three_over_beta, 1};
+    const UpdateConsts uc{a.three_over_beta_f64, a.three_over_beta, a.max_tries};
     double2* U = (double2*)a.subs + (size_t)k * a.sub_elems;
-    c = update_link_f64<MU, false, false>(g, U, h, a.parity, *a.sweep, a.key, uc);
+    c = update_link_f64<MU, false, REPEAT, MEAS>(g, U, h, a.parity, *a.sweep, a.key, uc, &m);
   }
-  count_stats_d<STATS>(c, a.stats);
+  if (a.count_stats) count_stats_d(c, a.stats);
+  if (MEAS) block_partial_d(m, a.meas);
 }
 
-template <int MU, bool STATS, bool EFT>
+template <int MU, bool EFT, bool REPEAT, bool MEAS>
 __global__ void __launch_bounds__(kMaxSweepThreads, 4) k_decomp_half_sweep_f32(DecompArgs a) {
   const int k = blockIdx.y;
   const SubGeometry g = sub_geometry(a.g, a.nf, a.ndmpi, k);
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   UpdateCount c{0, 0};
+  double m = 0.0;
   if (h < g.in.Vh) {
-    const UpdateConsts uc{a.three_over_beta_f64, a.three_over_beta, 1};
+    const UpdateConsts uc{a.three_over_beta_f64, a.three_over_beta, a.max_tries};
     float4* U = (float4*)a.subs + (size_t)k * a.sub_elems;
-    c = update_link_f32<MU, false, EFT, false>(g, U, h, a.parity, *a.sweep, a.key, uc);
+    c = update_link_f32<MU, false, EFT, REPEAT, MEAS>(g, U, h, a.parity, *a.sweep, a.key, uc, &m);
   }
-  count_stats_d<STATS>(c, a.stats);
+  if (a.count_stats) count_stats_d(c, a.stats);
+  if (MEAS) block_partial_d(m, a.meas);
 }
 
 // Boundary exchange of the (mu, parity) links: one thread per ghost cell.
 template <typename E, int NC>
 __global__ void k_decomp_exchange(const int4* __restrict__ list, int n, int mu, int parity, E* subs,
-                                  size_t sub_elems, int Vh) {
+                                  size_t sub_elems, int Vh, int nsub) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int4 e = list[i];
+  if (!link_ok(mu, parity, e.y, Vh) || !link_ok(mu, parity, e.w, Vh) || !link_ok(0, 0, e.x, nsub) ||
+      !link_ok(0, 0, e.z, nsub))
+    return;
   const size_t off = link_base(mu, parity, Vh, NC);
   const E* src = subs + (size_t)e.z * sub_elems + off + e.w;
   E* dst = subs + (size_t)e.x * sub_elems + off + e.y;
@@ -135,6 +162,7 @@ __global__ void k_decomp_move(SubGeometry base, int nf, int ndmpi, E* global, in
   const SubSite st = site_of(g, h, p);
   const int hg = st.s >> 1;
   const int hs = store_index(g, st, h);
+  if (!link_ok(0, p, hg, Vh_global) || !link_ok(0, p, hs, g.Vh)) return;
   E* sub = subs + (size_t)k * sub_elems;
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
@@ -183,26 +211,30 @@ __global__ void k_decomp_move_f32_pairs(SubGeometry base, int nf, int ndmpi, flo
   }
 }
 
+template <int MU, bool REPEAT, bool MEAS>
+cudaError_t launch_update_form(const DecompArgs& a, int precision, const dim3& grid, int threads, cudaStream_t s) {
+  if (precision == SU3_FP64)
+    k_decomp_half_sweep_f64<MU, REPEAT, MEAS><<<grid, threads, 0, s>>>(a);
+  else if (precision == SU3_FP32_EFT)
+    k_decomp_half_sweep_f32<MU, true, REPEAT, MEAS><<<grid, threads, 0, s>>>(a);
+  else
+    k_decomp_half_sweep_f32<MU, false, REPEAT, MEAS><<<grid, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int MU>
 cudaError_t launch_update_mu(const DecompArgs& a, int precision, bool stats, int threads, int np, cudaStream_t s) {
   const dim3 grid((a.g.in.Vh + threads - 1) / threads, np);
-  if (precision == SU3_FP64) {
-    if (stats)
-      k_decomp_half_sweep_f64<MU, true><<<grid, threads, 0, s>>>(a);
-    else
-      k_decomp_half_sweep_f64<MU, false><<<grid, threads, 0, s>>>(a);
-  } else if (precision == SU3_FP32_EFT) {
-    if (stats)
-      k_decomp_half_sweep_f32<MU, true, true><<<grid, threads, 0, s>>>(a);
-    else
-      k_decomp_half_sweep_f32<MU, false, true><<<grid, threads, 0, s>>>(a);
-  } else {
-    if (stats)
-      k_decomp_half_sweep_f32<MU, true, false><<<grid, threads, 0, s>>>(a);
-    else
-      k_decomp_half_sweep_f32<MU, false, false><<<grid, threads, 0, s>>>(a);
+  DecompArgs b = a;
+  b.count_stats = stats ? 1 : 0;
+  const bool repeat = a.max_tries > 1;
+  if (MU > 0 && a.meas) {  // fused plaquette (statistics are not counted in these phases)
+    b.count_stats = 0;
+    return repeat ? launch_update_form<MU, true, (MU > 0)>(b, precision, grid, threads, s)
+                  : launch_update_form<MU, false, (MU > 0)>(b, precision, grid, threads, s);
   }
-  return cudaGetLastError();
+  return repeat ? launch_update_form<MU, true, false>(b, precision, grid, threads, s)
+                : launch_update_form<MU, false, false>(b, precision, grid, threads, s);
 }
 
 cudaError_t launch_update(const DecompArgs& a, int mu, int precision, bool stats, int threads, int np, cudaStream_t s) {
@@ -220,10 +252,12 @@ cudaError_t launch_exchange(const su3_decomp* d, int precision, int mu, int pari
   const int threads = 256, blocks = (n + threads - 1) / threads;
   if (precision == SU3_FP64)
     k_decomp_exchange<double2, kEntriesF64><<<blocks, threads, 0, s>>>(d->d_ghost[parity], n, mu, parity,
-                                                                       (double2*)d->d_sub, d->sub_elems, d->geo.Vh);
+                                                                       (double2*)d->d_sub, d->sub_elems, d->geo.Vh,
+                                                                       d->np);
   else
     k_decomp_exchange<float4, kGroupsF32><<<blocks, threads, 0, s>>>(d->d_ghost[parity], n, mu, parity,
-                                                                     (float4*)d->d_sub, d->sub_elems, d->geo.Vh);
+                                                                     (float4*)d->d_sub, d->sub_elems, d->geo.Vh,
+                                                                     d->np);
   return cudaGetLastError();
 }
 
@@ -270,12 +304,23 @@ DecompArgs decomp_args(const su3_lattice* h, int parity) {
   a.subs = d->d_sub;
   a.sub_elems = d->sub_elems;
   a.stats = h->d_stats;
+  a.max_tries = h->max_tries;
+  a.meas = nullptr;
   return a;
 }
 
-int enqueue_phase(su3_lattice* h, int mu, int parity) {
+// Blocks of one decomposed half-sweep launch (the fused plaquette leaves one
+// partial per block).
+int phase_blocks(const su3_lattice* h) {
+  const su3_decomp* d = h->decomp;
+  return (d->geo.in.Vh + h->threads - 1) / h->threads * d->np;
+}
+
+int enqueue_phase(su3_lattice* h, int mu, int parity, double* meas = nullptr) {
   su3_decomp* d = h->decomp;
-  SU3_CUDA(launch_update(decomp_args(h, parity), mu, h->precision, h->stats_on, h->threads, d->np, h->stream),
+  DecompArgs a = decomp_args(h, parity);
+  a.meas = meas;
+  SU3_CUDA(launch_update(a, mu, h->precision, h->stats_on, h->threads, d->np, h->stream),
            "decomposed half-sweep launch");
   SU3_CUDA(launch_exchange(d, h->precision, mu, parity, h->stream), "boundary exchange launch");
   return SU3_OK;
@@ -293,15 +338,25 @@ int ensure_subs(su3_lattice* h) {
   return SU3_OK;
 }
 
-int ensure_decomp_graph(su3_lattice* h) {
+// With `measured`, the odd-site phases of mu = 1, 2, 3 leave block partials of
+// the fused plaquette in h->d_meas_parts and a last kernel sums them into the
+// ring slot of this sweep (as in the undivided sweep).
+int ensure_decomp_graph(su3_lattice* h, bool measured = false) {
   su3_decomp* d = h->decomp;
-  cudaGraphExec_t& exec = d->graph[h->stats_on ? 1 : 0];
+  cudaGraphExec_t& exec = measured ? d->graph_meas : d->graph[h->stats_on ? 1 : 0];
   if (exec) return SU3_OK;
+  const int blocks = phase_blocks(h);
   cudaGraph_t graph = nullptr;
   SU3_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
   int rc = SU3_OK;
   for (int mu = 0; mu < 4 && rc == SU3_OK; ++mu)
-    for (int p = 0; p < 2 && rc == SU3_OK; ++p) rc = enqueue_phase(h, mu, p);
+    for (int p = 0; p < 2 && rc == SU3_OK; ++p)
+      rc = enqueue_phase(h, mu, p, measured && p == 1 && mu >= 1 ? h->d_meas_parts + (size_t)(mu - 1) * blocks : nullptr);
+  if (rc == SU3_OK && measured) {
+    const cudaError_t e = su3k_launch_meas_final(h->d_meas_parts, 3 * blocks, 1.0 / (6.0 * (double)h->V), h->d_sweep,
+                                                 h->d_meas, h->meas_cap, h->stream);
+    if (e != cudaSuccess) rc = su3_cuda_fail(e, "plaquette reduction launch");
+  }
   if (rc == SU3_OK) {
     const cudaError_t e = su3k_launch_increment(h->d_sweep, 1, h->stream);
     if (e != cudaSuccess) rc = su3_cuda_fail(e, "sweep counter launch");
@@ -410,12 +465,18 @@ void host_sub_geometry(const int L[4], int ndmpi, int mpifactor, SubGeometry& g)
 // ---------------------------------------------------------------------------
 bool su3_decomp_active(const su3_lattice* h) { return h && h->decomp && h->decomp->active; }
 
+SU3_BOUNDS_STATUS_FN(su3k_bounds_status_decomp)
+
 void su3_decomp_invalidate(su3_decomp* d) {
   for (auto& g : d->graph)
     if (g) {
       cudaGraphExecDestroy(g);
       g = nullptr;
     }
+  if (d->graph_meas) {
+    cudaGraphExecDestroy(d->graph_meas);
+    d->graph_meas = nullptr;
+  }
 }
 
 void su3_decomp_release(su3_decomp* d) {
@@ -435,6 +496,18 @@ int su3_decomp_sweep(su3_lattice* h, int nsweeps) {
   cudaGraphExec_t exec = h->decomp->graph[h->stats_on ? 1 : 0];
   for (int n = 0; n < nsweeps; ++n) SU3_CUDA(cudaGraphLaunch(exec, h->stream), "su3_sweep: graph launch");
   h->sweep_host += (uint64_t)nsweeps;
+  h->decomp->global_current = false;
+  return SU3_OK;
+}
+
+int su3_decomp_meas_blocks(su3_lattice* h) { return phase_blocks(h); }
+
+int su3_decomp_sweep_measured_graph(su3_lattice* h, cudaGraphExec_t* out) {
+  int rc = ensure_subs(h);
+  if (rc != SU3_OK) return rc;
+  rc = ensure_decomp_graph(h, true);
+  if (rc != SU3_OK) return rc;
+  *out = h->decomp->graph_meas;
   h->decomp->global_current = false;
   return SU3_OK;
 }
@@ -487,18 +560,18 @@ int su3_decomp_create(int L0, int L1, int L2, int L3, double beta, uint64_t seed
   d->nf = mpifactor;
   d->np = (int)np;
   d->lbcex = lbcex;
-  d->active = lbcex != 0;
-  if (!d->active) {  // one sublattice without exchange: the plain periodic lattice
-    *out = h;
-    return SU3_OK;
-  }
+  d->active = true;
+  // lbcex = 0 (np = 1): one sublattice covering the lattice, no direction
+  // cut, periodic wrap inside it and no exchange -- the sublattice kernel
+  // without ghost layers, the like-for-like baseline of the cut runs
+  const int ncut = lbcex ? ndmpi : 0;
   SubGeometry& g = d->geo;
-  host_sub_geometry(L, ndmpi, mpifactor, g);
+  host_sub_geometry(L, ncut, mpifactor, g);
   const int ncomp = precision == SU3_FP64 ? kEntriesF64 : kGroupsF32;
   const size_t elem = precision == SU3_FP64 ? sizeof(double2) : sizeof(float4);
   d->sub_elems = (size_t)8 * ncomp * g.Vh;
   std::vector<int4> lists[2];
-  build_ghost_lists(L, ndmpi, mpifactor, d->np, g, lists);
+  build_ghost_lists(L, ncut, mpifactor, d->np, g, lists);
   cudaError_t e = cudaMalloc(&d->d_sub, d->sub_elems * elem * np);
   for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
     d->nghost[p] = (int)lists[p].size();

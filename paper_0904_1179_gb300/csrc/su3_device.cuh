@@ -491,6 +491,49 @@ __device__ __forceinline__ int nb_half2(const SubGeometry& g, const SubSite& s, 
 }
 
 // ---------------------------------------------------------------------------
+// Bounds-checked build (compiled with -DSU3_BOUNDS_CHECK; the product build
+// has no checks): every link access checks its direction, parity and index
+// against the extent of the store it addresses -- a single lattice, one
+// replica of a batch, one sublattice's extended box.  An access out of range
+// is skipped (a load yields zeros) and bit 0 of the status word of its
+// translation unit is set; nothing traps.  su3_bounds_status() reads and
+// clears the words.
+// ---------------------------------------------------------------------------
+#ifdef SU3_BOUNDS_CHECK
+static __device__ unsigned int g_su3_bounds_status = 0u;
+#endif
+
+__device__ __forceinline__ bool link_ok(int mu, int p, long long h, long long n) {
+#ifdef SU3_BOUNDS_CHECK
+  if ((unsigned)mu >= 4u || (unsigned)p >= 2u || (unsigned long long)h >= (unsigned long long)n) {
+    atomicOr(&g_su3_bounds_status, 1u);
+    return false;
+  }
+#endif
+  return true;
+}
+
+// Host side: this translation unit's status word (0 and no error in a build
+// without checks).
+#ifdef SU3_BOUNDS_CHECK
+#define SU3_BOUNDS_STATUS_FN(name)                                                             \
+  cudaError_t name(unsigned int* v, bool clear) {                                               \
+    cudaError_t e = cudaMemcpyFromSymbol(v, g_su3_bounds_status, sizeof(unsigned int));         \
+    if (e == cudaSuccess && clear) {                                                            \
+      const unsigned int z = 0u;                                                                \
+      e = cudaMemcpyToSymbol(g_su3_bounds_status, &z, sizeof(unsigned int));                    \
+    }                                                                                           \
+    return e;                                                                                   \
+  }
+#else
+#define SU3_BOUNDS_STATUS_FN(name) \
+  cudaError_t name(unsigned int* v, bool) { \
+    *v = 0u;                                \
+    return cudaSuccess;                     \
+  }
+#endif
+
+// ---------------------------------------------------------------------------
 // Link loads and stores.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ size_t link_base(int mu, int p, int Vh, int ncomp) {
@@ -509,6 +552,11 @@ __device__ __forceinline__ float4 ld_link(const float4* p) {
 template <bool CG = false>
 __device__ __forceinline__ mat3<double> load_f64(const double2* __restrict__ U, int mu, int p, int h, int Vh) {
   mat3<double> m;
+  if (!link_ok(mu, p, h, Vh)) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) m.e[c / 3][c % 3] = mk(0.0, 0.0);
+    return m;
+  }
   const double2* b = U + link_base(mu, p, Vh, kEntriesF64) + h;
 #pragma unroll
   for (int c = 0; c < 9; ++c) {
@@ -519,6 +567,7 @@ __device__ __forceinline__ mat3<double> load_f64(const double2* __restrict__ U, 
 }
 
 __device__ __forceinline__ void store_f64(double2* U, int mu, int p, int h, int Vh, const mat3<double>& m) {
+  if (!link_ok(mu, p, h, Vh)) return;
   double2* b = U + link_base(mu, p, Vh, kEntriesF64) + h;
 #pragma unroll
   for (int c = 0; c < 9; ++c) b[(size_t)c * Vh] = make_double2(m.e[c / 3][c % 3].re, m.e[c / 3][c % 3].im);
@@ -528,6 +577,11 @@ __device__ __forceinline__ void store_f64(double2* U, int mu, int p, int h, int 
 template <bool CG = false>
 __device__ __forceinline__ mat3<float> load_f32_rows01(const float4* __restrict__ U, int mu, int p, int h, int Vh) {
   mat3<float> m;
+  if (!link_ok(mu, p, h, Vh)) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) m.e[0][k] = m.e[1][k] = mk(0.f, 0.f);
+    return m;
+  }
   const float4* b = U + link_base(mu, p, Vh, kGroupsF32) + h;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -547,6 +601,7 @@ __device__ __forceinline__ mat3<float> load_f32(const float4* __restrict__ U, in
 
 // r = row 0 (re, im) x 3 columns, then row 1 (re, im) x 3 columns.
 __device__ __forceinline__ void store_f32_rows01(float4* U, int mu, int p, int h, int Vh, const float r[12]) {
+  if (!link_ok(mu, p, h, Vh)) return;
   float4* b = U + link_base(mu, p, Vh, kGroupsF32) + h;
 #pragma unroll
   for (int k = 0; k < 3; ++k) b[(size_t)k * Vh] = make_float4(r[2 * k], r[6 + 2 * k], r[2 * k + 1], r[6 + 2 * k + 1]);

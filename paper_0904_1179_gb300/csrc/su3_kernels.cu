@@ -533,6 +533,8 @@ cudaError_t su3k_launch_half_sweep(const HalfSweepArgs& a, int mu, int precision
   }
 }
 
+SU3_BOUNDS_STATUS_FN(su3k_bounds_status_kernels)
+
 int su3k_half_sweep_blocks(const HalfSweepArgs& a, int precision, int threads) {
   const int n = (precision != 0 && a.pairs) ? a.pgeom.Vh : a.geom.Vh;
   return (n + threads - 1) / threads;

@@ -25,6 +25,7 @@ struct HalfSweepArgs {
   int split;                  // FP64 one-hit sweep of a small lattice: four lanes per link (see k_half_sweep_f64_split)
   int pairs;                  // FP32 store in the site-paired layout (L3 a multiple of 4; su3_sitepair.cuh)
   su3dev::Geometry pgeom;     // the pair lattice L0 x L1 x L2 x L3/2 (pairs only)
+  int tile2;                  // paired kernel: > 0 runs its blocks in tiles of tile2 x2-lines (su3_kernels_pair.cu)
 };
 
 struct InitArgs {
@@ -62,10 +63,21 @@ int su3k_half_sweep_blocks(const HalfSweepArgs& a, int precision, int threads);
 // The site-paired FP32 half-sweep (su3_kernels_pair.cu): one thread per pair
 // of links, the staple's loads staged through shared memory.
 cudaError_t su3k_launch_half_sweep_pair(const HalfSweepArgs& a, int mu, bool eft, bool stats, int threads, cudaStream_t s);
+// Block order of the paired kernel for a pair lattice gp and block size:
+// tile2 (> 0: blocks walk tiles of tile2 lines of x2 per step of x3), 0 for
+// the natural order.
+int su3k_pair_tile2(const su3dev::Geometry& gp, int threads);
 // Dynamic shared memory per thread of the site-paired half-sweep, and the
 // kernel attributes it needs (set once, before any stream capture).
 constexpr int kPairRingBytesPerThread = 3 * 7 * 16;
 cudaError_t su3k_prepare();
+
+// Status words of the bounds-checked build, one per translation unit with
+// kernels (su3_device.cuh, link_ok); 0 in the product build.
+cudaError_t su3k_bounds_status_kernels(unsigned int* v, bool clear);
+cudaError_t su3k_bounds_status_pair(unsigned int* v, bool clear);
+cudaError_t su3k_bounds_status_batch(unsigned int* v, bool clear);
+cudaError_t su3k_bounds_status_decomp(unsigned int* v, bool clear);
 cudaError_t su3k_launch_increment(uint64_t* counter, uint64_t n, cudaStream_t s);
 // Sum the nparts fused-plaquette partials of one sweep (fixed order) into
 // out[*sweep % cap] * scale.

@@ -32,12 +32,31 @@ __device__ __forceinline__ void block_partial_pair(double v, double* out) {
   }
 }
 
+// Order of the blocks.  A line is the hL0 L1 pairs of one (x2, x3) of the
+// pair lattice.  In the natural order the x3 neighbours of a line were last
+// touched one whole x2 sweep (L2 lines) earlier; when that window of L2 lines
+// of all eight (mu, parity) arrays outgrows the L2 cache (a 64^4 lattice: 64
+// lines of 1.5 MB), the blocks instead walk the (x2, x3) plane in columns of
+// tile2 lines of x2, x3 slower inside a column, so that the x3 neighbours are
+// tile2 lines back.  Only the x2 neighbours across a column edge are then
+// far away.  The mapping is a permutation of the blocks, each block still one
+// contiguous range of pairs inside one line.
+__device__ __forceinline__ int pair_block_start(const Geometry& gp, int tile2, int block, int threads) {
+  if (tile2 <= 0) return block * threads;
+  const int npl = gp.hL0 * gp.L1;  // pairs per line (a multiple of threads when tile2 > 0)
+  const int bpl = npl / threads;
+  const int line = block / bpl, sub = block - line * bpl;
+  const int col = line / (tile2 * gp.L3), r = line - col * tile2 * gp.L3;
+  const int x3 = r / tile2, x2 = col * tile2 + (r - x3 * tile2);
+  return npl * (x2 + gp.L2 * x3) + sub * threads;
+}
+
 // 128 registers per thread: two blocks of 256 or four of 128 threads per SM.
 template <int MU, bool EFT, bool REPEAT, bool MEAS>
 __global__ void __launch_bounds__(256, 2) k_half_sweep_f32_pair(HalfSweepArgs args, int stats) {
   extern __shared__ float4 smem[];
   const Geometry& gp = args.pgeom;
-  const int j0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = pair_block_start(gp, args.tile2, blockIdx.x, blockDim.x) + threadIdx.x;
   const bool active = j0 < gp.Vh;
   const int j = active ? j0 : gp.Vh - 1;  // every lane takes part; a lane past the end stores nothing
   const UpdateConsts uc{args.three_over_beta_f64, args.three_over_beta, args.max_tries};
@@ -122,6 +141,19 @@ cudaError_t su3k_launch_half_sweep_pair(const HalfSweepArgs& a, int mu, bool eft
     case 2: return launch_pair_mu<2, false>(a, stats, threads, s);
     default: return launch_pair_mu<3, false>(a, stats, threads, s);
   }
+}
+
+SU3_BOUNDS_STATUS_FN(su3k_bounds_status_pair)
+
+int su3k_pair_tile2(const Geometry& gp, int threads) {
+  const long long npl = (long long)gp.hL0 * gp.L1;
+  const long long line_bytes = npl * 96 * 8;  // one line of all eight (mu, parity) arrays
+  const long long window = 32LL << 20;        // keep the x3 reuse window well inside the 129 MB L2
+  if (npl % threads != 0 || line_bytes * gp.L2 <= window) return 0;
+  int best = 0;
+  for (int t = 2; t < gp.L2; ++t)
+    if (gp.L2 % t == 0 && line_bytes * t <= window) best = t;
+  return best;
 }
 
 // The paired kernels take up to 86 KB of dynamic shared memory (256 threads);

@@ -43,6 +43,11 @@ __device__ __forceinline__ void pset(pm3& m, int i, int k, cx<float> v) {
 template <bool CG>
 __device__ __forceinline__ pm3 load_pm3(const float4* __restrict__ U, int mu, int p, int h, int Vh) {
   pm3 m;
+  if (!link_ok(mu, p, h, Vh)) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) m.re[k] = m.im[k] = make_float2(0.f, 0.f);
+    return m;
+  }
   const float4* b = U + link_base(mu, p, Vh, kGroupsF32) + h;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {

@@ -80,6 +80,11 @@ void su3_decomp_release(su3_decomp* d);
 void su3_decomp_invalidate(su3_decomp* d);
 int su3_decomp_sweep(su3_lattice* h, int nsweeps);
 int su3_decomp_half_sweep(su3_lattice* h, int mu, int parity);
+// Partials per phase of the decomposed sweep's fused plaquette, and the graph
+// of one measured decomposed sweep (built on first use; it writes the
+// handle's d_meas_parts and d_meas ring).
+int su3_decomp_meas_blocks(su3_lattice* h);
+int su3_decomp_sweep_measured_graph(su3_lattice* h, cudaGraphExec_t* out);
 int su3_decomp_sync_global(su3_lattice* h);   // before reading the global store
 void su3_decomp_global_written(su3_lattice* h);  // after writing it
 // Largest number of SU(2) proposals per subgroup (the try index has 26 bits

@@ -138,6 +138,7 @@ __device__ __forceinline__ void swap_halves(PM& m, bool sw) {
 
 __device__ __forceinline__ void store_pm_rows01(float4* U, int mu, int p, int j, int Vp, const float2 re[2][3],
                                                 const float2 im[2][3]) {
+  if (!link_ok(mu, p, j, Vp)) return;
   float4* b = U + link_base(mu, p, Vp, kEntriesPair) + j;
 #pragma unroll
   for (int e = 0; e < 6; ++e)
@@ -309,6 +310,7 @@ __device__ __forceinline__ RolledLink rolled_link(const Geometry& gp, const Site
 template <bool CG>
 __device__ __forceinline__ void rolled_issue(const Geometry& gp, const float4* U, const RolledLink& l,
                                              const PairRing& rg, int slot) {
+  if (!link_ok(l.mu, l.par, l.idx, gp.Vh)) return;
   const float4* b = U + link_base(l.mu, l.par, gp.Vh, kEntriesPair) + l.idx;
   const uint32_t sa = rg.sa + (uint32_t)(16 * slot * rg.step);
 #pragma unroll

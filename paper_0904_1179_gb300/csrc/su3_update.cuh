@@ -61,8 +61,13 @@ __device__ __forceinline__ pm3 load_pm3_l(const float4* __restrict__ U, int mu, 
   if constexpr (PAIRS) {
     const int Vp = Vh / 2;
     const int half = h >= Vp ? 1 : 0;
-    const float* b = (const float*)(U + link_base(mu, p, Vp, 6) + (h - half * Vp)) + half;
     pm3 m;
+    if (!link_ok(mu, p, h, Vh)) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) m.re[k] = m.im[k] = make_float2(0.f, 0.f);
+      return m;
+    }
+    const float* b = (const float*)(U + link_base(mu, p, Vp, 6) + (h - half * Vp)) + half;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const float* e0 = b + (size_t)4 * k * Vp;        // entry (row 0, column k)
@@ -80,6 +85,11 @@ __device__ __forceinline__ pm3 load_pm3_l(const float4* __restrict__ U, int mu, 
 // as 12 floats, row 0 then row 1, (re, im) per column (as store_f32_rows01
 // takes them); Vp = V/4 pairs per (mu, parity), pair h mod Vp, member h / Vp.
 __device__ __forceinline__ void load_pair_site(const float4* __restrict__ U, int mu, int p, int h, int Vp, float r[12]) {
+  if (!link_ok(mu, p, h, 2LL * Vp)) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) r[c] = 0.f;
+    return;
+  }
   const int half = h >= Vp ? 1 : 0;
   const float* b = (const float*)(U + link_base(mu, p, Vp, 6) + (h - half * Vp)) + half;
 #pragma unroll
@@ -90,6 +100,7 @@ __device__ __forceinline__ void load_pair_site(const float4* __restrict__ U, int
 }
 
 __device__ __forceinline__ void store_pair_site(float4* U, int mu, int p, int h, int Vp, const float r[12]) {
+  if (!link_ok(mu, p, h, 2LL * Vp)) return;
   const int half = h >= Vp ? 1 : 0;
   float* b = (float*)(U + link_base(mu, p, Vp, 6) + (h - half * Vp)) + half;
 #pragma unroll

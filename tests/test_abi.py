@@ -96,6 +96,10 @@ def test_null_handle_calls(lib):
     assert lib.su3_set_sweep_count(None, 0) == su3.SU3_EINVAL
     assert lib.su3_set_block_size(None, 64) == su3.SU3_EINVAL
     assert lib.su3_set_lanes(None, 1) == su3.SU3_EINVAL
+    # the product build has no bounds checks compiled in
+    v = ctypes.c_uint(7)
+    assert lib.su3_bounds_status(ctypes.byref(v), 0) == su3.SU3_EINVAL
+    assert "without bounds checks" in su3.su3_last_error()
     v = lib.su3_plaquette(None)
     assert v != v
 

@@ -124,11 +124,55 @@ def test_bad_arguments():
             su3.su3_decomp_create(*L, BETA, 1, su3.SU3_COLD, su3.SU3_FP64, nd, nf, ex)
     with su3.Lattice(L, BETA, 1, start=su3.SU3_COLD, decomp=(2, 2, 1)) as lat:
         with pytest.raises(su3.Su3Error):
-            lat.sweep_measured(1)
+            lat.set_lanes(1)
+        lat.set_stats(True)
         with pytest.raises(su3.Su3Error):
-            lat.set_heatbath(4)
-        lat.set_heatbath(1)
+            lat.sweep_measured(1)
+        lat.set_stats(False)
         lat.sweep(1)
+
+
+# The fused plaquette and the repeat-until-accepted heatbath on decomposed
+# lattices: the same chain and the same per-sweep plaquettes as the undivided
+# lattice, bit for bit (the sublattice kernels run the same update code on
+# the same neighbours and random numbers, and the per-block partial sums of
+# the plaquette are added in a fixed order -- different blocks than the
+# undivided kernel's, so the plaquettes agree to summation order).
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("decomp", [(2, 2, 1), (4, 2, 1), (1, 1, 0)])
+def test_decomposed_measured_sweep_and_repeat_heatbath(prec, decomp):
+    L = (8, 8, 8, 8)
+    tol = 1e-13 if prec == su3.SU3_FP64 else 2e-6
+    for max_tries in (1, 6):
+        with su3.Lattice(L, BETA, 12, start=su3.SU3_HOT, precision=prec) as a, \
+                su3.Lattice(L, BETA, 12, start=su3.SU3_HOT, precision=prec, decomp=decomp) as b:
+            a.set_heatbath(max_tries)
+            b.set_heatbath(max_tries)
+            pa = a.sweep_measured(3)
+            pb = b.sweep_measured(3)
+            assert np.array_equal(a.get_links(), b.get_links())
+            assert np.abs(pa - pb).max() < 1e-13
+            assert abs(pb[-1] - b.plaquette()) < tol
+            a.set_stats(True)
+            b.set_stats(True)
+            a.sweep(1)
+            b.sweep(1)
+            assert a.stats() == b.stats()
+            assert np.array_equal(a.get_links(), b.get_links())
+
+
+def test_decomposed_measured_and_repeat_match_oracle():
+    L = (4, 8, 4, 4)
+    U0 = oracle.hot_start(L, 3)
+    for max_tries in (1, 5):
+        O = U0.copy()
+        stats, plaq = oracle.sweep(L, BETA, 9, 0, 2, O, max_tries=max_tries)
+        with su3.Lattice(L, BETA, 9, start=su3.SU3_COLD, decomp=(2, 2, 1)) as lat:
+            lat.set_links(U0)
+            lat.set_heatbath(max_tries)
+            got = lat.sweep_measured(2)
+            assert np.abs(lat.get_links() - O).max() < 1e-12
+            assert np.abs(got - plaq).max() < 1e-13
 
 
 def test_full_size_32x4_sixteen_sublattices():
