@@ -81,7 +81,17 @@ def peaks():
 # paper_0904_1179_gb300/csrc/*.cu and *.cuh, sorted by name) at capture time.
 # A line reports the figure only while the sources still hash the same;
 # otherwise its traffic is null and the line says why.
-NCU_TRAFFIC = {}
+_SRC_A04220F = "449a92e7f01809806104f79742e0e6963fa6c958ec01f177500c8d013e2905bb"
+NCU_TRAFFIC = {
+    "fp32_mixed": {"bytes": 208.123392e6 + 16.535552e6, "sources_sha256": _SRC_A04220F,
+                   "capture": "ncu --set full -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile fp32_mixed"},
+    "fp32_eft": {"bytes": 208.156416e6 + 16.818176e6, "sources_sha256": _SRC_A04220F,
+                 "capture": "ncu --set full -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile fp32_eft"},
+    "batched": {"bytes": 3.033858e9 + 0.418697216e9, "sources_sha256": _SRC_A04220F,
+                "capture": "ncu -k regex:k_batch_sweep -s 1 -c 1 python bench.py --profile batched"},
+    "batched_eft": {"bytes": 3.033844e9 + 0.419232512e9, "sources_sha256": _SRC_A04220F,
+                    "capture": "ncu -k regex:k_batch_sweep -s 1 -c 1 python bench.py --profile batched_eft"},
+}
 
 
 def kernel_sources_sha():
