@@ -508,5 +508,8 @@ class Lattice:
     def set_lanes(self, lanes):
         su3_set_lanes(self.handle, lanes)
 
+    def status(self):
+        su3_status(self.handle)
+
     def set_heatbath(self, max_tries):
         su3_set_heatbath(self.handle, max_tries)
