@@ -427,29 +427,37 @@ def run_reference(args):
     return 0
 
 
-def variant_fp32(su3, stream, steps, warmup, world, hbm_peak, peak_kind, precision=None):
-    """The FP32 sweep of the 32^4 lattice.  The events bracket each sweep's
-    graph (eight half-sweep kernels and the sweep-counter increment), so the
-    kernel time below slightly overstates the kernels' own."""
+def variant_fp32(su3, stream, steps, warmup, world, hbm_peak, peak_kind, precision=None, schedule=None):
+    """The FP32 sweep of the 32^4 lattice.  schedule: None = the library's
+    default (one persistent kernel per sweep at 32^4), or su3.SU3_SCHED_PHASES
+    for the eight half-sweep kernels.  The events bracket each sweep's graph
+    (counter reset, sweep kernel(s), sweep-counter increment), so the kernel
+    time below slightly overstates the kernels' own."""
     import numpy as np
     if precision is None:
         precision = su3.SU3_FP32_MIXED
     eft = precision == su3.SU3_FP32_EFT
     with su3.Lattice(DIMS, BETA, SEED, start=su3.SU3_HOT, precision=precision,
                      stream=stream.cuda_stream) as lat:
+        if schedule is not None:
+            lat.set_schedule(schedule)
+        persistent = lat.schedule == su3.SU3_SCHED_PERSISTENT
         total_ms, sweep_ms, _ = time_sweeps(lat, stream, steps, warmup, SWEEPS_PER_STEP, world)
         plaq = lat.plaquette()
     V = int(np.prod(DIMS))
     ups = 4 * V * SWEEPS_PER_STEP * steps / (total_ms * 1e-3)
-    kernel_ms = statistics.mean(sweep_ms) / 8
-    bytes_per_launch = BYTES_PER_UPDATE["fp32_mixed"] * (V // 2)
+    launches = 1 if persistent else 8  # sweep kernel launches per sweep
+    kernel_ms = statistics.mean(sweep_ms) / launches
+    bytes_per_launch = BYTES_PER_UPDATE["fp32_mixed"] * (V // 2) * (8 // launches)
     achieved = bytes_per_launch / (kernel_ms * 1e-3) / 1e9
     gs = ("Gram-Schmidt coefficients as compensated FP32 sums (error-free transformations, ~2^-47)" if eft
           else "FP64 Gram-Schmidt coefficients")
-    traffic, provenance = traffic_of("fp32_eft" if eft else "fp32_mixed")
-    kernel = "k_half_sweep_f32_pair (site-paired FP32 half-sweep, eight launches per sweep)"
+    traffic, provenance = traffic_of(("fp32_eft" if eft else "fp32_mixed") + ("" if persistent else "_phases"))
+    kernel = ("k_sweep_f32_pair (site-paired FP32 sweep: the eight half-sweeps in one launch)" if persistent
+              else "k_half_sweep_f32_pair (site-paired FP32 half-sweep, eight launches per sweep)")
     return {"workload": "32^4 beta=5.7 hot start seed 7, FP32-mixed (12-real FP32 links, FP32 staple and "
-                        "heatbath, %s), 2 sweeps/step" % gs,
+                        "heatbath, %s), 2 sweeps/step, %s" % (gs, "one persistent kernel per sweep" if persistent
+                                                             else "eight half-sweep kernels per sweep"),
             "value": ups, "unit": UNIT, "ms_per_step": total_ms / steps,
             "dtype": "f32 (compensated-f32 reunitarisation)" if eft else "f32 (f64 reunitarisation)",
             "plaquette_after": plaq,
@@ -513,6 +521,9 @@ def run_profile_case(case):
                               "halo_links_per_sweep": lat.decomp_info()[4], "plaquette": lat.plaquette()}))
         return 0
     dims, beta = (DIMS, BETA)
+    schedule = None
+    if case.endswith("_phases"):  # the eight half-sweep kernels instead of the persistent sweep
+        schedule, case = su3.SU3_SCHED_PHASES, case[:-7]
     if case.endswith("_64"):
         dims, beta, case = (64, 64, 64, 64), 6.0, case[:-3]
     elif case.endswith("_64s"):  # 64^3 x 16: the x3 lines of 64^4 in 805 MB (FP32)
@@ -523,8 +534,11 @@ def run_profile_case(case):
         dims, case = (8, 8, 8, 8), case[:-2]
     prec = {"fp64": su3.SU3_FP64, "fp32_mixed": su3.SU3_FP32_MIXED, "fp32_eft": su3.SU3_FP32_EFT}[case]
     with su3.Lattice(dims, beta, SEED, start=su3.SU3_HOT, precision=prec) as lat:
+        if schedule is not None:
+            lat.set_schedule(schedule)
         lat.sweep(3)
-        print(json.dumps({"profile_case": case, "lattice": list(dims), "sweeps": 3, "plaquette": lat.plaquette()}))
+        print(json.dumps({"profile_case": case, "lattice": list(dims), "sweeps": 3, "schedule": lat.schedule,
+                          "plaquette": lat.plaquette()}))
     return 0
 
 
@@ -889,7 +903,8 @@ def main():
                     help="the paper's Table 1 columns in full (FP64 and FP32-mixed), with the oracle beside them")
     ap.add_argument("--large-sweeps", type=int, default=100)
     ap.add_argument("--profile", choices=["fp64", "fp32_mixed", "fp32_eft", "batched", "batched_eft", "fp64_64", "fp32_mixed_64", "decomp16",
-                             "fp64_8", "fp32_mixed_64s", "fp32_eft_64s", "fp32_mixed_48", "fp32_eft_48"],
+                             "fp64_8", "fp32_mixed_64s", "fp32_eft_64s", "fp32_mixed_48", "fp32_eft_48",
+                             "fp32_mixed_phases", "fp32_eft_phases"],
                     help="small case for ncu: create the 32^4 lattice (or the 96-replica batch) and run 3 graphed "
                          "sweeps, nothing else")
     args = ap.parse_args()
@@ -941,6 +956,11 @@ def main():
         variants["fp32_mixed"] = variant_fp32(su3, stream, args.steps, args.warmup, 1, hbm_peak, peak_kind)
         variants["fp32_eft"] = variant_fp32(su3, stream, args.steps, args.warmup, 1, hbm_peak, peak_kind,
                                             su3.SU3_FP32_EFT)
+        # like for like: the same sweeps as eight half-sweep kernels
+        variants["fp32_mixed_phases"] = variant_fp32(su3, stream, args.steps, args.warmup, 1, hbm_peak, peak_kind,
+                                                     schedule=su3.SU3_SCHED_PHASES)
+        variants["fp32_eft_phases"] = variant_fp32(su3, stream, args.steps, args.warmup, 1, hbm_peak, peak_kind,
+                                                   su3.SU3_FP32_EFT, schedule=su3.SU3_SCHED_PHASES)
         variants["batched"] = variant_batched(su3, stream, args.steps, args.warmup, hbm_peak, peak_kind)
         variants["batched_eft"] = variant_batched_eft(su3, stream, args.steps, args.warmup, hbm_peak, peak_kind)
         variants["measured_fp64"] = variant_measured(su3, stream, args.steps, args.warmup, su3.SU3_FP64)

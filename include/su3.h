@@ -75,7 +75,7 @@ enum {
   SU3_EINVAL = -1,   /* bad argument: NULL handle/pointer, odd or too large extent, beta <= 0, bad enum */
   SU3_ENOMEM = -2,   /* device or pinned-host allocation failed */
   SU3_ECUDA = -3,    /* a CUDA runtime call or kernel failed */
-  SU3_ETIMEOUT = -4, /* a bounded device-side wait gave up (batched sweep) */
+  SU3_ETIMEOUT = -4, /* a bounded device-side wait gave up (batched or persistent sweep) */
   SU3_ESIZE = -5     /* caller buffer size does not match the lattice */
 };
 
@@ -108,7 +108,8 @@ SU3_API int su3_destroy(su3_handle h);
 
 /* Perform nsweeps full checkerboard sweeps (nsweeps >= 0).  Asynchronous on
  * the handle's stream: each sweep replays a captured CUDA graph of eight
- * half-sweep kernels followed by the sweep-counter increment. */
+ * half-sweep kernels, or of one persistent sweep kernel (su3_set_schedule),
+ * followed by the sweep-counter increment. */
 SU3_API int su3_sweep(su3_handle h, int nsweeps);
 
 /* nsweeps sweeps like su3_sweep, with the mean plaquette after each sweep
@@ -193,6 +194,43 @@ SU3_API int su3_set_block_size(su3_handle h, int threads);
  * that measure the plaquette and the repeat-until-accepted heatbath always
  * take the one-thread form.  Not for batch or decomposed handles: SU3_EINVAL. */
 SU3_API int su3_set_lanes(su3_handle h, int lanes);
+
+/* How a sweep is scheduled on the GPU (an implementation choice; the paper's
+ * sweep is the eight half-sweeps mu = 0..3, even then odd sites, Sec. 1):
+ *   SU3_SCHED_PHASES: eight half-sweep kernels, one after the other;
+ *   SU3_SCHED_PERSISTENT: one kernel per sweep whose blocks take tiles of
+ *     the eight half-sweeps in order from a device counter; a tile starts
+ *     once the previous half-sweep has finished the tiles its staples read or
+ *     that read its links (the x3 layers of the pair lattice next to its
+ *     own), so that one half-sweep's last wave overlaps the next one's first.
+ *     Applies to FP32 stores in the site-paired layout (L3 a multiple of 4)
+ *     with one thread per pair, at least 4 layers (L3 >= 8), a layer of
+ *     L0*L1*L2/2 pairs that is a whole number of blocks, and lattices whose
+ *     blocks run in the natural order (an x3 layer of all eight link arrays
+ *     of at most 48 MiB: 32^4, 40^4, 48^4; 64^4 keeps the eight kernels and
+ *     their tiled block order).  Its waits are bounded in time
+ *     (su3_sweep_debug); if one runs out, the sweep stops and the next
+ *     synchronising call returns SU3_ETIMEOUT;
+ *   SU3_SCHED_AUTO (the default): SU3_SCHED_PERSISTENT where it applies and a
+ *     half-sweep is under 8 waves of the GPU (V/4 pairs < 8 x 512 x SMs, e.g.
+ *     32^4; there the tails of eight launches are a tenth of the work), else
+ *     SU3_SCHED_PHASES.
+ * Results do not depend on it, bit for bit.  SU3_EINVAL for an unknown value,
+ * for SU3_SCHED_PERSISTENT where it does not apply, and for batch or
+ * decomposed handles. */
+enum { SU3_SCHED_AUTO = 0, SU3_SCHED_PHASES = 1, SU3_SCHED_PERSISTENT = 2 };
+SU3_API int su3_set_schedule(su3_handle h, int schedule);
+
+/* The schedule the next sweep runs with (SU3_SCHED_PHASES or
+ * SU3_SCHED_PERSISTENT) into *schedule. */
+SU3_API int su3_get_schedule(su3_handle h, int* schedule);
+
+/* Fault-detection hook of the persistent sweep (single lattices), as
+ * su3_batch_debug for batches: wait_limit_s (0 < limit <= 60) bounds each
+ * wait (default 2 s); withhold_item >= 0 makes that work item (in dispatch
+ * order: phase * tiles per phase + position) never report completion, so
+ * that the waits on it run out; -1 disables withholding. */
+SU3_API int su3_sweep_debug(su3_handle h, double wait_limit_s, int withhold_item);
 
 /* ---------------------------------------------------------------------------
  * Domain decomposition emulated on one device (Sec. 2.1, Eq. (MPInp), Tables
@@ -307,7 +345,8 @@ SU3_API int su3_batch_autotune(su3_handle b, int* threads, int* blocks_per_sm, i
 SU3_API int su3_batch_debug(su3_handle b, double wait_limit_s, int withhold_item);
 
 /* Synchronise the handle's stream and report asynchronous failures:
- * SU3_ETIMEOUT if a batched sweep gave up waiting (the status is then cleared),
+ * SU3_ETIMEOUT if a batched or persistent sweep gave up waiting (the status
+ * is then cleared),
  * SU3_ECUDA for a CUDA error, else SU3_OK. */
 SU3_API int su3_status(su3_handle h);
 

@@ -21,13 +21,15 @@ __all__ = [
     "su3_create", "su3_create_ex", "su3_destroy", "su3_sweep", "su3_sweep_measured", "su3_half_sweep", "su3_plaquette",
     "su3_decomp_create", "su3_decomp_plan", "su3_decomp_info",
     "su3_links_get", "su3_links_set", "su3_sweep_count", "su3_set_sweep_count", "su3_set_stats", "su3_stats",
-    "su3_info", "su3_set_block_size", "su3_set_lanes", "su3_bounds_status", "use_library", "su3_set_heatbath", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
+    "su3_info", "su3_set_block_size", "su3_set_lanes", "su3_set_schedule", "su3_get_schedule", "su3_sweep_debug",
+    "SU3_SCHED_AUTO", "SU3_SCHED_PHASES", "SU3_SCHED_PERSISTENT", "su3_bounds_status", "use_library", "su3_set_heatbath", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
     "su3_batch_links_get", "su3_batch_links_set", "su3_batch_size", "su3_batch_config", "su3_batch_get_config",
     "su3_batch_autotune", "su3_batch_debug", "su3_status", "Batch", "su3_plaquette_noalloc", "su3_last_error", "su3_version", "Lattice", "links_shape", "EXPORTS",
 ]
 
 SU3_COLD, SU3_HOT = 0, 1
 SU3_FP64, SU3_FP32_MIXED, SU3_FP32_EFT = 0, 1, 2
+SU3_SCHED_AUTO, SU3_SCHED_PHASES, SU3_SCHED_PERSISTENT = 0, 1, 2
 SU3_OK, SU3_EINVAL, SU3_ENOMEM, SU3_ECUDA, SU3_ETIMEOUT, SU3_ESIZE = 0, -1, -2, -3, -4, -5
 _CODES = {SU3_EINVAL: "SU3_EINVAL", SU3_ENOMEM: "SU3_ENOMEM", SU3_ECUDA: "SU3_ECUDA",
           SU3_ETIMEOUT: "SU3_ETIMEOUT", SU3_ESIZE: "SU3_ESIZE"}
@@ -70,6 +72,9 @@ EXPORTS = [
     ("su3_info", ctypes.c_int, [_h, _pi, _pd, _pu64, _pi]),
     ("su3_set_block_size", ctypes.c_int, [_h, ctypes.c_int]),
     ("su3_set_lanes", ctypes.c_int, [_h, ctypes.c_int]),
+    ("su3_set_schedule", ctypes.c_int, [_h, ctypes.c_int]),
+    ("su3_get_schedule", ctypes.c_int, [_h, _pi]),
+    ("su3_sweep_debug", ctypes.c_int, [_h, ctypes.c_double, ctypes.c_int]),
     ("su3_bounds_status", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint), ctypes.c_int]),
     ("su3_set_heatbath", ctypes.c_int, [_h, ctypes.c_int]),
     ("su3_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _pd, _pu64, ctypes.c_int,
@@ -261,6 +266,21 @@ def su3_set_block_size(h, threads):
 def su3_set_lanes(h, lanes):
     """0: automatic; 1: one thread per link (or link pair); 4: four lanes per link."""
     _check(load_library().su3_set_lanes(h, int(lanes)))
+
+
+def su3_set_schedule(h, schedule):
+    """SU3_SCHED_AUTO, SU3_SCHED_PHASES (eight half-sweep kernels) or SU3_SCHED_PERSISTENT (one kernel)."""
+    _check(load_library().su3_set_schedule(h, int(schedule)))
+
+
+def su3_get_schedule(h):
+    v = ctypes.c_int(0)
+    _check(load_library().su3_get_schedule(h, ctypes.byref(v)))
+    return v.value
+
+
+def su3_sweep_debug(h, wait_limit_s, withhold_item=-1):
+    _check(load_library().su3_sweep_debug(h, float(wait_limit_s), int(withhold_item)))
 
 
 def su3_bounds_status(clear=False):
@@ -507,6 +527,16 @@ class Lattice:
 
     def set_lanes(self, lanes):
         su3_set_lanes(self.handle, lanes)
+
+    def set_schedule(self, schedule):
+        su3_set_schedule(self.handle, schedule)
+
+    @property
+    def schedule(self):
+        return su3_get_schedule(self.handle)
+
+    def debug(self, wait_limit_s, withhold_item=-1):
+        su3_sweep_debug(self.handle, wait_limit_s, withhold_item)
 
     def status(self):
         su3_status(self.handle)

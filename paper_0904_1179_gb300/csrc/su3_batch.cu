@@ -64,24 +64,6 @@ struct BatchArgs {
   int max_tries;      // SU(2) proposals per subgroup (1: one-hit heatbath)
 };
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
-  int v;
-  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 template <typename T, bool EFT, bool REPEAT>
 __device__ __forceinline__ void update_item(int mu, const ReplicaDesc& rd, void* links, int h, int p, uint64_t t,
                                             int max_tries) {

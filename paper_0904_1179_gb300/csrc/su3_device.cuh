@@ -534,6 +534,30 @@ __device__ __forceinline__ bool link_ok(int mu, int p, long long h, long long n)
 #endif
 
 // ---------------------------------------------------------------------------
+// Ordering between thread blocks of one persistent launch (the batched sweep
+// and the persistent site-paired sweep): a block that finished a work item
+// releases its count, a block that depends on it reads the count and
+// acquires, under a time bound.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------------------
 // Link loads and stores.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ size_t link_base(int mu, int p, int Vh, int ncomp) {

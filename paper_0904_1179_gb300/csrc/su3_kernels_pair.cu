@@ -17,8 +17,8 @@ using namespace su3dev;
 
 namespace {
 
-// Block sum of one value per thread into out[blockIdx.x] (fixed order).
-__device__ __forceinline__ void block_partial_pair(double v, double* out) {
+// Block sum of one value per thread into *slot (fixed order).
+__device__ __forceinline__ void block_partial_pair(double v, double* slot) {
   __shared__ double red[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -28,7 +28,7 @@ __device__ __forceinline__ void block_partial_pair(double v, double* out) {
     double w = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    if (threadIdx.x == 0) out[blockIdx.x] = w;
+    if (threadIdx.x == 0) *slot = w;
   }
 }
 
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256, 2) k_half_sweep_f32_pair(HalfSweepArgs ar
       atomicAdd(&args.stats[1], (unsigned long long)prop);
     }
   }
-  if (MEAS) block_partial_pair(m.x + m.y, args.meas);
+  if (MEAS) block_partial_pair(m.x + m.y, args.meas + blockIdx.x);
 }
 
 template <int MU, bool EFT, bool REPEAT, bool MEAS>
@@ -95,6 +95,156 @@ cudaError_t launch_pair_mu(const HalfSweepArgs& a, bool stats, int threads, cuda
                   : launch_pair<MU, EFT, false, (MU > 0)>(a, false, threads, s);
   return repeat ? launch_pair<MU, EFT, true, false>(a, stats, threads, s)
                 : launch_pair<MU, EFT, false, false>(a, stats, threads, s);
+}
+
+// ---------------------------------------------------------------------------
+// The persistent sweep.  Each of the eight half-sweep launches of a sweep
+// leaves its SMs partly idle while its last blocks drain and the next launch
+// ramps up (at 32^4, 3.4 waves of 152 SMs x 4 blocks, the SMs hold no warp
+// for about a tenth of each launch).  Here one launch holds the tiles of all
+// eight half-sweeps, handed out phase by phase from one counter; the tiles of
+// phase q walk the x3 layers of the pair lattice starting one layer further
+// than those of phase q-1, and a tile waits only for the three layers of
+// phase q-1 its staples reach (neighbours x +- nu move x3 by at most one; on
+// the pair lattice a step across the x3 boundary stays in a neighbouring
+// layer).  When a tile of phase q is taken, phase q-1 has handed out all its
+// tiles and those layers were among its first three, so in practice nothing
+// waits, and the next phase fills the SMs while the previous one drains.
+// Completed layers of phase q-1 imply completed layers of every earlier
+// phase around them (each tile waited for its own predecessors before it
+// ran), which also keeps a tile from overwriting links that a still-running
+// earlier tile reads.  The results are those of the per-phase launches bit
+// for bit: the same update of the same links from the same inputs.
+//
+// Ordering: a block reports its tile with one release reduction by thread 0
+// after a block barrier; a waiting block polls the three counts with relaxed
+// loads (lanes 0-2 of warp 0), then thread 0 issues one acquire fence and a
+// block barrier passes it on -- one acquire per tile, because an acquire also
+// drops the SM's L1 lines, which the staging ring (cp.async.ca) relies on.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+template <int MU, bool EFT, bool REPEAT, bool MEAS>
+__device__ __forceinline__ UpdateCount pair_item(const HalfSweepArgs& args, int j, int p, uint64_t t,
+                                                 const UpdateConsts& uc, const PairRing& rg, double2* m) {
+  return update_pair_f32_rolled<MU, true, EFT, REPEAT, MEAS>(args.pgeom, (float4*)args.links, j, p, t, args.key, uc,
+                                                             rg, true, m);
+}
+
+// One block per tile of the sweep (8 x tiles per phase blocks).  A block
+// takes its work item from the counter, not from blockIdx, so items are handed
+// out in order to blocks that are running: every item a block waits for is
+// held by a running block or done, and the lowest item in flight never waits,
+// so the order cannot deadlock however many blocks are resident.  (A loop of
+// items per persistent block would let the compiler keep loop-invariant
+// values of the four update variants in registers across the loop, and the
+// update spills; one item per block keeps the per-phase kernel's registers.)
+// MEAS: the odd-site phases of mu = 1, 2, 3 leave the fused plaquette's block
+// partials (statistics are not counted in them, as in the per-phase launches).
+template <bool EFT, bool REPEAT, bool MEAS>
+__global__ void __launch_bounds__(256, 2)
+    k_sweep_f32_pair(HalfSweepArgs args, PairSweepQueue qa, int tiles_per_layer, int layers, int stats) {
+  extern __shared__ float4 smem[];
+  __shared__ int s_tile, s_phase, s_layer, s_idx;
+  const int tiles_per_phase = tiles_per_layer * layers;
+  unsigned* const done = qa.counters + 1;
+  if (threadIdx.x < 32) {
+    const int lane = (int)threadIdx.x;
+    int idx = 0;
+    if (lane == 0) idx = (int)atomicAdd(qa.counters, 1u);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    int phase = -1, tile = 0, layer = 0;
+    if (idx < 8 * tiles_per_phase) {
+      phase = idx / tiles_per_phase;
+      const int i = idx - phase * tiles_per_phase;
+      const int il = i / tiles_per_layer;
+      layer = (il + phase) % layers;
+      tile = layer * tiles_per_layer + (i - il * tiles_per_layer);
+    }
+    bool ok = phase >= 0 && (lane != 0 || ld_relaxed_s32(qa.status) == 0);
+    if (phase > 0 && lane < 3) {
+      // lane k waits for layer l + k - 1 of the previous phase
+      const int lk = layer + lane - 1 < 0 ? layers - 1 : (layer + lane - 1 == layers ? 0 : layer + lane - 1);
+      const unsigned* cnt = done + (phase - 1) * layers + lk;
+      unsigned long long t0 = 0;
+      while (ok && ld_relaxed_u32(cnt) < (unsigned)tiles_per_layer) {
+        if (t0 == 0) t0 = global_ns();
+        if (ld_relaxed_s32(qa.status) != 0) {
+          ok = false;
+        } else if (global_ns() - t0 > (unsigned long long)qa.wait_ns) {
+          atomicCAS(qa.status, 0, kPairSweepTimeout);
+          ok = false;
+        } else {
+          __nanosleep(64);
+        }
+      }
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) {
+      if (ok && phase > 0) fence_acquire_gpu();
+      s_phase = ok ? phase : -1;
+      s_tile = tile;
+      s_layer = layer;
+      s_idx = idx;
+    }
+  }
+  __syncthreads();
+  const int phase = s_phase, tile = s_tile;
+  if (phase < 0) return;
+  const UpdateConsts uc{args.three_over_beta_f64, args.three_over_beta, args.max_tries};
+  const PairRing rg = pair_ring(smem);
+  const uint64_t t = *args.sweep;
+  const int mu = phase >> 1, p = phase & 1;
+  const int j = tile * (int)blockDim.x + (int)threadIdx.x;  // layers are whole tiles: always a pair of the lattice
+  const bool meas = MEAS && p == 1 && mu > 0;
+  double2 m = make_double2(0.0, 0.0);
+  UpdateCount c;
+  switch (mu) {
+    case 0: c = pair_item<0, EFT, REPEAT, false>(args, j, p, t, uc, rg, &m); break;
+    case 1:
+      c = meas ? pair_item<1, EFT, REPEAT, MEAS>(args, j, p, t, uc, rg, &m)
+               : pair_item<1, EFT, REPEAT, false>(args, j, p, t, uc, rg, &m);
+      break;
+    case 2:
+      c = meas ? pair_item<2, EFT, REPEAT, MEAS>(args, j, p, t, uc, rg, &m)
+               : pair_item<2, EFT, REPEAT, false>(args, j, p, t, uc, rg, &m);
+      break;
+    default:
+      c = meas ? pair_item<3, EFT, REPEAT, MEAS>(args, j, p, t, uc, rg, &m)
+               : pair_item<3, EFT, REPEAT, false>(args, j, p, t, uc, rg, &m);
+      break;
+  }
+  if (stats && !meas) {
+    const int acc = __reduce_add_sync(0xffffffffu, c.accepted);
+    const int prop = __reduce_add_sync(0xffffffffu, c.proposed);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&args.stats[0], (unsigned long long)acc);
+      atomicAdd(&args.stats[1], (unsigned long long)prop);
+    }
+  }
+  if (meas) block_partial_pair(m.x + m.y, args.meas + (size_t)(mu - 1) * tiles_per_phase + tile);
+  __syncthreads();  // every thread's stores are issued before the tile is reported
+  if (threadIdx.x == 0 && s_idx != qa.withhold) red_release_add(done + phase * layers + s_layer, 1u);
+}
+
+template <bool EFT, bool REPEAT, bool MEAS>
+cudaError_t launch_sweep(const HalfSweepArgs& a, const PairSweepQueue& q, int tpl, int layers, bool stats, int threads,
+                         cudaStream_t s) {
+  const size_t smem = (size_t)kPairRingBytesPerThread * threads;
+  const int blocks = 8 * tpl * layers;
+  k_sweep_f32_pair<EFT, REPEAT, MEAS><<<blocks, threads, smem, s>>>(a, q, tpl, layers, stats ? 1 : 0);
+  return cudaGetLastError();
 }
 
 template <typename F>
@@ -117,6 +267,10 @@ cudaError_t prepare_mu() {
 template <bool EFT>
 cudaError_t prepare_all() {
   cudaError_t e;
+  if ((e = set_smem(k_sweep_f32_pair<EFT, false, false>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<EFT, true, false>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<EFT, false, true>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<EFT, true, true>)) != cudaSuccess) return e;
   if ((e = prepare_mu<0, EFT>()) != cudaSuccess) return e;
   if ((e = prepare_mu<1, EFT>()) != cudaSuccess) return e;
   if ((e = prepare_mu<2, EFT>()) != cudaSuccess) return e;
@@ -144,6 +298,33 @@ cudaError_t su3k_launch_half_sweep_pair(const HalfSweepArgs& a, int mu, bool eft
 }
 
 SU3_BOUNDS_STATUS_FN(su3k_bounds_status_pair)
+
+int su3k_pair_sweep_layers(const Geometry& gp, int threads, int* tiles_per_layer) {
+  const long long per_layer = (long long)gp.hL0 * gp.L1 * gp.L2;  // pairs of one parity in one x3 layer
+  if (threads <= 0 || per_layer % threads != 0 || gp.L3 < 4 || su3k_pair_tile2(gp, threads) != 0) return 0;
+  *tiles_per_layer = (int)(per_layer / threads);
+  return gp.L3;
+}
+
+cudaError_t su3k_launch_sweep_pair(const HalfSweepArgs& a, const PairSweepQueue& q, bool eft, bool stats, int threads,
+                                   cudaStream_t s) {
+  int tpl = 0;
+  const int layers = su3k_pair_sweep_layers(a.pgeom, threads, &tpl);
+  if (layers == 0) return cudaErrorInvalidValue;
+  const bool rep = a.max_tries > 1, meas = a.meas != nullptr;
+  if (eft) {
+    if (meas)
+      return rep ? launch_sweep<true, true, true>(a, q, tpl, layers, false, threads, s)
+                 : launch_sweep<true, false, true>(a, q, tpl, layers, false, threads, s);
+    return rep ? launch_sweep<true, true, false>(a, q, tpl, layers, stats, threads, s)
+               : launch_sweep<true, false, false>(a, q, tpl, layers, stats, threads, s);
+  }
+  if (meas)
+    return rep ? launch_sweep<false, true, true>(a, q, tpl, layers, false, threads, s)
+               : launch_sweep<false, false, true>(a, q, tpl, layers, false, threads, s);
+  return rep ? launch_sweep<false, true, false>(a, q, tpl, layers, stats, threads, s)
+             : launch_sweep<false, false, false>(a, q, tpl, layers, stats, threads, s);
+}
 
 int su3k_pair_tile2(const Geometry& gp, int threads) {
   const long long npl = (long long)gp.hL0 * gp.L1;

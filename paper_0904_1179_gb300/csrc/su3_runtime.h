@@ -53,6 +53,14 @@ struct su3_lattice {
   su3dev::Geometry geom{};
   su3dev::Geometry pgeom{};  // pair lattice L0 x L1 x L2 x L3/2 (pairs only)
   su3dev::PhiloxKey key{};
+  // persistent site-paired FP32 sweep (su3k_launch_sweep_pair)
+  int schedule = 0;                  // SU3_SCHED_AUTO, SU3_SCHED_PHASES or SU3_SCHED_PERSISTENT
+  unsigned int* d_pq = nullptr;      // its work counter and per-(phase, layer) completion counts
+  int pq_words = 0;
+  int* d_pstatus = nullptr;          // kPairSweepTimeout after a wait ran out
+  int* h_pstatus = nullptr;          // pinned
+  long long pq_wait_ns = 2000000000LL;
+  int pq_withhold = -1;
   su3_batch* batch = nullptr;    // non-null for a batch of replicas
   su3_decomp* decomp = nullptr;  // non-null for a decomposed lattice (su3_decomp_create)
 };

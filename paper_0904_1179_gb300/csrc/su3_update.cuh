@@ -419,12 +419,14 @@ __device__ __forceinline__ pm3 staple_p(const G& g, const float4* U, const S& st
 // cp.async: 16-byte copies from global to shared memory that do not pass
 // through registers, tracked in commit groups per thread.
 // ---------------------------------------------------------------------------
+// Both forms copy through L1 (.ca): cache operators are performance hints
+// and do not change the memory-consistency behaviour, so links written by
+// other blocks of a persistent launch are seen once the block has acquired
+// their completion counts; and on GB300 the L1-bypassing cp.async.cg made the
+// site-paired sweep 1.7 times slower.
 template <bool CG>
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const float4* gsrc) {
-  if (CG)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gsrc) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gsrc) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>

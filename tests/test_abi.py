@@ -96,6 +96,9 @@ def test_null_handle_calls(lib):
     assert lib.su3_set_sweep_count(None, 0) == su3.SU3_EINVAL
     assert lib.su3_set_block_size(None, 64) == su3.SU3_EINVAL
     assert lib.su3_set_lanes(None, 1) == su3.SU3_EINVAL
+    assert lib.su3_set_schedule(None, su3.SU3_SCHED_PHASES) == su3.SU3_EINVAL
+    assert lib.su3_get_schedule(None, None) == su3.SU3_EINVAL
+    assert lib.su3_sweep_debug(None, 1.0, -1) == su3.SU3_EINVAL
     # the product build has no bounds checks compiled in
     v = ctypes.c_uint(7)
     assert lib.su3_bounds_status(ctypes.byref(v), 0) == su3.SU3_EINVAL

@@ -1,0 +1,176 @@
+"""The persistent sweep (su3_set_schedule: one kernel per sweep) against the
+eight half-sweep kernels and against the oracle.
+
+The persistent kernel applies the per-link update of the half-sweep kernels to
+the same inputs: a tile of a half-sweep starts only after the previous
+half-sweep has finished every tile whose links its staples read or whose
+staples read its links.  Its results are therefore compared bit for bit with
+the eight-kernel schedule (itself pinned to the oracle half-sweep by
+half-sweep in test_gpu_parity.py), and one full sweep also goes to the
+oracle's FP32 reading directly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_0904_1179_gb300 as su3
+from paper_0904_1179_gb300 import build as su3_build
+
+pytestmark = pytest.mark.gpu
+
+BETA = 5.7
+F32_TOL = 5e-5
+PRECS = [su3.SU3_FP32_MIXED, su3.SU3_FP32_EFT]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    su3_build.build()
+    oracle.build()
+
+
+def pair(L, prec, seed, lanes=0, threads=0):
+    """Two identical lattices, the first on the persistent schedule, the second on eight kernels."""
+    a = su3.Lattice(L, BETA, seed, start=su3.SU3_HOT, precision=prec)
+    b = su3.Lattice(L, BETA, seed, start=su3.SU3_HOT, precision=prec)
+    for lat in (a, b):
+        if lanes:
+            lat.set_lanes(lanes)
+        if threads:
+            lat.set_block_size(threads)
+    b.set_schedule(su3.SU3_SCHED_PHASES)
+    assert a.schedule == su3.SU3_SCHED_PERSISTENT
+    assert b.schedule == su3.SU3_SCHED_PHASES
+    return a, b
+
+
+# 8^4 (one lane per pair forced; 4 layers of 8 tiles of 32), 12^3 x 16
+# (8 layers of 27 tiles of 32), 16^4 (8 layers of 32 tiles of 64), 32^4 (the
+# bench lattice: 16 layers of 128 tiles of 128).
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("L,lanes", [((8, 8, 8, 8), 1), ((12, 12, 12, 16), 0), ((16, 16, 16, 16), 0),
+                                     ((32, 32, 32, 32), 0)])
+def test_persistent_sweep_equals_eight_kernels(L, lanes, prec):
+    a, b = pair(L, prec, 21, lanes=lanes)
+    with a, b:
+        for lat in (a, b):
+            lat.set_stats(True)
+            lat.sweep(3)
+            lat.status()
+        assert np.array_equal(a.get_links(), b.get_links())
+        assert a.stats() == b.stats()
+        assert a.sweep_count == b.sweep_count == 3
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_persistent_block_sizes(prec):
+    L = (16, 16, 16, 16)
+    ref = None
+    for threads in (32, 64, 128, 256):
+        a, b = pair(L, prec, 5, threads=threads)
+        with a, b:
+            a.sweep(2)
+            b.sweep(2)
+            Ua = a.get_links()
+            assert np.array_equal(Ua, b.get_links()), threads
+        if ref is None:
+            ref = Ua
+        assert np.array_equal(Ua, ref), threads
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_persistent_measured_sweep_equals_eight_kernels(prec):
+    L = (16, 16, 16, 16)
+    a, b = pair(L, prec, 8)
+    with a, b:
+        pa = a.sweep_measured(4)
+        pb = b.sweep_measured(4)
+        assert np.array_equal(pa, pb)
+        assert np.array_equal(a.get_links(), b.get_links())
+        assert abs(pa[-1] - a.plaquette()) < 2e-6
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_persistent_repeat_until_accepted_equals_eight_kernels(prec):
+    L = (12, 12, 12, 16)
+    a, b = pair(L, prec, 14)
+    with a, b:
+        for lat in (a, b):
+            lat.set_heatbath(8)
+            lat.set_stats(True)
+            lat.sweep(2)
+        assert np.array_equal(a.get_links(), b.get_links())
+        assert a.stats() == b.stats()
+
+
+# One full persistent sweep against the oracle's FP32 reading.  A one-hit
+# decision taken within FP32 rounding of its threshold may flip (see the
+# half-sweep tests); inside a full sweep such a flip also moves the later
+# updates that read the flipped link, a few dozen links at most, so all but a
+# small fraction of links must agree to 5e-5.
+@pytest.mark.parametrize("prec", PRECS)
+def test_persistent_sweep_matches_oracle_reading(prec):
+    L = (8, 8, 8, 8)
+    seed, t = 33, 4
+    U0 = oracle.hot_start(L, 19, f32=True)
+    oracle.sweep(L, BETA, 6, 0, 1, U0, f32=True)
+    O = U0.copy()
+    oracle.sweep(L, BETA, seed, t, 1, O, f32=True)
+    with su3.Lattice(L, BETA, seed, start=su3.SU3_COLD, precision=prec) as lat:
+        lat.set_lanes(1)
+        assert lat.schedule == su3.SU3_SCHED_PERSISTENT
+        lat.set_links(U0)
+        lat.sweep_count = t
+        lat.sweep(1)
+        G = lat.get_links()
+    d = np.abs(G - O).max(axis=(-1, -2, -3))
+    off = int((d > F32_TOL).sum())
+    assert off <= d.size // 100, (off, d.size)
+    print("persistent FP32 sweep (precision %d) vs oracle: worst |dU| %.2e over %d links, %d beyond 5e-5"
+          % (prec, float(np.sort(d.ravel())[d.size - off - 1]), d.size, off))
+
+
+def test_schedule_applies_where_documented():
+    # FP64, a layer that is not a whole number of blocks (10 x 20 x 20 = 4000
+    # pairs, 128 threads), a lattice below 4 layers (L3 = 4), the four-lane
+    # kernel: the eight kernels, and SU3_SCHED_PERSISTENT is refused
+    for L, prec in (((16, 16, 16, 16), su3.SU3_FP64), ((20, 20, 20, 16), su3.SU3_FP32_MIXED),
+                    ((16, 16, 16, 4), su3.SU3_FP32_MIXED), ((8, 8, 8, 8), su3.SU3_FP32_EFT)):
+        with su3.Lattice(L, BETA, 1, precision=prec) as lat:
+            assert lat.schedule == su3.SU3_SCHED_PHASES, L
+            with pytest.raises(su3.Su3Error) as e:
+                lat.set_schedule(su3.SU3_SCHED_PERSISTENT)
+            assert e.value.code == su3.SU3_EINVAL
+    with su3.Lattice((16, 16, 16, 16), BETA, 1, precision=su3.SU3_FP32_MIXED) as lat:
+        with pytest.raises(su3.Su3Error):
+            lat.set_schedule(7)
+        lat.set_schedule(su3.SU3_SCHED_PHASES)
+        assert lat.schedule == su3.SU3_SCHED_PHASES
+        lat.set_schedule(su3.SU3_SCHED_PERSISTENT)
+        assert lat.schedule == su3.SU3_SCHED_PERSISTENT
+        lat.set_schedule(su3.SU3_SCHED_AUTO)
+        assert lat.schedule == su3.SU3_SCHED_PERSISTENT
+        with pytest.raises(su3.Su3Error):
+            lat.debug(0.0)
+    with su3.Batch([(8, 8, 8, 8)], [BETA], [1]) as bt:
+        with pytest.raises(su3.Su3Error):
+            su3.su3_set_schedule(bt.handle, su3.SU3_SCHED_PHASES)
+
+
+# Fault detection without a fault: a work item that never reports completion
+# makes the waits on it run out (0.2 s), the sweep stops, su3_status reports
+# SU3_ETIMEOUT once, and the context keeps working.
+def test_withheld_tile_times_out_without_fault():
+    L = (16, 16, 16, 16)
+    with su3.Lattice(L, BETA, 2, precision=su3.SU3_FP32_MIXED) as lat:
+        assert lat.schedule == su3.SU3_SCHED_PERSISTENT
+        lat.debug(0.2, withhold_item=0)  # the first tile of phase 0 (mu = 0, even sites)
+        lat.sweep(1)
+        with pytest.raises(su3.Su3Error) as e:
+            lat.status()
+        assert e.value.code == su3.SU3_ETIMEOUT
+        lat.status()  # cleared
+        lat.debug(2.0, withhold_item=-1)
+        lat.sweep(2)
+        lat.status()
+        assert 0.0 < lat.plaquette() < 1.0
