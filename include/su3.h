@@ -215,6 +215,8 @@ SU3_API int su3_set_lanes(su3_handle h, int lanes);
  *     half-sweep is under 8 waves of the GPU (V/4 pairs < 8 x 512 x SMs, e.g.
  *     32^4; there the tails of eight launches are a tenth of the work), else
  *     SU3_SCHED_PHASES.
+ * su3_sweep_measured always runs the eight kernels (its measuring update
+ * variants would make the persistent kernel spill).
  * Results do not depend on it, bit for bit.  SU3_EINVAL for an unknown value,
  * for SU3_SCHED_PERSISTENT where it does not apply, and for batch or
  * decomposed handles. */

@@ -179,8 +179,8 @@ bool persistent_applies(const su3_lattice* h) {
 // launch tails it removes cost a tenth of a 32^4 half-sweep (3.4 waves) and
 // little at 48^4 (17 waves), against an acquire fence per tile.  Measured at
 // 32^4: 1.5 % (FP32-mixed) and 0.5 % (FP32-EFT) faster than eight launches.
-bool use_persistent(const su3_lattice* h) {
-  if (h->schedule == SU3_SCHED_PHASES || !persistent_applies(h)) return false;
+bool use_persistent(const su3_lattice* h, bool measured = false) {
+  if (measured || h->schedule == SU3_SCHED_PHASES || !persistent_applies(h)) return false;
   if (h->schedule == SU3_SCHED_PERSISTENT) return true;
   const int sms = sm_count();
   return sms > 0 && (long long)h->pgeom.Vh < 8LL * 512 * sms;
@@ -215,9 +215,8 @@ int ensure_pair_queue(su3_lattice* h) {
 // into the ring slot of this sweep.
 int enqueue_sweep_body(su3_lattice* h, bool measured) {
   const int blocks = su3k_half_sweep_blocks(half_sweep_args(h, 1), h->precision, h->threads);
-  if (use_persistent(h)) {
-    HalfSweepArgs a = half_sweep_args(h, 0);
-    if (measured) a.meas = h->d_meas_parts;
+  if (use_persistent(h, measured)) {
+    const HalfSweepArgs a = half_sweep_args(h, 0);
     const PairSweepQueue q{h->d_pq, h->d_pstatus, h->pq_wait_ns, h->pq_withhold};
     SU3_CUDA(cudaMemsetAsync(h->d_pq, 0, (size_t)h->pq_words * sizeof(unsigned int), h->stream),
              "sweep counters reset");
@@ -243,7 +242,7 @@ int enqueue_sweep_body(su3_lattice* h, bool measured) {
 int ensure_graph(su3_lattice* h, bool measured = false) {
   cudaGraphExec_t& exec = measured ? h->graph_meas : h->graph[h->stats_on ? 1 : 0];
   if (exec) return SU3_OK;
-  if (use_persistent(h)) {
+  if (use_persistent(h, measured)) {
     const int rc = ensure_pair_queue(h);
     if (rc != SU3_OK) return rc;
   }

@@ -91,8 +91,8 @@ constexpr int kPairSweepTimeout = 1;
 int su3k_pair_sweep_layers(const su3dev::Geometry& gp, int threads, int* tiles_per_layer);
 // Counter words for a pair lattice of `layers` layers.
 inline int su3k_pair_sweep_words(int layers) { return 1 + 8 * layers; }
-// One sweep.  a.parity is unused; a.meas (non-null) takes the fused
-// plaquette's partials as the per-phase launches leave them.
+// One sweep.  a.parity is unused; a.meas must be null (sweeps that measure
+// the plaquette run the eight half-sweep kernels).
 cudaError_t su3k_launch_sweep_pair(const HalfSweepArgs& a, const PairSweepQueue& q, bool eft, bool stats, int threads,
                                    cudaStream_t s);
 

@@ -135,11 +135,10 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 
 __device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
-template <int MU, bool EFT, bool REPEAT, bool MEAS>
+template <int MU, bool EFT, bool REPEAT>
 __device__ __forceinline__ UpdateCount pair_item(const HalfSweepArgs& args, int j, int p, uint64_t t,
-                                                 const UpdateConsts& uc, const PairRing& rg, double2* m) {
-  return update_pair_f32_rolled<MU, true, EFT, REPEAT, MEAS>(args.pgeom, (float4*)args.links, j, p, t, args.key, uc,
-                                                             rg, true, m);
+                                                 const UpdateConsts& uc, const PairRing& rg) {
+  return update_pair_f32_rolled<MU, true, EFT, REPEAT>(args.pgeom, (float4*)args.links, j, p, t, args.key, uc, rg);
 }
 
 // One block per tile of the sweep (8 x tiles per phase blocks).  A block
@@ -150,9 +149,10 @@ __device__ __forceinline__ UpdateCount pair_item(const HalfSweepArgs& args, int 
 // items per persistent block would let the compiler keep loop-invariant
 // values of the four update variants in registers across the loop, and the
 // update spills; one item per block keeps the per-phase kernel's registers.)
-// MEAS: the odd-site phases of mu = 1, 2, 3 leave the fused plaquette's block
-// partials (statistics are not counted in them, as in the per-phase launches).
-template <bool EFT, bool REPEAT, bool MEAS>
+// Sweeps that measure the plaquette run the eight half-sweep kernels: the
+// measuring update variants added to this kernel's four made it spill and
+// ran 6 % slower.
+template <bool EFT, bool REPEAT>
 __global__ void __launch_bounds__(256, 2)
     k_sweep_f32_pair(HalfSweepArgs args, PairSweepQueue qa, int tiles_per_layer, int layers, int stats) {
   extern __shared__ float4 smem[];
@@ -207,25 +207,14 @@ __global__ void __launch_bounds__(256, 2)
   const uint64_t t = *args.sweep;
   const int mu = phase >> 1, p = phase & 1;
   const int j = tile * (int)blockDim.x + (int)threadIdx.x;  // layers are whole tiles: always a pair of the lattice
-  const bool meas = MEAS && p == 1 && mu > 0;
-  double2 m = make_double2(0.0, 0.0);
   UpdateCount c;
   switch (mu) {
-    case 0: c = pair_item<0, EFT, REPEAT, false>(args, j, p, t, uc, rg, &m); break;
-    case 1:
-      c = meas ? pair_item<1, EFT, REPEAT, MEAS>(args, j, p, t, uc, rg, &m)
-               : pair_item<1, EFT, REPEAT, false>(args, j, p, t, uc, rg, &m);
-      break;
-    case 2:
-      c = meas ? pair_item<2, EFT, REPEAT, MEAS>(args, j, p, t, uc, rg, &m)
-               : pair_item<2, EFT, REPEAT, false>(args, j, p, t, uc, rg, &m);
-      break;
-    default:
-      c = meas ? pair_item<3, EFT, REPEAT, MEAS>(args, j, p, t, uc, rg, &m)
-               : pair_item<3, EFT, REPEAT, false>(args, j, p, t, uc, rg, &m);
-      break;
+    case 0: c = pair_item<0, EFT, REPEAT>(args, j, p, t, uc, rg); break;
+    case 1: c = pair_item<1, EFT, REPEAT>(args, j, p, t, uc, rg); break;
+    case 2: c = pair_item<2, EFT, REPEAT>(args, j, p, t, uc, rg); break;
+    default: c = pair_item<3, EFT, REPEAT>(args, j, p, t, uc, rg); break;
   }
-  if (stats && !meas) {
+  if (stats) {
     const int acc = __reduce_add_sync(0xffffffffu, c.accepted);
     const int prop = __reduce_add_sync(0xffffffffu, c.proposed);
     if ((threadIdx.x & 31) == 0) {
@@ -233,17 +222,16 @@ __global__ void __launch_bounds__(256, 2)
       atomicAdd(&args.stats[1], (unsigned long long)prop);
     }
   }
-  if (meas) block_partial_pair(m.x + m.y, args.meas + (size_t)(mu - 1) * tiles_per_phase + tile);
   __syncthreads();  // every thread's stores are issued before the tile is reported
   if (threadIdx.x == 0 && s_idx != qa.withhold) red_release_add(done + phase * layers + s_layer, 1u);
 }
 
-template <bool EFT, bool REPEAT, bool MEAS>
+template <bool EFT, bool REPEAT>
 cudaError_t launch_sweep(const HalfSweepArgs& a, const PairSweepQueue& q, int tpl, int layers, bool stats, int threads,
                          cudaStream_t s) {
   const size_t smem = (size_t)kPairRingBytesPerThread * threads;
   const int blocks = 8 * tpl * layers;
-  k_sweep_f32_pair<EFT, REPEAT, MEAS><<<blocks, threads, smem, s>>>(a, q, tpl, layers, stats ? 1 : 0);
+  k_sweep_f32_pair<EFT, REPEAT><<<blocks, threads, smem, s>>>(a, q, tpl, layers, stats ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -267,10 +255,8 @@ cudaError_t prepare_mu() {
 template <bool EFT>
 cudaError_t prepare_all() {
   cudaError_t e;
-  if ((e = set_smem(k_sweep_f32_pair<EFT, false, false>)) != cudaSuccess) return e;
-  if ((e = set_smem(k_sweep_f32_pair<EFT, true, false>)) != cudaSuccess) return e;
-  if ((e = set_smem(k_sweep_f32_pair<EFT, false, true>)) != cudaSuccess) return e;
-  if ((e = set_smem(k_sweep_f32_pair<EFT, true, true>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<EFT, false>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<EFT, true>)) != cudaSuccess) return e;
   if ((e = prepare_mu<0, EFT>()) != cudaSuccess) return e;
   if ((e = prepare_mu<1, EFT>()) != cudaSuccess) return e;
   if ((e = prepare_mu<2, EFT>()) != cudaSuccess) return e;
@@ -311,19 +297,13 @@ cudaError_t su3k_launch_sweep_pair(const HalfSweepArgs& a, const PairSweepQueue&
   int tpl = 0;
   const int layers = su3k_pair_sweep_layers(a.pgeom, threads, &tpl);
   if (layers == 0) return cudaErrorInvalidValue;
-  const bool rep = a.max_tries > 1, meas = a.meas != nullptr;
-  if (eft) {
-    if (meas)
-      return rep ? launch_sweep<true, true, true>(a, q, tpl, layers, false, threads, s)
-                 : launch_sweep<true, false, true>(a, q, tpl, layers, false, threads, s);
-    return rep ? launch_sweep<true, true, false>(a, q, tpl, layers, stats, threads, s)
-               : launch_sweep<true, false, false>(a, q, tpl, layers, stats, threads, s);
-  }
-  if (meas)
-    return rep ? launch_sweep<false, true, true>(a, q, tpl, layers, false, threads, s)
-               : launch_sweep<false, false, true>(a, q, tpl, layers, false, threads, s);
-  return rep ? launch_sweep<false, true, false>(a, q, tpl, layers, stats, threads, s)
-             : launch_sweep<false, false, false>(a, q, tpl, layers, stats, threads, s);
+  if (a.meas) return cudaErrorInvalidValue;  // measuring sweeps run the eight half-sweep kernels
+  const bool rep = a.max_tries > 1;
+  if (eft)
+    return rep ? launch_sweep<true, true>(a, q, tpl, layers, stats, threads, s)
+               : launch_sweep<true, false>(a, q, tpl, layers, stats, threads, s);
+  return rep ? launch_sweep<false, true>(a, q, tpl, layers, stats, threads, s)
+             : launch_sweep<false, false>(a, q, tpl, layers, stats, threads, s);
 }
 
 int su3k_pair_tile2(const Geometry& gp, int threads) {
