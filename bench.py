@@ -77,31 +77,67 @@ def peaks():
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel of each line, from one ncu capture: the bytes, the command
-# that captured them, and the SHA-256 of the kernel sources (every
-# paper_0904_1179_gb300/csrc/*.cu and *.cuh, sorted by name) at capture time.
-# A line reports the figure only while the sources still hash the same;
-# otherwise its traffic is null and the line says why.
-_SRC_A04220F = "449a92e7f01809806104f79742e0e6963fa6c958ec01f177500c8d013e2905bb"
+# that captured them (after the same command ran without ncu), and the SHA-256
+# of the kernel code at capture time (kernel_sources_sha: every
+# paper_0904_1179_gb300/csrc/*.cu and *.cuh, sorted by name, comments
+# stripped).  A line reports the figure only while the code still hashes the
+# same; otherwise its traffic is null and the line says why.
+_SRC_A321BBC = "57021bc74ec7564d1f2e32bd76054603dd0aa537c4b5fe0cd874dba248473284"
+_NCU_METRICS = "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none"
 NCU_TRAFFIC = {
-    "fp32_mixed": {"bytes": 208.123392e6 + 16.535552e6, "sources_sha256": _SRC_A04220F,
-                   "capture": "ncu --set full -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile fp32_mixed"},
-    "fp32_eft": {"bytes": 208.156416e6 + 16.818176e6, "sources_sha256": _SRC_A04220F,
-                 "capture": "ncu --set full -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile fp32_eft"},
-    "batched": {"bytes": 3.033858e9 + 0.418697216e9, "sources_sha256": _SRC_A04220F,
-                "capture": "ncu -k regex:k_batch_sweep -s 1 -c 1 python bench.py --profile batched"},
-    "batched_eft": {"bytes": 3.033844e9 + 0.419232512e9, "sources_sha256": _SRC_A04220F,
-                    "capture": "ncu -k regex:k_batch_sweep -s 1 -c 1 python bench.py --profile batched_eft"},
+    "fp32_mixed": {"bytes": 1666981632 + 190839040, "sources_sha256": _SRC_A321BBC,
+                   "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 1 -c 1 python bench.py --profile fp32_mixed"},
+    "fp32_eft": {"bytes": 1669437184 + 191675648, "sources_sha256": _SRC_A321BBC,
+                 "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 1 -c 1 python bench.py --profile fp32_eft"},
+    "fp32_mixed_phases": {"bytes": 207923456 + 15627008, "sources_sha256": _SRC_A321BBC,
+                          "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile "
+                                                    "fp32_mixed_phases"},
+    "fp32_eft_phases": {"bytes": 208064000 + 16438016, "sources_sha256": _SRC_A321BBC,
+                        "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile "
+                                                  "fp32_eft_phases"},
+    "fp64": {"bytes": 623867648 + 64909568, "sources_sha256": _SRC_A321BBC,
+             "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile fp64"},
+    "batched": {"bytes": 3034118144 + 418453248, "sources_sha256": _SRC_A321BBC,
+                "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 1 -c 1 python bench.py --profile batched"},
+    "batched_eft": {"bytes": 3033794560 + 418881024, "sources_sha256": _SRC_A321BBC,
+                    "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 1 -c 1 python bench.py --profile batched_eft"},
 }
 
 
+def _code_only(text):
+    """C/C++ source without comments and with whitespace runs collapsed, so
+    that the provenance hash below changes with the code, not with its prose."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_sources_sha():
+    """sha256 of the code (comments stripped) of csrc/*.cu and *.cuh, sorted by name."""
     import hashlib
     d = os.path.join(ROOT, "paper_0904_1179_gb300", "csrc")
     h = hashlib.sha256()
     for fn in sorted(os.listdir(d)):
         if fn.endswith((".cu", ".cuh")):
-            with open(os.path.join(d, fn), "rb") as f:
-                h.update(fn.encode() + b"\0" + f.read())
+            with open(os.path.join(d, fn), encoding="utf-8") as f:
+                h.update(fn.encode() + b"\0" + _code_only(f.read()).encode())
     return h.hexdigest()
 
 

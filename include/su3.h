@@ -354,19 +354,25 @@ SU3_API int su3_status(su3_handle h);
 
 /* Mean plaquette of a link store held by the caller in device memory,
  * computed without allocating any memory.  The paper has no counterpart: this
- * entry point exists for callers that cannot call cudaMalloc -- code that runs
- * while its stream is being captured into a CUDA graph (allocation cannot be
- * captured), runtimes that hand out device memory only from their own pool or
- * arena, and plugins or callbacks that must not touch the process allocator.
- * It performs no cudaMalloc, cudaFree or other allocating call.
+ * entry point exists for callers that cannot call cudaMalloc -- runtimes that
+ * hand out device memory only from their own pool or arena, and plugins or
+ * callbacks that must not touch the process allocator.  It performs no
+ * cudaMalloc, cudaFree or other allocating call.
  *   links: device pointer to a configuration in the library's device layout,
  *     half-lattice structure of arrays indexed by h = s/2 (s the canonical
  *     site index; each parity holds one site of every pair 2h, 2h+1):
  *       SU3_FP64:       double2 [4 mu][2 parity][9 entries row*3+col][V/2]
- *       SU3_FP32_MIXED, SU3_FP32_EFT (the same store):
- *                       float4  [4 mu][2 parity][3 columns k][V/2], rows 0
+ *       SU3_FP32_MIXED, SU3_FP32_EFT (the same store), L3 not a multiple
+ *       of 4:           float4  [4 mu][2 parity][3 columns k][V/2], rows 0
  *                       and 1 only: column k = (re u0k, re u1k, im u0k,
- *                       im u1k); row 2 is conj(row0 x row1).
+ *                       im u1k); row 2 is conj(row0 x row1);
+ *       SU3_FP32_MIXED, SU3_FP32_EFT, L3 a multiple of 4 (site pairs x and
+ *       x + (L3/2) e3 side by side):
+ *                       float4  [4 mu][2 parity][6 entries e = 3r+k][V/4],
+ *                       rows r = 0, 1: entry e of pair j = (re u_rk(x),
+ *                       re u_rk(x'), im u_rk(x), im u_rk(x')), where j is
+ *                       the half index of x on the L0 x L1 x L2 x L3/2 pair
+ *                       lattice (x3 < L3/2) and x' = x + (L3/2) e3.
  *   out: device pointer to one double that receives the mean plaquette, as
  *     defined for su3_plaquette, when the work enqueued on cuda_stream runs.
  *   cuda_stream: the cudaStream_t to enqueue on (NULL = the default stream).
@@ -378,11 +384,10 @@ SU3_API int su3_status(su3_handle h);
  * calls share the one array: calls that overlap on the GPU (on different
  * streams, or from several host threads) race and return wrong results.  The
  * first call on each device looks up the array's device address with that
- * device current (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture.  The cache remembers the CUDA context it was
- * filled in: after the context is destroyed and created again
- * (cudaDeviceReset) the next call looks the address up again, so make that
- * call, too, outside a capture.  Errors: SU3_EINVAL (NULL pointer, odd or
+ * device current (cudaGetSymbolAddress) and caches it.  The cache remembers
+ * the CUDA context it was filled in: after the context is destroyed and
+ * created again (cudaDeviceReset) the next call looks the address up again.
+ * Errors: SU3_EINVAL (NULL pointer, odd or
  * < 2 extent, bad precision), SU3_ESIZE (too many sites), SU3_ECUDA (lookup
  * or launch failed); su3_last_error() describes them. */
 SU3_API int su3_plaquette_noalloc(const void* links, int L0, int L1, int L2, int L3, int precision, double* out,

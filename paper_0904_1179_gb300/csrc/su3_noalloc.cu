@@ -2,12 +2,11 @@
 // that the caller holds in device memory, computed without allocating
 // anything.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA stream is
-// being captured into a graph (allocation is not a capturable operation),
-// runtimes that hand out device memory only through their own pool or arena,
-// and callbacks or plugins that must not touch the process's allocator.  For
-// them the reduction's scratch -- one partial sum per thread block -- lives in
-// a fixed file-scope device array instead of a handle's cudaMalloc'd buffer.
+// Some callers cannot call cudaMalloc: runtimes that hand out device memory
+// only through their own pool or arena, and callbacks or plugins that must
+// not touch the process's allocator.  For them the reduction's scratch -- one
+// partial sum per thread block -- lives in a fixed file-scope device array
+// instead of a handle's cudaMalloc'd buffer.
 // Every GPU that loads libsu3 holds this array (512 KiB) until the process
 // exits.  The kernels are the library's plaquette kernels (su3_kernels.cu),
 // launched with that array as their partial-sum buffer.
