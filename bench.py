@@ -78,28 +78,31 @@ def peaks():
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel of each line, from one ncu capture: the bytes, the command
 # that captured them (after the same command ran without ncu), and the SHA-256
-# of the kernel code at capture time (kernel_sources_sha: every
-# paper_0904_1179_gb300/csrc/*.cu and *.cuh, sorted by name, comments
-# stripped).  A line reports the figure only while the code still hashes the
+# of the kernel's code at capture time (kernel_sources_sha: the translation
+# units that define and launch the kernel and every csrc/*.cuh, comments
+# stripped).  A line reports the figure only while that code still hashes the
 # same; otherwise its traffic is null and the line says why.
-_SRC_A321BBC = "57021bc74ec7564d1f2e32bd76054603dd0aa537c4b5fe0cd874dba248473284"
+_U_F64, _U_F32, _U_BATCH = ("su3_kernels.cu",), ("su3_kernels.cu", "su3_kernels_pair.cu"), ("su3_batch.cu",)
+_SHA_F64 = "674790eeb6cadbfad662bf71b033a2b476af3ed90f850a86e0fbfcb85f355a9a"
+_SHA_F32 = "1ea1f36ad62a866a95f22736c29d02d4949689dcda83c6ba9a787b7877b22c98"
+_SHA_BATCH = "e8531b9371664a0326511a55b5a8be802e48c1790f43b10cd13e52330f885ce0"
 _NCU_METRICS = "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none"
 NCU_TRAFFIC = {
-    "fp32_mixed": {"bytes": 1666981632 + 190839040, "sources_sha256": _SRC_A321BBC,
+    "fp32_mixed": {"bytes": 1666981632 + 190839040, "units": _U_F32, "sources_sha256": _SHA_F32,
                    "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 1 -c 1 python bench.py --profile fp32_mixed"},
-    "fp32_eft": {"bytes": 1669437184 + 191675648, "sources_sha256": _SRC_A321BBC,
+    "fp32_eft": {"bytes": 1669437184 + 191675648, "units": _U_F32, "sources_sha256": _SHA_F32,
                  "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 1 -c 1 python bench.py --profile fp32_eft"},
-    "fp32_mixed_phases": {"bytes": 207923456 + 15627008, "sources_sha256": _SRC_A321BBC,
+    "fp32_mixed_phases": {"bytes": 207923456 + 15627008, "units": _U_F32, "sources_sha256": _SHA_F32,
                           "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile "
                                                     "fp32_mixed_phases"},
-    "fp32_eft_phases": {"bytes": 208064000 + 16438016, "sources_sha256": _SRC_A321BBC,
+    "fp32_eft_phases": {"bytes": 208064000 + 16438016, "units": _U_F32, "sources_sha256": _SHA_F32,
                         "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile "
                                                   "fp32_eft_phases"},
-    "fp64": {"bytes": 623867648 + 64909568, "sources_sha256": _SRC_A321BBC,
+    "fp64": {"bytes": 623867648 + 64909568, "units": _U_F64, "sources_sha256": _SHA_F64,
              "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile fp64"},
-    "batched": {"bytes": 3034118144 + 418453248, "sources_sha256": _SRC_A321BBC,
+    "batched": {"bytes": 3034118144 + 418453248, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
                 "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 1 -c 1 python bench.py --profile batched"},
-    "batched_eft": {"bytes": 3033794560 + 418881024, "sources_sha256": _SRC_A321BBC,
+    "batched_eft": {"bytes": 3033794560 + 418881024, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
                     "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 1 -c 1 python bench.py --profile batched_eft"},
 }
 
@@ -129,13 +132,14 @@ def _code_only(text):
     return " ".join("".join(out).split())
 
 
-def kernel_sources_sha():
-    """sha256 of the code (comments stripped) of csrc/*.cu and *.cuh, sorted by name."""
+def kernel_sources_sha(units=None):
+    """sha256 of the code (comments stripped) of the translation units `units`
+    (csrc/*.cu names; None = all) and of every csrc/*.cuh, sorted by name."""
     import hashlib
     d = os.path.join(ROOT, "paper_0904_1179_gb300", "csrc")
     h = hashlib.sha256()
     for fn in sorted(os.listdir(d)):
-        if fn.endswith((".cu", ".cuh")):
+        if fn.endswith(".cuh") or (fn.endswith(".cu") and (units is None or fn in units)):
             with open(os.path.join(d, fn), encoding="utf-8") as f:
                 h.update(fn.encode() + b"\0" + _code_only(f.read()).encode())
     return h.hexdigest()
@@ -146,9 +150,10 @@ def traffic_of(variant):
     rec = NCU_TRAFFIC.get(variant)
     if rec is None:
         return None, "no ncu capture recorded for this kernel"
-    if rec["sources_sha256"] != kernel_sources_sha():
+    if rec["sources_sha256"] != kernel_sources_sha(rec["units"]):
         return None, "kernel sources changed since the ncu capture (%s)" % rec["capture"]
-    return rec["bytes"], "ncu capture: %s; kernel sources sha256 %s" % (rec["capture"], rec["sources_sha256"][:16])
+    return rec["bytes"], "ncu capture: %s; code sha256 of %s and csrc/*.cuh: %s" % (
+        rec["capture"], ", ".join(rec["units"]), rec["sources_sha256"][:16])
 
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA per
 # clock (1/64 of the 128 FP32 lanes) x 2 flop x 2.070 GHz = 1.2586 TFLOP/s

@@ -331,7 +331,8 @@ SU3_API int su3_batch_config(su3_handle b, int threads, int blocks_per_sm, int w
 SU3_API int su3_batch_get_config(su3_handle b, int* threads, int* blocks_per_sm, int* window);
 
 /* Time every candidate configuration (threads 64/128/256, blocks per SM up to
- * the occupancy limit, windows of n, n/2, n/4, ... replicas) on this batch,
+ * the occupancy limit, windows of n, n/2, n/4, ... replicas) on this batch
+ * -- one untimed sweep, then the median of three timed sweeps each --,
  * keep the fastest, and remember it for batches of the same replica extents
  * and precision on the same GPU model in this process.  The links and the
  * sweep index are saved before and restored after tuning, so the chain is
