@@ -85,7 +85,7 @@ def peaks():
 _U_F64, _U_F32, _U_BATCH = ("su3_kernels.cu",), ("su3_kernels.cu", "su3_kernels_pair.cu"), ("su3_batch.cu",)
 _SHA_F64 = "674790eeb6cadbfad662bf71b033a2b476af3ed90f850a86e0fbfcb85f355a9a"
 _SHA_F32 = "1ea1f36ad62a866a95f22736c29d02d4949689dcda83c6ba9a787b7877b22c98"
-_SHA_BATCH = "e8531b9371664a0326511a55b5a8be802e48c1790f43b10cd13e52330f885ce0"
+_SHA_BATCH = "ca07367f370764aebcf51a906f9f42f6a0f3127a5b5ccebeed8f605bbecf5ac4"
 _NCU_METRICS = "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none"
 NCU_TRAFFIC = {
     "fp32_mixed": {"bytes": 1666981632 + 190839040, "units": _U_F32, "sources_sha256": _SHA_F32,
@@ -100,9 +100,9 @@ NCU_TRAFFIC = {
                                                   "fp32_eft_phases"},
     "fp64": {"bytes": 623867648 + 64909568, "units": _U_F64, "sources_sha256": _SHA_F64,
              "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile fp64"},
-    "batched": {"bytes": 3034118144 + 418453248, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
+    "batched": {"bytes": 3034027776 + 418116352, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
                 "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 1 -c 1 python bench.py --profile batched"},
-    "batched_eft": {"bytes": 3033794560 + 418881024, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
+    "batched_eft": {"bytes": 3033860352 + 418545408, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
                     "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 1 -c 1 python bench.py --profile batched_eft"},
 }
 
