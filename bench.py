@@ -88,9 +88,9 @@ _SHA_F32 = "1ea1f36ad62a866a95f22736c29d02d4949689dcda83c6ba9a787b7877b22c98"
 _SHA_BATCH = "ca07367f370764aebcf51a906f9f42f6a0f3127a5b5ccebeed8f605bbecf5ac4"
 _NCU_METRICS = "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none"
 NCU_TRAFFIC = {
-    "fp32_mixed": {"bytes": 1666981632 + 190839040, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_mixed_onelaunch": {"bytes": 1666981632 + 190839040, "units": _U_F32, "sources_sha256": _SHA_F32,
                    "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 1 -c 1 python bench.py --profile fp32_mixed"},
-    "fp32_eft": {"bytes": 1669437184 + 191675648, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_eft_onelaunch": {"bytes": 1669437184 + 191675648, "units": _U_F32, "sources_sha256": _SHA_F32,
                  "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 1 -c 1 python bench.py --profile fp32_eft"},
     "fp32_mixed_phases": {"bytes": 207923456 + 15627008, "units": _U_F32, "sources_sha256": _SHA_F32,
                           "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile "
@@ -470,10 +470,10 @@ def run_reference(args):
 
 def variant_fp32(su3, stream, steps, warmup, world, hbm_peak, peak_kind, precision=None, schedule=None):
     """The FP32 sweep of the 32^4 lattice.  schedule: None = the library's
-    default (one persistent kernel per sweep at 32^4), or su3.SU3_SCHED_PHASES
-    for the eight half-sweep kernels.  The events bracket each sweep's graph
-    (counter reset, sweep kernel(s), sweep-counter increment), so the kernel
-    time below slightly overstates the kernels' own."""
+    default (at 32^4 one persistent kernel per direction mu, four per sweep),
+    or su3.SU3_SCHED_PHASES for the eight half-sweep kernels.  The events
+    bracket each sweep's graph (counter reset, sweep kernels, sweep-counter
+    increment), so the kernel time below slightly overstates the kernels' own."""
     import numpy as np
     if precision is None:
         precision = su3.SU3_FP32_MIXED
@@ -482,23 +482,27 @@ def variant_fp32(su3, stream, steps, warmup, world, hbm_peak, peak_kind, precisi
                      stream=stream.cuda_stream) as lat:
         if schedule is not None:
             lat.set_schedule(schedule)
-        persistent = lat.schedule == su3.SU3_SCHED_PERSISTENT
+        sched = lat.schedule
         total_ms, sweep_ms, _ = time_sweeps(lat, stream, steps, warmup, SWEEPS_PER_STEP, world)
         plaq = lat.plaquette()
     V = int(np.prod(DIMS))
     ups = 4 * V * SWEEPS_PER_STEP * steps / (total_ms * 1e-3)
-    launches = 1 if persistent else 8  # sweep kernel launches per sweep
+    launches = {su3.SU3_SCHED_PERSISTENT: 1, su3.SU3_SCHED_PER_DIRECTION: 4}.get(sched, 8)  # per sweep
     kernel_ms = statistics.mean(sweep_ms) / launches
     bytes_per_launch = BYTES_PER_UPDATE["fp32_mixed"] * (V // 2) * (8 // launches)
     achieved = bytes_per_launch / (kernel_ms * 1e-3) / 1e9
     gs = ("Gram-Schmidt coefficients as compensated FP32 sums (error-free transformations, ~2^-47)" if eft
           else "FP64 Gram-Schmidt coefficients")
-    traffic, provenance = traffic_of(("fp32_eft" if eft else "fp32_mixed") + ("" if persistent else "_phases"))
-    kernel = ("k_sweep_f32_pair (site-paired FP32 sweep: the eight half-sweeps in one launch)" if persistent
-              else "k_half_sweep_f32_pair (site-paired FP32 half-sweep, eight launches per sweep)")
+    traffic, provenance = traffic_of(("fp32_eft" if eft else "fp32_mixed") +
+                                     {1: "_onelaunch", 4: "", 8: "_phases"}[launches])
+    kernel = {1: "k_sweep_f32_pair<-1> (site-paired FP32 sweep: the eight half-sweeps in one launch)",
+              4: "k_sweep_f32_pair<mu> (site-paired FP32 sweep of one direction: two half-sweeps per launch, "
+                 "four launches per sweep)",
+              8: "k_half_sweep_f32_pair (site-paired FP32 half-sweep, eight launches per sweep)"}[launches]
     return {"workload": "32^4 beta=5.7 hot start seed 7, FP32-mixed (12-real FP32 links, FP32 staple and "
-                        "heatbath, %s), 2 sweeps/step, %s" % (gs, "one persistent kernel per sweep" if persistent
-                                                             else "eight half-sweep kernels per sweep"),
+                        "heatbath, %s), 2 sweeps/step, %s" % (gs, {1: "one persistent kernel per sweep",
+                                                                  4: "one persistent kernel per direction",
+                                                                  8: "eight half-sweep kernels per sweep"}[launches]),
             "value": ups, "unit": UNIT, "ms_per_step": total_ms / steps,
             "dtype": "f32 (compensated-f32 reunitarisation)" if eft else "f32 (f64 reunitarisation)",
             "plaquette_after": plaq,
@@ -565,6 +569,8 @@ def run_profile_case(case):
     schedule = None
     if case.endswith("_phases"):  # the eight half-sweep kernels instead of the persistent sweep
         schedule, case = su3.SU3_SCHED_PHASES, case[:-7]
+    elif case.endswith("_onelaunch"):  # the whole sweep in one persistent launch
+        schedule, case = su3.SU3_SCHED_PERSISTENT, case[:-10]
     if case.endswith("_64"):
         dims, beta, case = (64, 64, 64, 64), 6.0, case[:-3]
     elif case.endswith("_64s"):  # 64^3 x 16: the x3 lines of 64^4 in 805 MB (FP32)
@@ -945,7 +951,7 @@ def main():
     ap.add_argument("--large-sweeps", type=int, default=100)
     ap.add_argument("--profile", choices=["fp64", "fp32_mixed", "fp32_eft", "batched", "batched_eft", "fp64_64", "fp32_mixed_64", "decomp16",
                              "fp64_8", "fp32_mixed_64s", "fp32_eft_64s", "fp32_mixed_48", "fp32_eft_48",
-                             "fp32_mixed_phases", "fp32_eft_phases"],
+                             "fp32_mixed_phases", "fp32_eft_phases", "fp32_mixed_onelaunch", "fp32_eft_onelaunch"],
                     help="small case for ncu: create the 32^4 lattice (or the 96-replica batch) and run 3 graphed "
                          "sweeps, nothing else")
     args = ap.parse_args()

@@ -211,20 +211,25 @@ SU3_API int su3_set_lanes(su3_handle h, int lanes);
  *     their tiled block order).  Its waits are bounded in time
  *     (su3_sweep_debug); if one runs out, the sweep stops and the next
  *     synchronising call returns SU3_ETIMEOUT;
- *   SU3_SCHED_AUTO (the default): SU3_SCHED_PERSISTENT where it applies and a
- *     half-sweep is under 8 waves of the GPU (V/4 pairs < 8 x 512 x SMs, e.g.
- *     32^4; there the tails of eight launches are a tenth of the work), else
- *     SU3_SCHED_PHASES.
+ *   SU3_SCHED_PER_DIRECTION: the same tiles in four persistent launches, one
+ *     per direction mu with its even and odd half-sweeps (each launch runs the
+ *     update code of one direction; tails remain between directions);
+ *   SU3_SCHED_AUTO (the default): SU3_SCHED_PER_DIRECTION where the
+ *     persistent forms apply and a half-sweep is under 8 waves of the GPU
+ *     (V/4 pairs < 8 x 512 x SMs, e.g. 32^4; there the tails of eight
+ *     launches are a tenth of the work), else SU3_SCHED_PHASES.  Measured at
+ *     32^4 against eight launches: per direction +2.4 % (FP32-mixed) and
+ *     +0.3 % (FP32-EFT), one launch +1.2 % and +0.1 %.
  * su3_sweep_measured always runs the eight kernels (its measuring update
  * variants would make the persistent kernel spill).
  * Results do not depend on it, bit for bit.  SU3_EINVAL for an unknown value,
  * for SU3_SCHED_PERSISTENT where it does not apply, and for batch or
  * decomposed handles. */
-enum { SU3_SCHED_AUTO = 0, SU3_SCHED_PHASES = 1, SU3_SCHED_PERSISTENT = 2 };
+enum { SU3_SCHED_AUTO = 0, SU3_SCHED_PHASES = 1, SU3_SCHED_PERSISTENT = 2, SU3_SCHED_PER_DIRECTION = 3 };
 SU3_API int su3_set_schedule(su3_handle h, int schedule);
 
-/* The schedule the next sweep runs with (SU3_SCHED_PHASES or
- * SU3_SCHED_PERSISTENT) into *schedule. */
+/* The schedule the next sweep runs with (SU3_SCHED_PHASES,
+ * SU3_SCHED_PERSISTENT or SU3_SCHED_PER_DIRECTION) into *schedule. */
 SU3_API int su3_get_schedule(su3_handle h, int* schedule);
 
 /* Fault-detection hook of the persistent sweep (single lattices), as

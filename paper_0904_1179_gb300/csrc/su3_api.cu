@@ -174,17 +174,22 @@ bool persistent_applies(const su3_lattice* h) {
   return h->pairs && !h->split && su3k_pair_sweep_layers(h->pgeom, h->threads, &tpl) > 0;
 }
 
-// SU3_SCHED_AUTO takes the persistent sweep where a half-sweep is under 8
+// SU3_SCHED_AUTO takes a persistent sweep where a half-sweep is under 8
 // waves of the GPU (about 512 threads resident per SM at 128 registers): the
 // launch tails it removes cost a tenth of a 32^4 half-sweep (3.4 waves) and
-// little at 48^4 (17 waves), against an acquire fence per tile.  Measured at
-// 32^4: 1.5 % (FP32-mixed) and 0.5 % (FP32-EFT) faster than eight launches.
+// little at 48^4 (17 waves), against an acquire fence per waiting tile.
 bool use_persistent(const su3_lattice* h, bool measured = false) {
   if (measured || h->schedule == SU3_SCHED_PHASES || !persistent_applies(h)) return false;
-  if (h->schedule == SU3_SCHED_PERSISTENT) return true;
+  if (h->schedule == SU3_SCHED_PERSISTENT || h->schedule == SU3_SCHED_PER_DIRECTION) return true;
   const int sms = sm_count();
   return sms > 0 && (long long)h->pgeom.Vh < 8LL * 512 * sms;
 }
+
+// The persistent form: one launch per sweep, or one per direction (the
+// default: at 32^4 it ran 2.4 % (FP32-mixed) and 0.3 % (FP32-EFT) faster than
+// eight launches, against 1.2 % and 0.1 % for the single launch, whose four
+// update variants compete for the instruction caches).
+bool per_direction(const su3_lattice* h) { return h->schedule != SU3_SCHED_PERSISTENT; }
 
 // Counters and status word of the persistent sweep (allocated on first use,
 // outside any stream capture).
@@ -220,7 +225,8 @@ int enqueue_sweep_body(su3_lattice* h, bool measured) {
     const PairSweepQueue q{h->d_pq, h->d_pstatus, h->pq_wait_ns, h->pq_withhold};
     SU3_CUDA(cudaMemsetAsync(h->d_pq, 0, (size_t)h->pq_words * sizeof(unsigned int), h->stream),
              "sweep counters reset");
-    SU3_CUDA(su3k_launch_sweep_pair(a, q, h->precision == SU3_FP32_EFT, h->stats_on, h->threads, h->stream),
+    SU3_CUDA(su3k_launch_sweep_pair(a, q, h->precision == SU3_FP32_EFT, h->stats_on, h->threads, per_direction(h),
+                                    h->stream),
              "persistent sweep launch");
   } else {
     for (int mu = 0; mu < 4; ++mu)
@@ -630,9 +636,10 @@ int su3_set_schedule(su3_handle h, int schedule) {
   if (!h) return fail(SU3_EINVAL, "su3_set_schedule: NULL handle");
   if (is_batch(h) || su3_decomp_active(h))
     return fail(SU3_EINVAL, "su3_set_schedule: not for batch or decomposed handles");
-  if (schedule != SU3_SCHED_AUTO && schedule != SU3_SCHED_PHASES && schedule != SU3_SCHED_PERSISTENT)
+  if (schedule != SU3_SCHED_AUTO && schedule != SU3_SCHED_PHASES && schedule != SU3_SCHED_PERSISTENT &&
+      schedule != SU3_SCHED_PER_DIRECTION)
     return fail(SU3_EINVAL, "su3_set_schedule: unknown schedule %d", schedule);
-  if (schedule == SU3_SCHED_PERSISTENT && !persistent_applies(h))
+  if ((schedule == SU3_SCHED_PERSISTENT || schedule == SU3_SCHED_PER_DIRECTION) && !persistent_applies(h))
     return fail(SU3_EINVAL,
                 "su3_set_schedule: the persistent sweep needs the site-paired FP32 store, one thread per pair, "
                 "L3 >= 8, layers of whole blocks and the natural block order");
@@ -647,7 +654,9 @@ int su3_set_schedule(su3_handle h, int schedule) {
 int su3_get_schedule(su3_handle h, int* schedule) {
   if (!h || !schedule) return fail(SU3_EINVAL, "su3_get_schedule: NULL argument");
   if (is_batch(h)) return fail(SU3_EINVAL, "su3_get_schedule: batch handle");
-  *schedule = !su3_decomp_active(h) && use_persistent(h) ? SU3_SCHED_PERSISTENT : SU3_SCHED_PHASES;
+  *schedule = su3_decomp_active(h) || !use_persistent(h) ? SU3_SCHED_PHASES
+              : per_direction(h)                         ? SU3_SCHED_PER_DIRECTION
+                                                         : SU3_SCHED_PERSISTENT;
   return SU3_OK;
 }
 

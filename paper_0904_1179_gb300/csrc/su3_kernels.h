@@ -78,23 +78,26 @@ cudaError_t su3k_prepare();
 // finished the x3 layers of the pair lattice its staples reach (its own layer
 // and the two beside it).
 struct PairSweepQueue {
-  unsigned int* counters;  // [0]: next work item; [1 + q * layers + l]: tiles of phase q done in layer l; zeroed before each launch
+  unsigned int* counters;  // [0]: next work item of a one-launch sweep, [mu]: of direction mu's launch;
+                           // [kPairSweepTickets + q * layers + l]: tiles of phase q done in layer l; zeroed before each sweep
   int* status;             // 0, or kPairSweepTimeout once a bounded wait ran out (then every block stops)
   long long wait_ns;       // bound of one wait
   int withhold;            // fault-injection hook: this work item never reports completion (-1: none)
 };
 constexpr int kPairSweepTimeout = 1;
+constexpr int kPairSweepTickets = 4;
 // Layers of the pair lattice for the persistent sweep with blocks of
 // `threads`, or 0 where it does not apply (a layer is not a whole number of
 // tiles, fewer than four layers, or a block order other than the natural
 // one); *tiles_per_layer is set with it.
 int su3k_pair_sweep_layers(const su3dev::Geometry& gp, int threads, int* tiles_per_layer);
 // Counter words for a pair lattice of `layers` layers.
-inline int su3k_pair_sweep_words(int layers) { return 1 + 8 * layers; }
-// One sweep.  a.parity is unused; a.meas must be null (sweeps that measure
-// the plaquette run the eight half-sweep kernels).
+inline int su3k_pair_sweep_words(int layers) { return kPairSweepTickets + 8 * layers; }
+// One sweep: one launch, or (per_direction) four, one per direction mu with
+// its two half-sweeps.  a.parity is unused; a.meas must be null (sweeps that
+// measure the plaquette run the eight half-sweep kernels).
 cudaError_t su3k_launch_sweep_pair(const HalfSweepArgs& a, const PairSweepQueue& q, bool eft, bool stats, int threads,
-                                   cudaStream_t s);
+                                   bool per_direction, cudaStream_t s);
 
 // Status words of the bounds-checked build, one per translation unit with
 // kernels (su3_device.cuh, link_ok); 0 in the product build.

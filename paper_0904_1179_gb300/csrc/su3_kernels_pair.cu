@@ -152,28 +152,34 @@ __device__ __forceinline__ UpdateCount pair_item(const HalfSweepArgs& args, int 
 // Sweeps that measure the plaquette run the eight half-sweep kernels: the
 // measuring update variants added to this kernel's four made it spill and
 // ran 6 % slower.
-template <bool EFT, bool REPEAT>
+// MUSEL = -1: the eight half-sweeps of the sweep in one launch; MUSEL = 0..3:
+// the two half-sweeps (even, odd sites) of direction MUSEL, one launch per
+// direction, so that a launch runs a single update variant (the code of one
+// direction) and its first half-sweep waits for nothing.
+template <int MUSEL, bool EFT, bool REPEAT>
 __global__ void __launch_bounds__(256, 2)
     k_sweep_f32_pair(HalfSweepArgs args, PairSweepQueue qa, int tiles_per_layer, int layers, int stats) {
   extern __shared__ float4 smem[];
   __shared__ int s_tile, s_phase, s_layer, s_idx;
+  constexpr int kPhases = MUSEL < 0 ? 8 : 2, kFirst = MUSEL < 0 ? 0 : 2 * MUSEL;
   const int tiles_per_phase = tiles_per_layer * layers;
-  unsigned* const done = qa.counters + 1;
+  unsigned* const done = qa.counters + kPairSweepTickets;
   if (threadIdx.x < 32) {
     const int lane = (int)threadIdx.x;
     int idx = 0;
-    if (lane == 0) idx = (int)atomicAdd(qa.counters, 1u);
+    if (lane == 0) idx = (int)atomicAdd(qa.counters + (MUSEL < 0 ? 0 : MUSEL), 1u);
     idx = __shfl_sync(0xffffffffu, idx, 0);
     int phase = -1, tile = 0, layer = 0;
-    if (idx < 8 * tiles_per_phase) {
-      phase = idx / tiles_per_phase;
-      const int i = idx - phase * tiles_per_phase;
+    if (idx < kPhases * tiles_per_phase) {
+      phase = kFirst + idx / tiles_per_phase;
+      const int i = idx - (phase - kFirst) * tiles_per_phase;
       const int il = i / tiles_per_layer;
       layer = (il + phase) % layers;
       tile = layer * tiles_per_layer + (i - il * tiles_per_layer);
     }
     bool ok = phase >= 0 && (lane != 0 || ld_relaxed_s32(qa.status) == 0);
-    if (phase > 0 && lane < 3) {
+    const bool wait = phase > kFirst;  // the launch's first half-sweep follows the previous launch
+    if (wait && lane < 3) {
       // lane k waits for layer l + k - 1 of the previous phase
       const int lk = layer + lane - 1 < 0 ? layers - 1 : (layer + lane - 1 == layers ? 0 : layer + lane - 1);
       const unsigned* cnt = done + (phase - 1) * layers + lk;
@@ -192,7 +198,7 @@ __global__ void __launch_bounds__(256, 2)
     }
     ok = __all_sync(0xffffffffu, ok);
     if (lane == 0) {
-      if (ok && phase > 0) fence_acquire_gpu();
+      if (ok && wait) fence_acquire_gpu();
       s_phase = ok ? phase : -1;
       s_tile = tile;
       s_layer = layer;
@@ -208,11 +214,15 @@ __global__ void __launch_bounds__(256, 2)
   const int mu = phase >> 1, p = phase & 1;
   const int j = tile * (int)blockDim.x + (int)threadIdx.x;  // layers are whole tiles: always a pair of the lattice
   UpdateCount c;
-  switch (mu) {
-    case 0: c = pair_item<0, EFT, REPEAT>(args, j, p, t, uc, rg); break;
-    case 1: c = pair_item<1, EFT, REPEAT>(args, j, p, t, uc, rg); break;
-    case 2: c = pair_item<2, EFT, REPEAT>(args, j, p, t, uc, rg); break;
-    default: c = pair_item<3, EFT, REPEAT>(args, j, p, t, uc, rg); break;
+  if (MUSEL >= 0) {
+    c = pair_item<(MUSEL < 0 ? 0 : MUSEL), EFT, REPEAT>(args, j, p, t, uc, rg);
+  } else {
+    switch (mu) {
+      case 0: c = pair_item<0, EFT, REPEAT>(args, j, p, t, uc, rg); break;
+      case 1: c = pair_item<1, EFT, REPEAT>(args, j, p, t, uc, rg); break;
+      case 2: c = pair_item<2, EFT, REPEAT>(args, j, p, t, uc, rg); break;
+      default: c = pair_item<3, EFT, REPEAT>(args, j, p, t, uc, rg); break;
+    }
   }
   if (stats) {
     const int acc = __reduce_add_sync(0xffffffffu, c.accepted);
@@ -228,10 +238,18 @@ __global__ void __launch_bounds__(256, 2)
 
 template <bool EFT, bool REPEAT>
 cudaError_t launch_sweep(const HalfSweepArgs& a, const PairSweepQueue& q, int tpl, int layers, bool stats, int threads,
-                         cudaStream_t s) {
+                         bool per_direction, cudaStream_t s) {
   const size_t smem = (size_t)kPairRingBytesPerThread * threads;
-  const int blocks = 8 * tpl * layers;
-  k_sweep_f32_pair<EFT, REPEAT><<<blocks, threads, smem, s>>>(a, q, tpl, layers, stats ? 1 : 0);
+  const int st = stats ? 1 : 0;
+  if (!per_direction) {
+    k_sweep_f32_pair<-1, EFT, REPEAT><<<8 * tpl * layers, threads, smem, s>>>(a, q, tpl, layers, st);
+    return cudaGetLastError();
+  }
+  const int blocks = 2 * tpl * layers;
+  k_sweep_f32_pair<0, EFT, REPEAT><<<blocks, threads, smem, s>>>(a, q, tpl, layers, st);
+  k_sweep_f32_pair<1, EFT, REPEAT><<<blocks, threads, smem, s>>>(a, q, tpl, layers, st);
+  k_sweep_f32_pair<2, EFT, REPEAT><<<blocks, threads, smem, s>>>(a, q, tpl, layers, st);
+  k_sweep_f32_pair<3, EFT, REPEAT><<<blocks, threads, smem, s>>>(a, q, tpl, layers, st);
   return cudaGetLastError();
 }
 
@@ -255,8 +273,16 @@ cudaError_t prepare_mu() {
 template <bool EFT>
 cudaError_t prepare_all() {
   cudaError_t e;
-  if ((e = set_smem(k_sweep_f32_pair<EFT, false>)) != cudaSuccess) return e;
-  if ((e = set_smem(k_sweep_f32_pair<EFT, true>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<-1, EFT, false>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<-1, EFT, true>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<0, EFT, false>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<1, EFT, false>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<2, EFT, false>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<3, EFT, false>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<0, EFT, true>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<1, EFT, true>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<2, EFT, true>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_sweep_f32_pair<3, EFT, true>)) != cudaSuccess) return e;
   if ((e = prepare_mu<0, EFT>()) != cudaSuccess) return e;
   if ((e = prepare_mu<1, EFT>()) != cudaSuccess) return e;
   if ((e = prepare_mu<2, EFT>()) != cudaSuccess) return e;
@@ -293,17 +319,17 @@ int su3k_pair_sweep_layers(const Geometry& gp, int threads, int* tiles_per_layer
 }
 
 cudaError_t su3k_launch_sweep_pair(const HalfSweepArgs& a, const PairSweepQueue& q, bool eft, bool stats, int threads,
-                                   cudaStream_t s) {
+                                   bool per_direction, cudaStream_t s) {
   int tpl = 0;
   const int layers = su3k_pair_sweep_layers(a.pgeom, threads, &tpl);
   if (layers == 0) return cudaErrorInvalidValue;
   if (a.meas) return cudaErrorInvalidValue;  // measuring sweeps run the eight half-sweep kernels
   const bool rep = a.max_tries > 1;
   if (eft)
-    return rep ? launch_sweep<true, true>(a, q, tpl, layers, stats, threads, s)
-               : launch_sweep<true, false>(a, q, tpl, layers, stats, threads, s);
-  return rep ? launch_sweep<false, true>(a, q, tpl, layers, stats, threads, s)
-             : launch_sweep<false, false>(a, q, tpl, layers, stats, threads, s);
+    return rep ? launch_sweep<true, true>(a, q, tpl, layers, stats, threads, per_direction, s)
+               : launch_sweep<true, false>(a, q, tpl, layers, stats, threads, per_direction, s);
+  return rep ? launch_sweep<false, true>(a, q, tpl, layers, stats, threads, per_direction, s)
+             : launch_sweep<false, false>(a, q, tpl, layers, stats, threads, per_direction, s);
 }
 
 int su3k_pair_tile2(const Geometry& gp, int threads) {

@@ -29,8 +29,11 @@ def built():
     oracle.build()
 
 
-def pair(L, prec, seed, lanes=0, threads=0):
-    """Two identical lattices, the first on the persistent schedule, the second on eight kernels."""
+SCHEDS = [su3.SU3_SCHED_PERSISTENT, su3.SU3_SCHED_PER_DIRECTION]
+
+
+def pair(L, prec, seed, lanes=0, threads=0, schedule=su3.SU3_SCHED_PERSISTENT):
+    """Two identical lattices, the first on a persistent schedule, the second on eight kernels."""
     a = su3.Lattice(L, BETA, seed, start=su3.SU3_HOT, precision=prec)
     b = su3.Lattice(L, BETA, seed, start=su3.SU3_HOT, precision=prec)
     for lat in (a, b):
@@ -38,8 +41,9 @@ def pair(L, prec, seed, lanes=0, threads=0):
             lat.set_lanes(lanes)
         if threads:
             lat.set_block_size(threads)
+    a.set_schedule(schedule)
     b.set_schedule(su3.SU3_SCHED_PHASES)
-    assert a.schedule == su3.SU3_SCHED_PERSISTENT
+    assert a.schedule == schedule
     assert b.schedule == su3.SU3_SCHED_PHASES
     return a, b
 
@@ -47,11 +51,12 @@ def pair(L, prec, seed, lanes=0, threads=0):
 # 8^4 (one lane per pair forced; 4 layers of 8 tiles of 32), 12^3 x 16
 # (8 layers of 27 tiles of 32), 16^4 (8 layers of 32 tiles of 64), 32^4 (the
 # bench lattice: 16 layers of 128 tiles of 128).
+@pytest.mark.parametrize("sched", SCHEDS)
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("L,lanes", [((8, 8, 8, 8), 1), ((12, 12, 12, 16), 0), ((16, 16, 16, 16), 0),
                                      ((32, 32, 32, 32), 0)])
-def test_persistent_sweep_equals_eight_kernels(L, lanes, prec):
-    a, b = pair(L, prec, 21, lanes=lanes)
+def test_persistent_sweep_equals_eight_kernels(L, lanes, prec, sched):
+    a, b = pair(L, prec, 21, lanes=lanes, schedule=sched)
     with a, b:
         for lat in (a, b):
             lat.set_stats(True)
@@ -96,10 +101,11 @@ def test_persistent_and_measured_sweeps_interleave(prec):
         assert a.sweep_count == b.sweep_count == 6
 
 
+@pytest.mark.parametrize("sched", SCHEDS)
 @pytest.mark.parametrize("prec", PRECS)
-def test_persistent_repeat_until_accepted_equals_eight_kernels(prec):
+def test_persistent_repeat_until_accepted_equals_eight_kernels(prec, sched):
     L = (12, 12, 12, 16)
-    a, b = pair(L, prec, 14)
+    a, b = pair(L, prec, 14, schedule=sched)
     with a, b:
         for lat in (a, b):
             lat.set_heatbath(8)
@@ -124,7 +130,7 @@ def test_persistent_sweep_matches_oracle_reading(prec):
     oracle.sweep(L, BETA, seed, t, 1, O, f32=True)
     with su3.Lattice(L, BETA, seed, start=su3.SU3_COLD, precision=prec) as lat:
         lat.set_lanes(1)
-        assert lat.schedule == su3.SU3_SCHED_PERSISTENT
+        assert lat.schedule == su3.SU3_SCHED_PER_DIRECTION
         lat.set_links(U0)
         lat.sweep_count = t
         lat.sweep(1)
@@ -144,9 +150,10 @@ def test_schedule_applies_where_documented():
                     ((16, 16, 16, 4), su3.SU3_FP32_MIXED), ((8, 8, 8, 8), su3.SU3_FP32_EFT)):
         with su3.Lattice(L, BETA, 1, precision=prec) as lat:
             assert lat.schedule == su3.SU3_SCHED_PHASES, L
-            with pytest.raises(su3.Su3Error) as e:
-                lat.set_schedule(su3.SU3_SCHED_PERSISTENT)
-            assert e.value.code == su3.SU3_EINVAL
+            for sched in SCHEDS:
+                with pytest.raises(su3.Su3Error) as e:
+                    lat.set_schedule(sched)
+                assert e.value.code == su3.SU3_EINVAL
     with su3.Lattice((16, 16, 16, 16), BETA, 1, precision=su3.SU3_FP32_MIXED) as lat:
         with pytest.raises(su3.Su3Error):
             lat.set_schedule(7)
@@ -154,8 +161,10 @@ def test_schedule_applies_where_documented():
         assert lat.schedule == su3.SU3_SCHED_PHASES
         lat.set_schedule(su3.SU3_SCHED_PERSISTENT)
         assert lat.schedule == su3.SU3_SCHED_PERSISTENT
+        lat.set_schedule(su3.SU3_SCHED_PER_DIRECTION)
+        assert lat.schedule == su3.SU3_SCHED_PER_DIRECTION
         lat.set_schedule(su3.SU3_SCHED_AUTO)
-        assert lat.schedule == su3.SU3_SCHED_PERSISTENT
+        assert lat.schedule == su3.SU3_SCHED_PER_DIRECTION
         with pytest.raises(su3.Su3Error):
             lat.debug(0.0)
     with su3.Batch([(8, 8, 8, 8)], [BETA], [1]) as bt:
@@ -166,10 +175,12 @@ def test_schedule_applies_where_documented():
 # Fault detection without a fault: a work item that never reports completion
 # makes the waits on it run out (0.2 s), the sweep stops, su3_status reports
 # SU3_ETIMEOUT once, and the context keeps working.
-def test_withheld_tile_times_out_without_fault():
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_withheld_tile_times_out_without_fault(sched):
     L = (16, 16, 16, 16)
     with su3.Lattice(L, BETA, 2, precision=su3.SU3_FP32_MIXED) as lat:
-        assert lat.schedule == su3.SU3_SCHED_PERSISTENT
+        lat.set_schedule(sched)
+        assert lat.schedule == sched
         lat.debug(0.2, withhold_item=0)  # the first tile of phase 0 (mu = 0, even sites)
         lat.sweep(1)
         with pytest.raises(su3.Su3Error) as e:
