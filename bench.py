@@ -84,18 +84,26 @@ def peaks():
 # same; otherwise its traffic is null and the line says why.
 _U_F64, _U_F32, _U_BATCH = ("su3_kernels.cu",), ("su3_kernels.cu", "su3_kernels_pair.cu"), ("su3_batch.cu",)
 _SHA_F64 = "674790eeb6cadbfad662bf71b033a2b476af3ed90f850a86e0fbfcb85f355a9a"
-_SHA_F32 = "1ea1f36ad62a866a95f22736c29d02d4949689dcda83c6ba9a787b7877b22c98"
+_SHA_F32 = "f361ce718b7991383c6ec3f6aa8cda928488d01abfa66bbf70538720b21afad1"
 _SHA_BATCH = "ca07367f370764aebcf51a906f9f42f6a0f3127a5b5ccebeed8f605bbecf5ac4"
 _NCU_METRICS = "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none"
 NCU_TRAFFIC = {
-    "fp32_mixed_onelaunch": {"bytes": 1666981632 + 190839040, "units": _U_F32, "sources_sha256": _SHA_F32,
-                   "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 1 -c 1 python bench.py --profile fp32_mixed"},
-    "fp32_eft_onelaunch": {"bytes": 1669437184 + 191675648, "units": _U_F32, "sources_sha256": _SHA_F32,
-                 "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 1 -c 1 python bench.py --profile fp32_eft"},
-    "fp32_mixed_phases": {"bytes": 207923456 + 15627008, "units": _U_F32, "sources_sha256": _SHA_F32,
+    # one launch of the default 32^4 FP32 sweep = one direction's two half-sweeps; the mean of the four
+    # launches (mu = 0..3) of the second sweep
+    "fp32_mixed": {"bytes": 456205888, "units": _U_F32, "sources_sha256": _SHA_F32,
+                   "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 4 -c 4 python bench.py --profile fp32_mixed"},
+    "fp32_eft": {"bytes": 457019520, "units": _U_F32, "sources_sha256": _SHA_F32,
+                 "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 4 -c 4 python bench.py --profile fp32_eft"},
+    "fp32_mixed_onelaunch": {"bytes": 1666766336 + 190898176, "units": _U_F32, "sources_sha256": _SHA_F32,
+                             "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 1 -c 1 python bench.py --profile "
+                                                       "fp32_mixed_onelaunch"},
+    "fp32_eft_onelaunch": {"bytes": 1668618496 + 191699456, "units": _U_F32, "sources_sha256": _SHA_F32,
+                           "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 1 -c 1 python bench.py --profile "
+                                                     "fp32_eft_onelaunch"},
+    "fp32_mixed_phases": {"bytes": 207856384 + 15830784, "units": _U_F32, "sources_sha256": _SHA_F32,
                           "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile "
                                                     "fp32_mixed_phases"},
-    "fp32_eft_phases": {"bytes": 208064000 + 16438016, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_eft_phases": {"bytes": 208006656 + 16648960, "units": _U_F32, "sources_sha256": _SHA_F32,
                         "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile "
                                                   "fp32_eft_phases"},
     "fp64": {"bytes": 623867648 + 64909568, "units": _U_F64, "sources_sha256": _SHA_F64,
