@@ -215,11 +215,11 @@ SU3_API int su3_set_lanes(su3_handle h, int lanes);
  *     per direction mu with its even and odd half-sweeps (each launch runs the
  *     update code of one direction; tails remain between directions);
  *   SU3_SCHED_AUTO (the default): SU3_SCHED_PER_DIRECTION where the
- *     persistent forms apply and a half-sweep is under 8 waves of the GPU
- *     (V/4 pairs < 8 x 512 x SMs, e.g. 32^4; there the tails of eight
- *     launches are a tenth of the work), else SU3_SCHED_PHASES.  Measured at
- *     32^4 against eight launches: per direction +2.4 % (FP32-mixed) and
- *     +0.3 % (FP32-EFT), one launch +1.2 % and +0.1 %.
+ *     persistent forms apply and one half-sweep is 2 to 5 waves of the GPU,
+ *     w = (V/4 pairs) / (512 x SMs) (32^4: +2.4 % FP32-mixed, +0.3 % FP32-EFT
+ *     against eight launches), else eight half-sweep kernels (fastest from
+ *     32^3 x 64, 40^4, 48^4 on, and on small lattices whose half-sweep is in
+ *     flight at once; 24^4 alone ran faster in one launch: +7 %, +12 %).
  * su3_sweep_measured always runs the eight kernels (its measuring update
  * variants would make the persistent kernel spill).
  * Results do not depend on it, bit for bit.  SU3_EINVAL for an unknown value,

@@ -174,22 +174,37 @@ bool persistent_applies(const su3_lattice* h) {
   return h->pairs && !h->split && su3k_pair_sweep_layers(h->pgeom, h->threads, &tpl) > 0;
 }
 
-// SU3_SCHED_AUTO takes a persistent sweep where a half-sweep is under 8
-// waves of the GPU (about 512 threads resident per SM at 128 registers): the
-// launch tails it removes cost a tenth of a 32^4 half-sweep (3.4 waves) and
-// little at 48^4 (17 waves), against an acquire fence per waiting tile.
+// Waves of the GPU in one half-sweep of the paired store (about 512 threads,
+// one pair each, resident per SM at 128 registers).
+double half_sweep_waves(const su3_lattice* h) {
+  const int sms = sm_count();
+  return sms > 0 ? (double)h->pgeom.Vh / (512.0 * sms) : 1e9;
+}
+
+// SU3_SCHED_AUTO by the number of waves of a half-sweep, after measurements
+// on GB300 (FP32-mixed / FP32-EFT, against eight launches): 32^4 (3.4 waves)
+// per direction +2.4 / +0.3 %, one launch +1.2 / +0.1 %; from 32^3 x 64 (6.7
+// waves) on, and at 40^4 and 48^4, eight launches are fastest (per direction
+// -0.6 to -6 %).  Below 2 waves the result depends on the x3 layers: 24^4
+// (1.1 waves, 12 layers) one launch +7 / +12 %, but 24^3 x 16 (0.7 waves, 8
+// layers) -28 / -27 % and 16^4 -55 / -57 %, where a whole half-sweep is in
+// flight at once and the tiles of the next one wait on it: eight launches.
+int auto_schedule(const su3_lattice* h) {
+  const double w = half_sweep_waves(h);
+  return w >= 2.0 && w < 5.0 ? SU3_SCHED_PER_DIRECTION : SU3_SCHED_PHASES;
+}
+
 bool use_persistent(const su3_lattice* h, bool measured = false) {
   if (measured || h->schedule == SU3_SCHED_PHASES || !persistent_applies(h)) return false;
   if (h->schedule == SU3_SCHED_PERSISTENT || h->schedule == SU3_SCHED_PER_DIRECTION) return true;
-  const int sms = sm_count();
-  return sms > 0 && (long long)h->pgeom.Vh < 8LL * 512 * sms;
+  return auto_schedule(h) != SU3_SCHED_PHASES;
 }
 
-// The persistent form: one launch per sweep, or one per direction (the
-// default: at 32^4 it ran 2.4 % (FP32-mixed) and 0.3 % (FP32-EFT) faster than
-// eight launches, against 1.2 % and 0.1 % for the single launch, whose four
-// update variants compete for the instruction caches).
-bool per_direction(const su3_lattice* h) { return h->schedule != SU3_SCHED_PERSISTENT; }
+// The persistent form: one launch per sweep, or one per direction.
+bool per_direction(const su3_lattice* h) {
+  return h->schedule == SU3_SCHED_PER_DIRECTION ||
+         (h->schedule == SU3_SCHED_AUTO && auto_schedule(h) == SU3_SCHED_PER_DIRECTION);
+}
 
 // Counters and status word of the persistent sweep (allocated on first use,
 // outside any stream capture).

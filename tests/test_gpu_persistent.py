@@ -130,7 +130,7 @@ def test_persistent_sweep_matches_oracle_reading(prec):
     oracle.sweep(L, BETA, seed, t, 1, O, f32=True)
     with su3.Lattice(L, BETA, seed, start=su3.SU3_COLD, precision=prec) as lat:
         lat.set_lanes(1)
-        assert lat.schedule == su3.SU3_SCHED_PER_DIRECTION
+        lat.set_schedule(su3.SU3_SCHED_PERSISTENT)
         lat.set_links(U0)
         lat.sweep_count = t
         lat.sweep(1)
@@ -140,6 +140,15 @@ def test_persistent_sweep_matches_oracle_reading(prec):
     assert off <= d.size // 100, (off, d.size)
     print("persistent FP32 sweep (precision %d) vs oracle: worst |dU| %.2e over %d links, %d beyond 5e-5"
           % (prec, float(np.sort(d.ravel())[d.size - off - 1]), d.size, off))
+
+
+def test_automatic_schedule_follows_the_waves():
+    # 16^4: 0.2 waves per half-sweep, eight launches; 32^4: 3.4, one launch
+    # per direction; 32^3 x 64: 6.7, eight launches
+    for L, sched in (((16, 16, 16, 16), su3.SU3_SCHED_PHASES), ((32, 32, 32, 32), su3.SU3_SCHED_PER_DIRECTION),
+                     ((32, 32, 32, 64), su3.SU3_SCHED_PHASES)):
+        with su3.Lattice(L, BETA, 1, precision=su3.SU3_FP32_MIXED) as lat:
+            assert lat.schedule == sched, L
 
 
 def test_schedule_applies_where_documented():
@@ -164,7 +173,7 @@ def test_schedule_applies_where_documented():
         lat.set_schedule(su3.SU3_SCHED_PER_DIRECTION)
         assert lat.schedule == su3.SU3_SCHED_PER_DIRECTION
         lat.set_schedule(su3.SU3_SCHED_AUTO)
-        assert lat.schedule == su3.SU3_SCHED_PER_DIRECTION
+        assert lat.schedule == su3.SU3_SCHED_PHASES  # a fraction of a wave per half-sweep
         with pytest.raises(su3.Su3Error):
             lat.debug(0.0)
     with su3.Batch([(8, 8, 8, 8)], [BETA], [1]) as bt:
