@@ -290,7 +290,8 @@ SU3_API int su3_decomp_info(su3_handle h, int* ndmpi, int* mpifactor, int* lbcex
 /* ---------------------------------------------------------------------------
  * Batches: n independent replicas, each with its own extents, beta and Philox
  * seed (the same counter layout, keyed by the replica's seed), swept together
- * by ONE persistent kernel launch per sweep, captured in a CUDA graph.  Each
+ * by ONE kernel launch per sweep (one block per tile of a replica's
+ * half-sweep, tiles taken in phase order), captured in a CUDA graph.  Each
  * replica performs exactly the single-lattice sweep: replica r after k sweeps
  * equals a lattice created alone with dims[r], betas[r], seeds[r] after k
  * sweeps, bit for bit.
@@ -309,8 +310,8 @@ SU3_API int su3_batch_create(int n, const int (*dims)[4], const double* betas, c
                              int precision, void* cuda_stream, su3_handle* out);
 
 /* nsweeps sweeps of every replica; asynchronous, one graph replay (memset of
- * the arrival counters, the persistent sweep kernel, the sweep-counter
- * increment) per sweep.  Inside the kernel, a tile of phase k of replica r
+ * the arrival counters, the sweep kernel, the sweep-counter increment) per
+ * sweep.  Inside the kernel, a tile of phase k of replica r
  * waits for all tiles of phase k-1 of r; the wait is bounded in time and, if
  * it runs out, the sweep stops and the next synchronising call returns
  * SU3_ETIMEOUT (the configuration is then incomplete). */
@@ -329,14 +330,16 @@ SU3_API int su3_batch_links_set(su3_handle b, int replica, const double* host, s
 SU3_API int su3_batch_size(su3_handle b, int* n);
 
 /* Dispatch configuration: threads per block (= half-sites per tile, a multiple
- * of 32 in [32, 256]; 0 = 128), persistent blocks per SM (0 = as many as fit),
+ * of 32 in [32, 256]; 0 = 128), blocks_per_sm (>= 0; accepted and kept, but
+ * without effect: the sweep launches one block per work item, and
+ * su3_batch_get_config reports the blocks the GPU keeps resident per SM),
  * replicas per L2 window (0 = all: phase-major order over the whole batch).
  * Results do not depend on it. */
 SU3_API int su3_batch_config(su3_handle b, int threads, int blocks_per_sm, int window);
 SU3_API int su3_batch_get_config(su3_handle b, int* threads, int* blocks_per_sm, int* window);
 
-/* Time every candidate configuration (threads 64/128/256, blocks per SM up to
- * the occupancy limit, windows of n, n/2, n/4, ... replicas) on this batch
+/* Time every candidate configuration (threads 64/128/256, windows of n, n/2,
+ * n/4, ... replicas) on this batch
  * -- one untimed sweep, then the median of three timed sweeps each --,
  * keep the fastest, and remember it for batches of the same replica extents
  * and precision on the same GPU model in this process.  The links and the

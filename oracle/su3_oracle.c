@@ -17,8 +17,8 @@
  *   - the MPI code uses a "1-hit" heatbath update of each SU(3) matrix
  *     (Sec. 2.1, remark on the non-MPI program's repeat-until-accepted
  *     heatbath and the 97.2% 1-hit acceptance at beta = 5.7);
- *   - PBC through neighbour pointer arrays, the "usual implementation"
- *     (Sec. 2.1, paragraph on the boundary exchange cost);
+ *   - PBC through neighbour pointer arrays, the common implementation that
+ *     Sec. 2.1 mentions in its paragraph on the boundary exchange cost;
  *   - one timed unit = one SU(3) matrix update (Sec. 2.1, Fig. 1 caption);
  *   - start-configuration creation is separate from the sweeps (Sec. 2).
  * Everything else is silent in the paper and follows these textbook
