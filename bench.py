@@ -85,7 +85,7 @@ def peaks():
 _U_F64, _U_F32, _U_BATCH = ("su3_kernels.cu",), ("su3_kernels.cu", "su3_kernels_pair.cu"), ("su3_batch.cu",)
 _SHA_F64 = "674790eeb6cadbfad662bf71b033a2b476af3ed90f850a86e0fbfcb85f355a9a"
 _SHA_F32 = "f361ce718b7991383c6ec3f6aa8cda928488d01abfa66bbf70538720b21afad1"
-_SHA_BATCH = "ca07367f370764aebcf51a906f9f42f6a0f3127a5b5ccebeed8f605bbecf5ac4"
+_SHA_BATCH = "07af98049c72020f9c70482ba36abe379016dd4ede3d459fa0a3157b2eda4179"
 _NCU_METRICS = "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none"
 NCU_TRAFFIC = {
     # one launch of the default 32^4 FP32 sweep = one direction's two half-sweeps; the mean of the four
@@ -108,9 +108,9 @@ NCU_TRAFFIC = {
                                                   "fp32_eft_phases"},
     "fp64": {"bytes": 623867648 + 64909568, "units": _U_F64, "sources_sha256": _SHA_F64,
              "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile fp64"},
-    "batched": {"bytes": 3034027776 + 418116352, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
+    "batched": {"bytes": 3033302272 + 490120192, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
                 "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 1 -c 1 python bench.py --profile batched"},
-    "batched_eft": {"bytes": 3033860352 + 418545408, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
+    "batched_eft": {"bytes": 3033470464 + 490923008, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
                     "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 1 -c 1 python bench.py --profile batched_eft"},
 }
 

@@ -148,3 +148,20 @@ def test_batch_repeat_until_accepted_equals_single_lattices():
                 lat.set_heatbath(4)
                 lat.sweep(2)
                 assert np.array_equal(b.get_links(r), lat.get_links()), r
+
+
+# More replicas than the kernel parameters carry (200): the descriptors are
+# read from global memory; each replica still equals the lattice run alone.
+@pytest.mark.parametrize("prec", [su3.SU3_FP32_MIXED, su3.SU3_FP64])
+def test_batch_beyond_parameter_descriptors(prec):
+    n = 203
+    dims = [MIX[r % len(MIX)] for r in range(n)]
+    betas = [BETAS[r % len(BETAS)] for r in range(n)]
+    seeds = [5000 + r for r in range(n)]
+    with su3.Batch(dims, betas, seeds, start=su3.SU3_HOT, precision=prec) as b:
+        b.sweep(2)
+        b.status()
+        for r in (0, 101, 202):
+            with su3.Lattice(dims[r], betas[r], seeds[r], start=su3.SU3_HOT, precision=prec) as lat:
+                lat.sweep(2)
+                assert np.array_equal(b.get_links(r), lat.get_links()), r
