@@ -377,11 +377,14 @@ SU3_API int su3_status(su3_handle h);
  *                       im u1k); row 2 is conj(row0 x row1);
  *       SU3_FP32_MIXED, SU3_FP32_EFT, L3 a multiple of 4 (site pairs x and
  *       x + (L3/2) e3 side by side):
- *                       float4  [4 mu][2 parity][6 entries e = 3r+k][V/4],
- *                       rows r = 0, 1: entry e of pair j = (re u_rk(x),
- *                       re u_rk(x'), im u_rk(x), im u_rk(x')), where j is
- *                       the half index of x on the L0 x L1 x L2 x L3/2 pair
- *                       lattice (x3 < L3/2) and x' = x + (L3/2) e3.
+ *                       float4  [4 mu][2 parity][Vp'/32][6 entries e = 3r+k]
+ *                       [32], Vp = V/4 pairs per (mu, parity) in tiles of
+ *                       32, Vp' = Vp rounded up to a multiple of 32 (the
+ *                       padding is never read): pair j is lane j mod 32 of
+ *                       tile j / 32, and for rows r = 0, 1 its entry e =
+ *                       (re u_rk(x), re u_rk(x'), im u_rk(x), im u_rk(x')),
+ *                       where j is the half index of x on the L0 x L1 x L2 x
+ *                       L3/2 pair lattice (x3 < L3/2) and x' = x + (L3/2) e3.
  *   out: device pointer to one double that receives the mean plaquette, as
  *     defined for su3_plaquette, when the work enqueued on cuda_stream runs.
  *   cuda_stream: the cudaStream_t to enqueue on (NULL = the default stream).

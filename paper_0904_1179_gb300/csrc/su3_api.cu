@@ -403,7 +403,9 @@ int su3_create_ex(int L0, int L1, int L2, int L3, double beta, uint64_t seed, in
     }
     h->own_stream = true;
   }
-  h->link_bytes = (size_t)V * 4 * (precision == SU3_FP64 ? 18 * sizeof(double) : 12 * sizeof(float));
+  // the site-paired FP32 store pads each (mu, parity) array to whole tiles of pairs
+  h->link_bytes = h->pairs ? (size_t)8 * 6 * su3dev::pair_padded(V / 4) * sizeof(float4)
+                           : (size_t)V * 4 * (precision == SU3_FP64 ? 18 * sizeof(double) : 12 * sizeof(float));
   const int nparts = su3k_plaquette_blocks(h->geom);
   const long long chunk = V < kChunkSites ? V : kChunkSites;
   if ((e = cudaMalloc(&h->links, h->link_bytes)) != cudaSuccess ||

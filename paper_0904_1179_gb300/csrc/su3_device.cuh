@@ -564,6 +564,21 @@ __device__ __forceinline__ size_t link_base(int mu, int p, int Vh, int ncomp) {
   return ((size_t)(mu * 2 + p) * ncomp) * (size_t)Vh;
 }
 
+// Site-paired FP32 store (su3_sitepair.cuh): the Vp pairs of one (mu, parity)
+// come in tiles of kPairTile, the last one padded; a tile holds its six
+// entries one after another, kPairTile float4 each.  Entry e of pair j sits
+// at pair_offset(mu, p, j, Vp) + kPairTile e: the six entries of a link pair
+// lie in one 3 KB block, and a warp's 32 consecutive pairs read 512
+// contiguous bytes per entry.
+constexpr int kPairTile = 32;
+__host__ __device__ __forceinline__ long long pair_padded(long long Vp) {
+  return (Vp + kPairTile - 1) / kPairTile * kPairTile;
+}
+__device__ __forceinline__ size_t pair_offset(int mu, int p, int j, int Vp) {
+  return (size_t)(mu * 2 + p) * 6 * (size_t)pair_padded(Vp) + (size_t)(j / kPairTile) * (6 * kPairTile) +
+         (size_t)(j % kPairTile);
+}
+
 template <bool CG>
 __device__ __forceinline__ double2 ld_link(const double2* p) {
   return CG ? __ldcg(p) : __ldg(p);

@@ -28,13 +28,14 @@
 namespace su3dev {
 
 // ---------------------------------------------------------------------------
-// Site-paired FP32 store: float4 [4 mu][2 parity][6 entries e = 3 r + k][Vp]
-// for rows r = 0, 1 and columns k, Vp = V/4 pairs per (mu, parity); entry e
-// of pair j holds (re u_rk(x), re u_rk(x'), im u_rk(x), im u_rk(x')).  Row 2
-// is conj(row0 x row1), as in the single-site store.  A single site h of the
-// full lattice (half index, h < V/2) is pair j = h mod Vp, member h / Vp.
+// Site-paired FP32 store: float4 [4 mu][2 parity][Vp' / 32 tiles][6 entries
+// e = 3 r + k][32 pairs] for rows r = 0, 1 and columns k, Vp = V/4 pairs per
+// (mu, parity), Vp' = Vp rounded up to a multiple of 32 (pair_offset in
+// su3_device.cuh); entry e of pair j holds (re u_rk(x), re u_rk(x'),
+// im u_rk(x), im u_rk(x')).  Row 2 is conj(row0 x row1), as in the
+// single-site store.  A single site h of the full lattice (half index,
+// h < V/2) is pair j = h mod Vp, member h / Vp.
 // ---------------------------------------------------------------------------
-constexpr int kEntriesPair = 6;
 
 // Whether an FP32 store of a lattice with these extents uses the site-paired
 // layout: L3 divisible by 4 (the two members of a pair then share parity and x0).
@@ -139,10 +140,10 @@ __device__ __forceinline__ void swap_halves(PM& m, bool sw) {
 __device__ __forceinline__ void store_pm_rows01(float4* U, int mu, int p, int j, int Vp, const float2 re[2][3],
                                                 const float2 im[2][3]) {
   if (!link_ok(mu, p, j, Vp)) return;
-  float4* b = U + link_base(mu, p, Vp, kEntriesPair) + j;
+  float4* b = U + pair_offset(mu, p, j, Vp);
 #pragma unroll
   for (int e = 0; e < 6; ++e)
-    b[(size_t)e * Vp] = make_float4(re[e / 3][e % 3].x, re[e / 3][e % 3].y, im[e / 3][e % 3].x, im[e / 3][e % 3].y);
+    b[kPairTile * e] = make_float4(re[e / 3][e % 3].x, re[e / 3][e % 3].y, im[e / 3][e % 3].x, im[e / 3][e % 3].y);
 }
 
 // Row 2 = conj(row0 x row1), in the order of complete_row2_p.
@@ -311,10 +312,10 @@ template <bool CG>
 __device__ __forceinline__ void rolled_issue(const Geometry& gp, const float4* U, const RolledLink& l,
                                              const PairRing& rg, int slot) {
   if (!link_ok(l.mu, l.par, l.idx, gp.Vh)) return;
-  const float4* b = U + link_base(l.mu, l.par, gp.Vh, kEntriesPair) + l.idx;
+  const float4* b = U + pair_offset(l.mu, l.par, l.idx, gp.Vh);
   const uint32_t sa = rg.sa + (uint32_t)(16 * slot * rg.step);
 #pragma unroll
-  for (int e = 0; e < 6; ++e) cp_async16<CG>(sa + 16 * e, b + (size_t)e * gp.Vh);
+  for (int e = 0; e < 6; ++e) cp_async16<CG>(sa + 16 * e, b + kPairTile * e);
 }
 
 // Take link c (0..5) of direction index i (direction nu) and request the link
@@ -571,31 +572,47 @@ __device__ __forceinline__ bool kp_member(float ia, uint32_t s, uint32_t w1base,
   return false;
 }
 
-// One-hit proposal of one member without branches (the accept decision is
-// returned, the proposal a[] computed whatever it is), so that the two
-// members' Philox and sampler chains can be interleaved.  Same arithmetic as
-// kp_member's first try.
+// Both members' one-hit proposals at once, without branches (the accept
+// decisions are returned, the proposals computed whatever they are): each
+// member draws from its own site's counters (s0, s1), and the FP32
+// arithmetic of kp_member's first try runs on paired instructions, lane by
+// lane the same roundings (the transcendentals stay one per lane).
+__device__ __forceinline__ float2 u01_q(uint32_t a, uint32_t b) {
+  return qsub(make_float2(__int_as_float((int)(0x3F800000u | (a >> 9))), __int_as_float((int)(0x3F800000u | (b >> 9)))),
+              make_float2(1.0f - 0x1p-24f, 1.0f - 0x1p-24f));
+}
+__device__ __forceinline__ float2 qconst(float c) { return make_float2(c, c); }
+
 template <typename KEY>
-__device__ __forceinline__ bool kp_member_1hit(float ia, uint32_t s, uint32_t w1base, uint64_t t, const KEY& key,
-                                               float a[4]) {
-  const uint4 w0 = philox4x32_10(rng_counter(s, w1base, t, kTagUpdate), key);
-  const uint4 w1 = philox4x32_10(rng_counter(s, w1base | (1u << 4), t, kTagUpdate), key);
-  const float u0 = u01_f32(w0.x), u1 = u01_f32(w0.y), u2 = u01_f32(w0.z), u3 = u01_f32(w0.w);
-  const float cc = __cosf(fmaf(6.2831853f, u1, -3.14159265f));
-  const float delta = __fmul_rn(-__fmaf_rn(__fmul_rn(cc, cc), __logf(u2), __logf(u0)), ia);
-  const bool acc = !(__fmul_rn(u3, u3) > __fmaf_rn(-0.5f, delta, 1.0f));
-  const float u4 = u01_f32(w1.x), u5 = u01_f32(w1.y);
-  const float rho = sqrt_approx(fmaxf(0.0f, delta * (2.0f - delta)));
-  const float ct = __fmaf_rn(-2.0f, u4, 1.0f);
-  const float sn = 2.0f * sqrt_approx(u4 * (1.0f - u4));
-  float sphi, cphi;
-  __sincosf(fmaf(6.2831853f, u5, -3.14159265f), &sphi, &cphi);
-  const float rs = -rho * sn;
-  a[0] = 1.0f - delta;
-  a[1] = rs * cphi;
-  a[2] = rs * sphi;
-  a[3] = rho * ct;
-  return acc;
+__device__ __forceinline__ void kp_pair_1hit(float2 ia, uint32_t s0, uint32_t s1, uint32_t w1base, uint64_t t,
+                                             const KEY& key, bool& accx, bool& accy, float2 a[4]) {
+  const uint4 x0 = philox4x32_10(rng_counter(s0, w1base, t, kTagUpdate), key);
+  const uint4 y0 = philox4x32_10(rng_counter(s1, w1base, t, kTagUpdate), key);
+  const uint4 x1 = philox4x32_10(rng_counter(s0, w1base | (1u << 4), t, kTagUpdate), key);
+  const uint4 y1 = philox4x32_10(rng_counter(s1, w1base | (1u << 4), t, kTagUpdate), key);
+  const float2 u0 = u01_q(x0.x, y0.x), u1 = u01_q(x0.y, y0.y), u2 = u01_q(x0.z, y0.z), u3 = u01_q(x0.w, y0.w);
+  const float2 ph = qfma(qconst(6.2831853f), u1, qconst(-3.14159265f));
+  const float2 cc = make_float2(__cosf(ph.x), __cosf(ph.y));
+  const float2 l0 = make_float2(__logf(u0.x), __logf(u0.y)), l2 = make_float2(__logf(u2.x), __logf(u2.y));
+  const float2 delta = qmul(qneg(qfma(qmul(cc, cc), l2, l0)), ia);
+  const float2 lhs = qmul(u3, u3), rhs = qfma(qconst(-0.5f), delta, qconst(1.0f));
+  accx = !(lhs.x > rhs.x);
+  accy = !(lhs.y > rhs.y);
+  const float2 u4 = u01_q(x1.x, y1.x), u5 = u01_q(x1.y, y1.y);
+  const float2 q = qmul(delta, qsub(qconst(2.0f), delta));
+  const float2 rho = make_float2(sqrt_approx(fmaxf(0.0f, q.x)), sqrt_approx(fmaxf(0.0f, q.y)));
+  const float2 ct = qfma(qconst(-2.0f), u4, qconst(1.0f));
+  const float2 w = qmul(u4, qsub(qconst(1.0f), u4));
+  const float2 sn = qmul(qconst(2.0f), make_float2(sqrt_approx(w.x), sqrt_approx(w.y)));
+  const float2 pf = qfma(qconst(6.2831853f), u5, qconst(-3.14159265f));
+  float2 sphi, cphi;
+  __sincosf(pf.x, &sphi.x, &cphi.x);
+  __sincosf(pf.y, &sphi.y, &cphi.y);
+  const float2 rs = qmul(qneg(rho), sn);
+  a[0] = qsub(qconst(1.0f), delta);
+  a[1] = qmul(rs, cphi);
+  a[2] = qmul(rs, sphi);
+  a[3] = qmul(rho, ct);
 }
 
 template <int MU, bool EFT, bool REPEAT, bool MEAS, typename KEY>
@@ -625,9 +642,10 @@ __device__ __forceinline__ UpdateCount heatbath_q(const Geometry& gp, float4* U,
     const float2 ia = qmul(tob, ik);
     const int ntries = REPEAT ? uc.max_tries : 1;
     const uint32_t w1base = (uint32_t)(MU | (sub << 2));
-    float ax[4] = {1.f, 0.f, 0.f, 0.f}, ay[4] = {1.f, 0.f, 0.f, 0.f};
     bool accx = false, accy = false;
+    float2 a0, a1, a2, a3;
     if (REPEAT) {
+      float ax[4] = {1.f, 0.f, 0.f, 0.f}, ay[4] = {1.f, 0.f, 0.f, 0.f};
       if (degx)
         ++cnt.proposed;
       else
@@ -637,16 +655,24 @@ __device__ __forceinline__ UpdateCount heatbath_q(const Geometry& gp, float4* U,
       else
         accy = kp_member<REPEAT>(ia.y, s1, w1base, t, key, ntries, cnt.proposed, ay);
       if (!(accx || accy)) continue;
+      a0 = make_float2(ax[0], ay[0]);
+      a1 = make_float2(ax[1], ay[1]);
+      a2 = make_float2(ax[2], ay[2]);
+      a3 = make_float2(ax[3], ay[3]);
     } else {
       // a degenerate member draws nothing in the single-site update; here its
       // draws are made and thrown away, which changes no other number
-      accx = kp_member_1hit(ia.x, s0, w1base, t, key, ax) && !degx;
-      accy = kp_member_1hit(ia.y, s1, w1base, t, key, ay) && !degy;
+      float2 a[4];
+      kp_pair_1hit(ia, s0, s1, w1base, t, key, accx, accy, a);
+      accx = accx && !degx;
+      accy = accy && !degy;
       cnt.proposed += 2;
+      a0 = a[0];
+      a1 = a[1];
+      a2 = a[2];
+      a3 = a[3];
     }
     cnt.accepted += (int)accx + (int)accy;
-    const float2 a0 = make_float2(ax[0], ay[0]), a1 = make_float2(ax[1], ay[1]);
-    const float2 a2 = make_float2(ax[2], ay[2]), a3 = make_float2(ax[3], ay[3]);
     const float2 v0 = qmul(r0, ik), v1 = qmul(r1, ik), v2 = qmul(r2, ik), v3 = qmul(r3, ik);
     // R = Y V^+, Y = m(a), V = m(v), m(q) = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]]
     const qcx y00 = qmk(a0, a3), y01 = qmk(a2, a1);

@@ -67,11 +67,11 @@ __device__ __forceinline__ pm3 load_pm3_l(const float4* __restrict__ U, int mu, 
       for (int k = 0; k < 3; ++k) m.re[k] = m.im[k] = make_float2(0.f, 0.f);
       return m;
     }
-    const float* b = (const float*)(U + link_base(mu, p, Vp, 6) + (h - half * Vp)) + half;
+    const float* b = (const float*)(U + pair_offset(mu, p, h - half * Vp, Vp)) + half;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const float* e0 = b + (size_t)4 * k * Vp;        // entry (row 0, column k)
-      const float* e1 = b + (size_t)4 * (3 + k) * Vp;  // entry (row 1, column k)
+      const float* e0 = b + 4 * kPairTile * k;        // entry (row 0, column k)
+      const float* e1 = b + 4 * kPairTile * (3 + k);  // entry (row 1, column k)
       m.re[k] = make_float2(CG ? __ldcg(e0) : __ldg(e0), CG ? __ldcg(e1) : __ldg(e1));
       m.im[k] = make_float2(CG ? __ldcg(e0 + 2) : __ldg(e0 + 2), CG ? __ldcg(e1 + 2) : __ldg(e1 + 2));
     }
@@ -91,22 +91,22 @@ __device__ __forceinline__ void load_pair_site(const float4* __restrict__ U, int
     return;
   }
   const int half = h >= Vp ? 1 : 0;
-  const float* b = (const float*)(U + link_base(mu, p, Vp, 6) + (h - half * Vp)) + half;
+  const float* b = (const float*)(U + pair_offset(mu, p, h - half * Vp, Vp)) + half;
 #pragma unroll
   for (int e = 0; e < 6; ++e) {
-    r[6 * (e / 3) + 2 * (e % 3)] = __ldg(b + (size_t)4 * e * Vp);
-    r[6 * (e / 3) + 2 * (e % 3) + 1] = __ldg(b + (size_t)4 * e * Vp + 2);
+    r[6 * (e / 3) + 2 * (e % 3)] = __ldg(b + 4 * kPairTile * e);
+    r[6 * (e / 3) + 2 * (e % 3) + 1] = __ldg(b + 4 * kPairTile * e + 2);
   }
 }
 
 __device__ __forceinline__ void store_pair_site(float4* U, int mu, int p, int h, int Vp, const float r[12]) {
   if (!link_ok(mu, p, h, 2LL * Vp)) return;
   const int half = h >= Vp ? 1 : 0;
-  float* b = (float*)(U + link_base(mu, p, Vp, 6) + (h - half * Vp)) + half;
+  float* b = (float*)(U + pair_offset(mu, p, h - half * Vp, Vp)) + half;
 #pragma unroll
   for (int e = 0; e < 6; ++e) {
-    b[(size_t)4 * e * Vp] = r[6 * (e / 3) + 2 * (e % 3)];
-    b[(size_t)4 * e * Vp + 2] = r[6 * (e / 3) + 2 * (e % 3) + 1];
+    b[4 * kPairTile * e] = r[6 * (e / 3) + 2 * (e % 3)];
+    b[4 * kPairTile * e + 2] = r[6 * (e / 3) + 2 * (e % 3) + 1];
   }
 }
 

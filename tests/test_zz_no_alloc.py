@@ -28,14 +28,18 @@ def device_layout(U, L, precision):
             soa[:, p] = sel.transpose(1, 2, 0, 3)
     elif L[3] % 4 == 0:
         # site pairs (h, h + V/4): entry e = 3 row + col of pair j holds
-        # (re u(h), re u(h + V/4), im u(h), im u(h + V/4))
+        # (re u(h), re u(h + V/4), im u(h), im u(h + V/4)); pairs in tiles of
+        # 32 (the last one padded), a tile's six entries one after another
         Vp = V // 4
-        soa = np.empty((4, 2, 6, Vp, 4), dtype=np.float32)
+        nt = (Vp + 31) // 32
+        soa = np.zeros((4, 2, nt, 6, 32, 4), dtype=np.float32)
         for p in (0, 1):
             rows01 = flat[parity == bool(p)][:, :, :2]  # (h, mu, row, col, re/im)
             a, b = rows01[:Vp], rows01[Vp:]
             quad = np.stack([a[..., 0], b[..., 0], a[..., 1], b[..., 1]], axis=-1)  # (j, mu, row, col, 4)
-            soa[:, p] = quad.transpose(1, 2, 3, 0, 4).reshape(4, 6, Vp, 4).astype(np.float32)
+            ent = np.zeros((nt * 32, 4, 6, 4), dtype=np.float32)
+            ent[:Vp] = quad.reshape(Vp, 4, 6, 4)
+            soa[:, p] = ent.reshape(nt, 32, 4, 6, 4).transpose(2, 0, 3, 1, 4)
     else:
         soa = np.empty((4, 2, 3, V // 2, 4), dtype=np.float32)
         for p in (0, 1):
@@ -49,9 +53,10 @@ def device_layout(U, L, precision):
 # equal up to the summation of the partials) and against the oracle (FP64:
 # rounding order; FP32 stores: the FP32 rounding of the plaquette products,
 # ~1e-7 per plaquette)
-# (8, 6, 4, 10): FP32 stores one site per column group; (8, 6, 4, 8): L3 a
-# multiple of 4, FP32 stores site pairs
-@pytest.mark.parametrize("L", [(8, 6, 4, 10), (8, 6, 4, 8)])
+# (8, 6, 4, 10): FP32 stores one site per column group; (8, 6, 4, 8) and
+# (6, 6, 6, 4): L3 a multiple of 4, FP32 stores site pairs (384 pairs per
+# (mu, parity): twelve whole tiles; 216: the last tile padded)
+@pytest.mark.parametrize("L", [(8, 6, 4, 10), (8, 6, 4, 8), (6, 6, 6, 4)])
 @pytest.mark.parametrize("precision,tol,tol_oracle", [(su3.SU3_FP64, 1e-13, 1e-13),
                                                       (su3.SU3_FP32_MIXED, 1e-12, 2e-6),
                                                       (su3.SU3_FP32_EFT, 1e-12, 2e-6)])
