@@ -212,14 +212,17 @@ SU3_API int su3_set_lanes(su3_handle h, int lanes);
  *     (su3_sweep_debug); if one runs out, the sweep stops and the next
  *     synchronising call returns SU3_ETIMEOUT;
  *   SU3_SCHED_PER_DIRECTION: the same tiles in four persistent launches, one
- *     per direction mu with its even and odd half-sweeps (each launch runs the
- *     update code of one direction; tails remain between directions);
+ *     per direction mu with its even and odd half-sweeps, so that each
+ *     launch runs the update code of one direction; launches 1-3 are
+ *     programmatic dependent launches whose tiles start while the previous
+ *     direction drains and wait, as inside a launch, for the layers they
+ *     read;
  *   SU3_SCHED_AUTO (the default): SU3_SCHED_PER_DIRECTION where the
- *     persistent forms apply and one half-sweep is 2 to 5 waves of the GPU,
- *     w = (V/4 pairs) / (512 x SMs) (32^4: +2.4 % FP32-mixed, +0.3 % FP32-EFT
- *     against eight launches), else eight half-sweep kernels (fastest from
- *     32^3 x 64, 40^4, 48^4 on, and on small lattices whose half-sweep is in
- *     flight at once; 24^4 alone ran faster in one launch: +7 %, +12 %).
+ *     persistent forms apply and one half-sweep is 1 to 5 waves of the GPU,
+ *     w = (V/4 pairs) / (512 x SMs) (24^4: +8 % FP32-mixed, +13 % FP32-EFT;
+ *     32^4: +8 %, +4.6 % against eight launches), else eight half-sweep
+ *     kernels (fastest from 40^4 and 48^4 on, and on small lattices whose
+ *     half-sweep is in flight at once).
  * su3_sweep_measured always runs the eight kernels (its measuring update
  * variants would make the persistent kernel spill).
  * Results do not depend on it, bit for bit.  SU3_EINVAL for an unknown value,

@@ -182,16 +182,15 @@ double half_sweep_waves(const su3_lattice* h) {
 }
 
 // SU3_SCHED_AUTO by the number of waves of a half-sweep, after measurements
-// on GB300 (FP32-mixed / FP32-EFT, against eight launches): 32^4 (3.4 waves)
-// per direction +2.4 / +0.3 %, one launch +1.2 / +0.1 %; from 32^3 x 64 (6.7
-// waves) on, and at 40^4 and 48^4, eight launches are fastest (per direction
-// -0.6 to -6 %).  Below 2 waves the result depends on the x3 layers: 24^4
-// (1.1 waves, 12 layers) one launch +7 / +12 %, but 24^3 x 16 (0.7 waves, 8
-// layers) -28 / -27 % and 16^4 -55 / -57 %, where a whole half-sweep is in
-// flight at once and the tiles of the next one wait on it: eight launches.
+// on GB300 of the chained per-direction launches (FP32-mixed / FP32-EFT,
+// against eight launches): 24^4 (1.1 waves) +8 / +13 %, 32^4 (3.4 waves)
+// +8 / +4.6 %; 32^3 x 64 (6.7 waves) +0.3 / -1.2 %, 40^4 -2.2 / -1.8 %, 48^4
+// -5.9 / -4.6 %: eight launches from 5 waves on.  Under one wave a whole
+// half-sweep is in flight at once and the tiles of the next one wait on it:
+// 24^3 x 16 (0.7 waves) -38 %, 16^4 (0.2 waves) -62 %: eight launches.
 int auto_schedule(const su3_lattice* h) {
   const double w = half_sweep_waves(h);
-  return w >= 2.0 && w < 5.0 ? SU3_SCHED_PER_DIRECTION : SU3_SCHED_PHASES;
+  return w >= 1.0 && w < 5.0 ? SU3_SCHED_PER_DIRECTION : SU3_SCHED_PHASES;
 }
 
 bool use_persistent(const su3_lattice* h, bool measured = false) {

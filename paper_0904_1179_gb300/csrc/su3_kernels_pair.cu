@@ -121,6 +121,16 @@ cudaError_t launch_pair_mu(const HalfSweepArgs& a, bool stats, int threads, cuda
 // loads (lanes 0-2 of warp 0), then thread 0 issues one acquire fence and a
 // block barrier passes it on -- one acquire per tile, because an acquire also
 // drops the SM's L1 lines, which the staging ring (cp.async.ca) relies on.
+//
+// Per direction: four launches per sweep, launch mu holding phases 2 mu and
+// 2 mu + 1 (one update variant per launch).  Launches 1-3 are chained to the
+// one before by programmatic dependent launch: every block signals
+// griddepcontrol.launch_dependents as it starts, so the next launch's blocks
+// may be scheduled once all blocks of this one have started, and its first
+// phase waits on the layer counts of this one's last phase exactly as the
+// phases inside a launch do.  Nothing of a launch waits for a later launch,
+// and a later launch's blocks start only when every block of the earlier one
+// is running or done, so the chain cannot deadlock either.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
@@ -155,7 +165,7 @@ __device__ __forceinline__ UpdateCount pair_item(const HalfSweepArgs& args, int 
 // MUSEL = -1: the eight half-sweeps of the sweep in one launch; MUSEL = 0..3:
 // the two half-sweeps (even, odd sites) of direction MUSEL, one launch per
 // direction, so that a launch runs a single update variant (the code of one
-// direction) and its first half-sweep waits for nothing.
+// direction); its first half-sweep waits on the previous launch's last.
 template <int MUSEL, bool EFT, bool REPEAT>
 __global__ void __launch_bounds__(256, 2)
     k_sweep_f32_pair(HalfSweepArgs args, PairSweepQueue qa, int tiles_per_layer, int layers, int stats) {
@@ -164,6 +174,7 @@ __global__ void __launch_bounds__(256, 2)
   constexpr int kPhases = MUSEL < 0 ? 8 : 2, kFirst = MUSEL < 0 ? 0 : 2 * MUSEL;
   const int tiles_per_phase = tiles_per_layer * layers;
   unsigned* const done = qa.counters + kPairSweepTickets;
+  if (MUSEL >= 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (threadIdx.x < 32) {
     const int lane = (int)threadIdx.x;
     int idx = 0;
@@ -178,7 +189,7 @@ __global__ void __launch_bounds__(256, 2)
       tile = layer * tiles_per_layer + (i - il * tiles_per_layer);
     }
     bool ok = phase >= 0 && (lane != 0 || ld_relaxed_s32(qa.status) == 0);
-    const bool wait = phase > kFirst;  // the launch's first half-sweep follows the previous launch
+    const bool wait = phase > 0;  // phase 0 follows the previous sweep (stream order)
     if (wait && lane < 3) {
       // lane k waits for layer l + k - 1 of the previous phase
       const int lk = layer + lane - 1 < 0 ? layers - 1 : (layer + lane - 1 == layers ? 0 : layer + lane - 1);
@@ -247,10 +258,22 @@ cudaError_t launch_sweep(const HalfSweepArgs& a, const PairSweepQueue& q, int tp
   }
   const int blocks = 2 * tpl * layers;
   k_sweep_f32_pair<0, EFT, REPEAT><<<blocks, threads, smem, s>>>(a, q, tpl, layers, st);
-  k_sweep_f32_pair<1, EFT, REPEAT><<<blocks, threads, smem, s>>>(a, q, tpl, layers, st);
-  k_sweep_f32_pair<2, EFT, REPEAT><<<blocks, threads, smem, s>>>(a, q, tpl, layers, st);
-  k_sweep_f32_pair<3, EFT, REPEAT><<<blocks, threads, smem, s>>>(a, q, tpl, layers, st);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // directions 1-3: programmatic dependent launches (see the section comment)
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if ((e = cudaLaunchKernelEx(&cfg, k_sweep_f32_pair<1, EFT, REPEAT>, a, q, tpl, layers, st)) != cudaSuccess) return e;
+  if ((e = cudaLaunchKernelEx(&cfg, k_sweep_f32_pair<2, EFT, REPEAT>, a, q, tpl, layers, st)) != cudaSuccess) return e;
+  return cudaLaunchKernelEx(&cfg, k_sweep_f32_pair<3, EFT, REPEAT>, a, q, tpl, layers, st);
 }
 
 template <typename F>

@@ -143,9 +143,11 @@ def test_persistent_sweep_matches_oracle_reading(prec):
 
 
 def test_automatic_schedule_follows_the_waves():
-    # 16^4: 0.2 waves per half-sweep, eight launches; 32^4: 3.4, one launch
-    # per direction; 32^3 x 64: 6.7, eight launches
-    for L, sched in (((16, 16, 16, 16), su3.SU3_SCHED_PHASES), ((32, 32, 32, 32), su3.SU3_SCHED_PER_DIRECTION),
+    # 16^4: 0.2 waves per half-sweep and 24^3 x 16: 0.7, eight launches;
+    # 24^4: 1.1 and 32^4: 3.4, one launch per direction; 32^3 x 64: 6.7,
+    # eight launches (waves on a GPU of 152 SMs)
+    for L, sched in (((16, 16, 16, 16), su3.SU3_SCHED_PHASES), ((24, 24, 24, 16), su3.SU3_SCHED_PHASES),
+                     ((24, 24, 24, 24), su3.SU3_SCHED_PER_DIRECTION), ((32, 32, 32, 32), su3.SU3_SCHED_PER_DIRECTION),
                      ((32, 32, 32, 64), su3.SU3_SCHED_PHASES)):
         with su3.Lattice(L, BETA, 1, precision=su3.SU3_FP32_MIXED) as lat:
             assert lat.schedule == sched, L
@@ -183,14 +185,20 @@ def test_schedule_applies_where_documented():
 
 # Fault detection without a fault: a work item that never reports completion
 # makes the waits on it run out (0.2 s), the sweep stops, su3_status reports
-# SU3_ETIMEOUT once, and the context keeps working.
+# SU3_ETIMEOUT once, and the context keeps working.  Item 0 is the first tile
+# of phase 0 (mu = 0, even sites), waited on inside the launch; item 128 (the
+# lattice's 16^4 / 4 / 128 = 128 tiles per phase) the first tile of phase 1
+# (mu = 0, odd sites), which in the per-direction form is waited on only by
+# the next launch, the programmatic dependent launch of mu = 1.
+@pytest.mark.parametrize("item", [0, 128])
 @pytest.mark.parametrize("sched", SCHEDS)
-def test_withheld_tile_times_out_without_fault(sched):
+def test_withheld_tile_times_out_without_fault(sched, item):
     L = (16, 16, 16, 16)
     with su3.Lattice(L, BETA, 2, precision=su3.SU3_FP32_MIXED) as lat:
+        lat.set_block_size(128)
         lat.set_schedule(sched)
         assert lat.schedule == sched
-        lat.debug(0.2, withhold_item=0)  # the first tile of phase 0 (mu = 0, even sites)
+        lat.debug(0.2, withhold_item=item)
         lat.sweep(1)
         with pytest.raises(su3.Su3Error) as e:
             lat.status()
