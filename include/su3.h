@@ -216,13 +216,15 @@ SU3_API int su3_set_lanes(su3_handle h, int lanes);
  *     launch runs the update code of one direction; launches 1-3 are
  *     programmatic dependent launches whose tiles start while the previous
  *     direction drains and wait, as inside a launch, for the layers they
- *     read;
- *   SU3_SCHED_AUTO (the default): SU3_SCHED_PER_DIRECTION where the
- *     persistent forms apply and one half-sweep is 1 to 5 waves of the GPU,
- *     w = (V/4 pairs) / (512 x SMs) (24^4: +8 % FP32-mixed, +13 % FP32-EFT;
- *     32^4: +8 %, +4.6 % against eight launches), else eight half-sweep
- *     kernels (fastest from 40^4 and 48^4 on, and on small lattices whose
- *     half-sweep is in flight at once).
+ *     read.  Applies also to FP64 stores (one thread per link, tiles of
+ *     sites of one x3 layer: L0*L1*L2/2 a whole number of blocks, L3 >= 4);
+ *   SU3_SCHED_AUTO (the default): SU3_SCHED_PER_DIRECTION where it applies
+ *     and one half-sweep is 1 to 5 waves of the GPU, w = (V/4 pairs) /
+ *     (512 x SMs) for the site-paired FP32 store and (V/2 links) /
+ *     (384 x SMs) for FP64 (FP32 24^4: +8 % mixed, +13 % EFT; 32^4: +8 %,
+ *     +4.6 %; FP64 24^4: +5 %, against eight launches), else eight
+ *     half-sweep kernels (equal or faster from 5 waves on, and on small
+ *     lattices whose half-sweep is in flight at once).
  * su3_sweep_measured always runs the eight kernels (its measuring update
  * variants would make the persistent kernel spill).
  * Results do not depend on it, bit for bit.  SU3_EINVAL for an unknown value,

@@ -166,28 +166,39 @@ HalfSweepArgs half_sweep_args(const su3_lattice* h, int parity) {
   return a;
 }
 
-// Whether the sweep runs as one persistent launch (su3k_launch_sweep_pair):
-// the site-paired FP32 store, one lane per link, and a pair lattice whose x3
-// layers are whole tiles.
-bool persistent_applies(const su3_lattice* h) {
+// Whether the sweep can run as persistent launches: the site-paired FP32
+// store with one lane per link and a pair lattice whose x3 layers are whole
+// tiles (one launch per sweep or one per direction, su3k_launch_sweep_pair);
+// or the FP64 store with one lane per link and x3 layers of whole tiles (one
+// launch per direction, su3k_launch_sweep_f64).
+bool pair_persistent_applies(const su3_lattice* h) {
   int tpl = 0;
   return h->pairs && !h->split && su3k_pair_sweep_layers(h->pgeom, h->threads, &tpl) > 0;
 }
+bool f64_persistent_applies(const su3_lattice* h) {
+  int tpl = 0;
+  return h->precision == SU3_FP64 && !h->split && su3k_f64_sweep_layers(h->geom, h->threads, &tpl) > 0;
+}
+bool persistent_applies(const su3_lattice* h) { return pair_persistent_applies(h) || f64_persistent_applies(h); }
 
-// Waves of the GPU in one half-sweep of the paired store (about 512 threads,
-// one pair each, resident per SM at 128 registers).
+// Waves of the GPU in one half-sweep: site pairs at about 512 threads per SM
+// (128 registers), FP64 links at 384 (3 warps of 136-142 registers per
+// scheduler).
 double half_sweep_waves(const su3_lattice* h) {
   const int sms = sm_count();
-  return sms > 0 ? (double)h->pgeom.Vh / (512.0 * sms) : 1e9;
+  if (sms <= 0) return 1e9;
+  return h->pairs ? (double)h->pgeom.Vh / (512.0 * sms) : (double)h->geom.Vh / (384.0 * sms);
 }
 
 // SU3_SCHED_AUTO by the number of waves of a half-sweep, after measurements
-// on GB300 of the chained per-direction launches (FP32-mixed / FP32-EFT,
-// against eight launches): 24^4 (1.1 waves) +8 / +13 %, 32^4 (3.4 waves)
+// on GB300 of the chained per-direction launches against eight launches.
+// FP32-mixed / FP32-EFT: 24^4 (1.1 waves) +8 / +13 %, 32^4 (3.4 waves)
 // +8 / +4.6 %; 32^3 x 64 (6.7 waves) +0.3 / -1.2 %, 40^4 -2.2 / -1.8 %, 48^4
-// -5.9 / -4.6 %: eight launches from 5 waves on.  Under one wave a whole
-// half-sweep is in flight at once and the tiles of the next one wait on it:
-// 24^3 x 16 (0.7 waves) -38 %, 16^4 (0.2 waves) -62 %: eight launches.
+// -5.9 / -4.6 %.  FP64: 24^4 (2.8 waves) +5.1 %, 32^4 (9 waves), 40^4 and
+// 48^4 +0.3 to +0.4 %.  So eight launches from 5 waves on.  Under one wave a
+// whole half-sweep is in flight at once and the tiles of the next one wait on
+// it: FP32 24^3 x 16 (0.7 waves) -38 %, 16^4 (0.2 waves) -62 %; FP64 16^4
+// (0.6 waves) -31 %: eight launches.
 int auto_schedule(const su3_lattice* h) {
   const double w = half_sweep_waves(h);
   return w >= 1.0 && w < 5.0 ? SU3_SCHED_PER_DIRECTION : SU3_SCHED_PHASES;
@@ -209,7 +220,7 @@ bool per_direction(const su3_lattice* h) {
 // outside any stream capture).
 int ensure_pair_queue(su3_lattice* h) {
   if (h->d_pq) return SU3_OK;
-  const int words = su3k_pair_sweep_words(h->pgeom.L3);
+  const int words = su3k_sweep_words(h->pairs ? h->pgeom.L3 : h->geom.L3);
   cudaError_t e;
   if ((e = cudaMalloc(&h->d_pq, (size_t)words * sizeof(unsigned int))) != cudaSuccess ||
       (e = cudaMalloc(&h->d_pstatus, sizeof(int))) != cudaSuccess ||
@@ -236,12 +247,15 @@ int enqueue_sweep_body(su3_lattice* h, bool measured) {
   const int blocks = su3k_half_sweep_blocks(half_sweep_args(h, 1), h->precision, h->threads);
   if (use_persistent(h, measured)) {
     const HalfSweepArgs a = half_sweep_args(h, 0);
-    const PairSweepQueue q{h->d_pq, h->d_pstatus, h->pq_wait_ns, h->pq_withhold};
+    const SweepQueue q{h->d_pq, h->d_pstatus, h->pq_wait_ns, h->pq_withhold};
     SU3_CUDA(cudaMemsetAsync(h->d_pq, 0, (size_t)h->pq_words * sizeof(unsigned int), h->stream),
              "sweep counters reset");
-    SU3_CUDA(su3k_launch_sweep_pair(a, q, h->precision == SU3_FP32_EFT, h->stats_on, h->threads, per_direction(h),
-                                    h->stream),
-             "persistent sweep launch");
+    if (h->precision == SU3_FP64)
+      SU3_CUDA(su3k_launch_sweep_f64(a, q, h->stats_on, h->threads, h->stream), "persistent sweep launch");
+    else
+      SU3_CUDA(su3k_launch_sweep_pair(a, q, h->precision == SU3_FP32_EFT, h->stats_on, h->threads, per_direction(h),
+                                      h->stream),
+               "persistent sweep launch");
   } else {
     for (int mu = 0; mu < 4; ++mu)
       for (int p = 0; p < 2; ++p) {
@@ -655,10 +669,12 @@ int su3_set_schedule(su3_handle h, int schedule) {
   if (schedule != SU3_SCHED_AUTO && schedule != SU3_SCHED_PHASES && schedule != SU3_SCHED_PERSISTENT &&
       schedule != SU3_SCHED_PER_DIRECTION)
     return fail(SU3_EINVAL, "su3_set_schedule: unknown schedule %d", schedule);
-  if ((schedule == SU3_SCHED_PERSISTENT || schedule == SU3_SCHED_PER_DIRECTION) && !persistent_applies(h))
+  if ((schedule == SU3_SCHED_PERSISTENT && !pair_persistent_applies(h)) ||
+      (schedule == SU3_SCHED_PER_DIRECTION && !persistent_applies(h)))
     return fail(SU3_EINVAL,
-                "su3_set_schedule: the persistent sweep needs the site-paired FP32 store, one thread per pair, "
-                "L3 >= 8, layers of whole blocks and the natural block order");
+                "su3_set_schedule: the persistent sweep needs one thread per link (pair) and x3 layers of whole blocks: "
+                "the site-paired FP32 store (L3 >= 8, the natural block order; one launch or one per direction) or "
+                "the FP64 store (L3 >= 4; one launch per direction)");
   if (schedule != h->schedule) {
     SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_set_schedule");
     drop_graphs(h);

@@ -13,6 +13,7 @@
 
 #include "su3_device.cuh"
 #include "su3_sitepair.cuh"
+#include "su3_sweepq.cuh"
 #include "su3_update.cuh"
 
 using namespace su3dev;
@@ -71,6 +72,31 @@ __global__ void __launch_bounds__(kMaxSweepThreads) k_half_sweep_f64(HalfSweepAr
   }
   count_stats<STATS>(c, args.stats);
   if (MEAS) block_partial(m, args.meas);
+}
+
+// The FP64 sweep as four persistent launches, one per direction MU with its
+// even and odd half-sweeps, chained by programmatic dependent launch
+// (su3_sweepq.cuh): a block takes a tile of `threads` sites of one parity in
+// one x3 layer of the lattice and waits only for the layers of the previous
+// half-sweep that its staples read, so one half-sweep's last wave overlaps
+// the next one's first and only one launch tail per sweep remains.  The
+// links change while the launch runs, so they are read through L2 (CG); the
+// update is that of k_half_sweep_f64, bit for bit.
+template <int MU, bool REPEAT>
+__global__ void __launch_bounds__(kMaxSweepThreads)
+    k_sweep_f64(HalfSweepArgs args, SweepQueue qa, int tiles_per_layer, int layers, int stats) {
+  __shared__ SweepItem s_item;
+  signal_dependents();
+  take_sweep_item<2, 2 * MU>(qa, MU, tiles_per_layer, layers, &s_item);
+  __syncthreads();
+  const SweepItem it = s_item;
+  if (it.phase < 0) return;
+  const UpdateConsts uc{args.three_over_beta_f64, args.three_over_beta, args.max_tries};
+  const int h = it.tile * (int)blockDim.x + (int)threadIdx.x;  // layers are whole tiles: always a site of the lattice
+  const UpdateCount c =
+      update_link_f64<MU, true, REPEAT, false>(args.geom, (double2*)args.links, h, it.phase & 1, *args.sweep, args.key, uc);
+  if (stats) count_stats<true>(c, args.stats);
+  report_sweep_item(qa, layers, it);
 }
 
 // A small lattice's half-sweep has too few links to fill the GPU, and each
@@ -461,6 +487,29 @@ __global__ void k_store_to_canon(ConvArgs args) {
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
+template <bool REPEAT>
+static cudaError_t launch_sweep_f64(const HalfSweepArgs& a, const SweepQueue& q, int tpl, int layers, bool stats,
+                                    int threads, cudaStream_t s) {
+  const int blocks = 2 * tpl * layers, st = stats ? 1 : 0;
+  k_sweep_f64<0, REPEAT><<<blocks, threads, 0, s>>>(a, q, tpl, layers, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // directions 1-3: programmatic dependent launches (su3_sweepq.cuh)
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if ((e = cudaLaunchKernelEx(&cfg, k_sweep_f64<1, REPEAT>, a, q, tpl, layers, st)) != cudaSuccess) return e;
+  if ((e = cudaLaunchKernelEx(&cfg, k_sweep_f64<2, REPEAT>, a, q, tpl, layers, st)) != cudaSuccess) return e;
+  return cudaLaunchKernelEx(&cfg, k_sweep_f64<3, REPEAT>, a, q, tpl, layers, st);
+}
+
 template <int MU, bool STATS, bool EFT, bool REPEAT, bool MEAS>
 static cudaError_t launch_f32(const HalfSweepArgs& a, int blocks, int threads, cudaStream_t s) {
   k_half_sweep_f32<MU, STATS, EFT, REPEAT, MEAS><<<blocks, threads, 0, s>>>(a);
@@ -522,6 +571,21 @@ static cudaError_t launch_half_sweep_mu(const HalfSweepArgs& a, int precision, b
                   : launch_prec<MU, true, false, false>(a, precision, blocks, threads, s);
   return repeat ? launch_prec<MU, false, true, false>(a, precision, blocks, threads, s)
                 : launch_prec<MU, false, false, false>(a, precision, blocks, threads, s);
+}
+
+int su3k_f64_sweep_layers(const Geometry& g, int threads, int* tiles_per_layer) {
+  const long long per_layer = (long long)g.hL0 * g.L1 * g.L2;  // sites of one parity in one x3 layer
+  if (threads <= 0 || threads > kMaxSweepThreads || per_layer % threads != 0 || g.L3 < 4) return 0;
+  *tiles_per_layer = (int)(per_layer / threads);
+  return g.L3;
+}
+
+cudaError_t su3k_launch_sweep_f64(const HalfSweepArgs& a, const SweepQueue& q, bool stats, int threads, cudaStream_t s) {
+  int tpl = 0;
+  const int layers = su3k_f64_sweep_layers(a.geom, threads, &tpl);
+  if (layers == 0 || a.meas || a.split) return cudaErrorInvalidValue;
+  return a.max_tries > 1 ? launch_sweep_f64<true>(a, q, tpl, layers, stats, threads, s)
+                         : launch_sweep_f64<false>(a, q, tpl, layers, stats, threads, s);
 }
 
 cudaError_t su3k_launch_half_sweep(const HalfSweepArgs& a, int mu, int precision, bool stats, int threads, cudaStream_t s) {

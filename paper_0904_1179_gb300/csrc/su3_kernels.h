@@ -72,32 +72,41 @@ int su3k_pair_tile2(const su3dev::Geometry& gp, int threads);
 constexpr int kPairRingBytesPerThread = 3 * 7 * 16;
 cudaError_t su3k_prepare();
 
-// The persistent site-paired FP32 sweep (su3_kernels_pair.cu): all eight
-// half-sweeps of one sweep in one launch, one block per work item.  Work items
-// are tiles of `threads` pairs; a tile of phase q starts once phase q-1 has
-// finished the x3 layers of the pair lattice its staples reach (its own layer
-// and the two beside it).
-struct PairSweepQueue {
+// The persistent sweeps (su3_sweepq.cuh): the half-sweeps of one sweep as
+// tiles of one block each, handed out in order from a device counter; a tile
+// of phase q starts once phase q-1 has finished the x3 layers its staples
+// reach (its own layer and the two beside it).  Site-paired FP32
+// (su3_kernels_pair.cu): x3 layers of the pair lattice, tiles of `threads`
+// pairs; FP64 (su3_kernels.cu): x3 layers of the lattice, tiles of `threads`
+// sites of one parity.
+struct SweepQueue {
   unsigned int* counters;  // [0]: next work item of a one-launch sweep, [mu]: of direction mu's launch;
-                           // [kPairSweepTickets + q * layers + l]: tiles of phase q done in layer l; zeroed before each sweep
-  int* status;             // 0, or kPairSweepTimeout once a bounded wait ran out (then every block stops)
+                           // [kSweepTickets + q * layers + l]: tiles of phase q done in layer l; zeroed before each sweep
+  int* status;             // 0, or kSweepTimeout once a bounded wait ran out (then every block stops)
   long long wait_ns;       // bound of one wait
   int withhold;            // fault-injection hook: this work item never reports completion (-1: none)
 };
-constexpr int kPairSweepTimeout = 1;
-constexpr int kPairSweepTickets = 4;
+constexpr int kSweepTimeout = 1;
+constexpr int kSweepTickets = 4;
 // Layers of the pair lattice for the persistent sweep with blocks of
 // `threads`, or 0 where it does not apply (a layer is not a whole number of
 // tiles, fewer than four layers, or a block order other than the natural
 // one); *tiles_per_layer is set with it.
 int su3k_pair_sweep_layers(const su3dev::Geometry& gp, int threads, int* tiles_per_layer);
-// Counter words for a pair lattice of `layers` layers.
-inline int su3k_pair_sweep_words(int layers) { return kPairSweepTickets + 8 * layers; }
+// The same for the FP64 store of lattice g (layers of L0 L1 L2 / 2 sites per
+// parity; at least four).
+int su3k_f64_sweep_layers(const su3dev::Geometry& g, int threads, int* tiles_per_layer);
+// Counter words for a lattice of `layers` layers.
+inline int su3k_sweep_words(int layers) { return kSweepTickets + 8 * layers; }
 // One sweep: one launch, or (per_direction) four, one per direction mu with
-// its two half-sweeps.  a.parity is unused; a.meas must be null (sweeps that
-// measure the plaquette run the eight half-sweep kernels).
-cudaError_t su3k_launch_sweep_pair(const HalfSweepArgs& a, const PairSweepQueue& q, bool eft, bool stats, int threads,
+// its two half-sweeps, chained by programmatic dependent launch.  a.parity is
+// unused; a.meas must be null (sweeps that measure the plaquette run the
+// eight half-sweep kernels).
+cudaError_t su3k_launch_sweep_pair(const HalfSweepArgs& a, const SweepQueue& q, bool eft, bool stats, int threads,
                                    bool per_direction, cudaStream_t s);
+// The FP64 sweep as four chained per-direction launches (k_sweep_f64), one
+// thread per link, loads through L2 (the links change during the launch).
+cudaError_t su3k_launch_sweep_f64(const HalfSweepArgs& a, const SweepQueue& q, bool stats, int threads, cudaStream_t s);
 
 // Status words of the bounds-checked build, one per translation unit with
 // kernels (su3_device.cuh, link_ok); 0 in the product build.

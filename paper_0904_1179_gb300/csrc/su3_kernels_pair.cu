@@ -12,6 +12,7 @@
 #include "su3_kernels.h"
 
 #include "su3_sitepair.cuh"
+#include "su3_sweepq.cuh"
 
 using namespace su3dev;
 
@@ -101,49 +102,11 @@ cudaError_t launch_pair_mu(const HalfSweepArgs& a, bool stats, int threads, cuda
 // The persistent sweep.  Each of the eight half-sweep launches of a sweep
 // leaves its SMs partly idle while its last blocks drain and the next launch
 // ramps up (at 32^4, 3.4 waves of 152 SMs x 4 blocks, the SMs hold no warp
-// for about a tenth of each launch).  Here one launch holds the tiles of all
-// eight half-sweeps, handed out phase by phase from one counter; the tiles of
-// phase q walk the x3 layers of the pair lattice starting one layer further
-// than those of phase q-1, and a tile waits only for the three layers of
-// phase q-1 its staples reach (neighbours x +- nu move x3 by at most one; on
-// the pair lattice a step across the x3 boundary stays in a neighbouring
-// layer).  When a tile of phase q is taken, phase q-1 has handed out all its
-// tiles and those layers were among its first three, so in practice nothing
-// waits, and the next phase fills the SMs while the previous one drains.
-// Completed layers of phase q-1 imply completed layers of every earlier
-// phase around them (each tile waited for its own predecessors before it
-// ran), which also keeps a tile from overwriting links that a still-running
-// earlier tile reads.  The results are those of the per-phase launches bit
-// for bit: the same update of the same links from the same inputs.
-//
-// Ordering: a block reports its tile with one release reduction by thread 0
-// after a block barrier; a waiting block polls the three counts with relaxed
-// loads (lanes 0-2 of warp 0), then thread 0 issues one acquire fence and a
-// block barrier passes it on -- one acquire per tile, because an acquire also
-// drops the SM's L1 lines, which the staging ring (cp.async.ca) relies on.
-//
-// Per direction: four launches per sweep, launch mu holding phases 2 mu and
-// 2 mu + 1 (one update variant per launch).  Launches 1-3 are chained to the
-// one before by programmatic dependent launch: every block signals
-// griddepcontrol.launch_dependents as it starts, so the next launch's blocks
-// may be scheduled once all blocks of this one have started, and its first
-// phase waits on the layer counts of this one's last phase exactly as the
-// phases inside a launch do.  Nothing of a launch waits for a later launch,
-// and a later launch's blocks start only when every block of the earlier one
-// is running or done, so the chain cannot deadlock either.
+// for about a tenth of each launch).  Here the tiles of the half-sweeps are
+// handed out from a device counter, each waiting only for the x3 layers of
+// the pair lattice that its staples read (su3_sweepq.cuh; on the pair
+// lattice a step across the x3 boundary stays in a neighbouring layer).
 // ---------------------------------------------------------------------------
-
-__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 template <int MU, bool EFT, bool REPEAT>
 __device__ __forceinline__ UpdateCount pair_item(const HalfSweepArgs& args, int j, int p, uint64_t t,
@@ -151,12 +114,9 @@ __device__ __forceinline__ UpdateCount pair_item(const HalfSweepArgs& args, int 
   return update_pair_f32_rolled<MU, true, EFT, REPEAT>(args.pgeom, (float4*)args.links, j, p, t, args.key, uc, rg);
 }
 
-// One block per tile of the sweep (8 x tiles per phase blocks).  A block
-// takes its work item from the counter, not from blockIdx, so items are handed
-// out in order to blocks that are running: every item a block waits for is
-// held by a running block or done, and the lowest item in flight never waits,
-// so the order cannot deadlock however many blocks are resident.  (A loop of
-// items per persistent block would let the compiler keep loop-invariant
+// One block per tile of the sweep (8 x tiles per phase blocks), its work item
+// taken from the queue (su3_sweepq.cuh).  (A loop of items per persistent
+// block would let the compiler keep loop-invariant
 // values of the four update variants in registers across the loop, and the
 // update spills; one item per block keeps the per-phase kernel's registers.)
 // Sweeps that measure the plaquette run the eight half-sweep kernels: the
@@ -168,62 +128,20 @@ __device__ __forceinline__ UpdateCount pair_item(const HalfSweepArgs& args, int 
 // direction); its first half-sweep waits on the previous launch's last.
 template <int MUSEL, bool EFT, bool REPEAT>
 __global__ void __launch_bounds__(256, 2)
-    k_sweep_f32_pair(HalfSweepArgs args, PairSweepQueue qa, int tiles_per_layer, int layers, int stats) {
+    k_sweep_f32_pair(HalfSweepArgs args, SweepQueue qa, int tiles_per_layer, int layers, int stats) {
   extern __shared__ float4 smem[];
-  __shared__ int s_tile, s_phase, s_layer, s_idx;
+  __shared__ SweepItem s_item;
   constexpr int kPhases = MUSEL < 0 ? 8 : 2, kFirst = MUSEL < 0 ? 0 : 2 * MUSEL;
-  const int tiles_per_phase = tiles_per_layer * layers;
-  unsigned* const done = qa.counters + kPairSweepTickets;
-  if (MUSEL >= 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  if (threadIdx.x < 32) {
-    const int lane = (int)threadIdx.x;
-    int idx = 0;
-    if (lane == 0) idx = (int)atomicAdd(qa.counters + (MUSEL < 0 ? 0 : MUSEL), 1u);
-    idx = __shfl_sync(0xffffffffu, idx, 0);
-    int phase = -1, tile = 0, layer = 0;
-    if (idx < kPhases * tiles_per_phase) {
-      phase = kFirst + idx / tiles_per_phase;
-      const int i = idx - (phase - kFirst) * tiles_per_phase;
-      const int il = i / tiles_per_layer;
-      layer = (il + phase) % layers;
-      tile = layer * tiles_per_layer + (i - il * tiles_per_layer);
-    }
-    bool ok = phase >= 0 && (lane != 0 || ld_relaxed_s32(qa.status) == 0);
-    const bool wait = phase > 0;  // phase 0 follows the previous sweep (stream order)
-    if (wait && lane < 3) {
-      // lane k waits for layer l + k - 1 of the previous phase
-      const int lk = layer + lane - 1 < 0 ? layers - 1 : (layer + lane - 1 == layers ? 0 : layer + lane - 1);
-      const unsigned* cnt = done + (phase - 1) * layers + lk;
-      unsigned long long t0 = 0;
-      while (ok && ld_relaxed_u32(cnt) < (unsigned)tiles_per_layer) {
-        if (t0 == 0) t0 = global_ns();
-        if (ld_relaxed_s32(qa.status) != 0) {
-          ok = false;
-        } else if (global_ns() - t0 > (unsigned long long)qa.wait_ns) {
-          atomicCAS(qa.status, 0, kPairSweepTimeout);
-          ok = false;
-        } else {
-          __nanosleep(64);
-        }
-      }
-    }
-    ok = __all_sync(0xffffffffu, ok);
-    if (lane == 0) {
-      if (ok && wait) fence_acquire_gpu();
-      s_phase = ok ? phase : -1;
-      s_tile = tile;
-      s_layer = layer;
-      s_idx = idx;
-    }
-  }
+  if (MUSEL >= 0) signal_dependents();
+  take_sweep_item<kPhases, kFirst>(qa, MUSEL < 0 ? 0 : MUSEL, tiles_per_layer, layers, &s_item);
   __syncthreads();
-  const int phase = s_phase, tile = s_tile;
-  if (phase < 0) return;
+  const SweepItem it = s_item;
+  if (it.phase < 0) return;
   const UpdateConsts uc{args.three_over_beta_f64, args.three_over_beta, args.max_tries};
   const PairRing rg = pair_ring(smem);
   const uint64_t t = *args.sweep;
-  const int mu = phase >> 1, p = phase & 1;
-  const int j = tile * (int)blockDim.x + (int)threadIdx.x;  // layers are whole tiles: always a pair of the lattice
+  const int mu = it.phase >> 1, p = it.phase & 1;
+  const int j = it.tile * (int)blockDim.x + (int)threadIdx.x;  // layers are whole tiles: always a pair of the lattice
   UpdateCount c;
   if (MUSEL >= 0) {
     c = pair_item<(MUSEL < 0 ? 0 : MUSEL), EFT, REPEAT>(args, j, p, t, uc, rg);
@@ -243,12 +161,11 @@ __global__ void __launch_bounds__(256, 2)
       atomicAdd(&args.stats[1], (unsigned long long)prop);
     }
   }
-  __syncthreads();  // every thread's stores are issued before the tile is reported
-  if (threadIdx.x == 0 && s_idx != qa.withhold) red_release_add(done + phase * layers + s_layer, 1u);
+  report_sweep_item(qa, layers, it);
 }
 
 template <bool EFT, bool REPEAT>
-cudaError_t launch_sweep(const HalfSweepArgs& a, const PairSweepQueue& q, int tpl, int layers, bool stats, int threads,
+cudaError_t launch_sweep(const HalfSweepArgs& a, const SweepQueue& q, int tpl, int layers, bool stats, int threads,
                          bool per_direction, cudaStream_t s) {
   const size_t smem = (size_t)kPairRingBytesPerThread * threads;
   const int st = stats ? 1 : 0;
@@ -341,7 +258,7 @@ int su3k_pair_sweep_layers(const Geometry& gp, int threads, int* tiles_per_layer
   return gp.L3;
 }
 
-cudaError_t su3k_launch_sweep_pair(const HalfSweepArgs& a, const PairSweepQueue& q, bool eft, bool stats, int threads,
+cudaError_t su3k_launch_sweep_pair(const HalfSweepArgs& a, const SweepQueue& q, bool eft, bool stats, int threads,
                                    bool per_direction, cudaStream_t s) {
   int tpl = 0;
   const int layers = su3k_pair_sweep_layers(a.pgeom, threads, &tpl);

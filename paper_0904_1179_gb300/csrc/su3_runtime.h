@@ -57,7 +57,7 @@ struct su3_lattice {
   int schedule = 0;                  // SU3_SCHED_AUTO, SU3_SCHED_PHASES or SU3_SCHED_PERSISTENT
   unsigned int* d_pq = nullptr;      // its work counter and per-(phase, layer) completion counts
   int pq_words = 0;
-  int* d_pstatus = nullptr;          // kPairSweepTimeout after a wait ran out
+  int* d_pstatus = nullptr;          // kSweepTimeout after a wait ran out
   int* h_pstatus = nullptr;          // pinned
   long long pq_wait_ns = 2000000000LL;
   int pq_withhold = -1;

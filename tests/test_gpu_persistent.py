@@ -1,5 +1,6 @@
-"""The persistent sweep (su3_set_schedule: one kernel per sweep) against the
-eight half-sweep kernels and against the oracle.
+"""The persistent sweeps (su3_set_schedule: one kernel per sweep, or one per
+direction; FP64 one per direction) against the eight half-sweep kernels and
+against the oracle.
 
 The persistent kernel applies the per-link update of the half-sweep kernels to
 the same inputs: a tile of a half-sweep starts only after the previous
@@ -65,6 +66,36 @@ def test_persistent_sweep_equals_eight_kernels(L, lanes, prec, sched):
         assert np.array_equal(a.get_links(), b.get_links())
         assert a.stats() == b.stats()
         assert a.sweep_count == b.sweep_count == 3
+
+
+# FP64, one launch per direction: 8^3 x 4 (4 layers of 2 tiles of 128),
+# 12^3 x 8 (8 layers of 864 sites: 27 tiles of 32), 16^4, 32^4 (the bench
+# lattice: 32 layers of 128 tiles of 128); one thread per link (the
+# four-lane form of the smallest lattices is switched off).
+@pytest.mark.parametrize("L,threads", [((8, 8, 8, 4), 128), ((12, 12, 12, 8), 32), ((16, 16, 16, 16), 0),
+                                       ((32, 32, 32, 32), 0)])
+def test_fp64_per_direction_equals_eight_kernels(L, threads):
+    a, b = pair(L, su3.SU3_FP64, 23, lanes=1, threads=threads, schedule=su3.SU3_SCHED_PER_DIRECTION)
+    with a, b:
+        for lat in (a, b):
+            lat.set_stats(True)
+            lat.sweep(3)
+            lat.status()
+        assert np.array_equal(a.get_links(), b.get_links())
+        assert a.stats() == b.stats()
+
+
+def test_fp64_per_direction_matches_oracle():
+    L = (8, 8, 8, 8)
+    with su3.Lattice(L, BETA, 31, start=su3.SU3_HOT, precision=su3.SU3_FP64) as lat:
+        lat.set_lanes(1)
+        lat.set_block_size(64)
+        lat.set_schedule(su3.SU3_SCHED_PER_DIRECTION)
+        U0 = lat.get_links()
+        lat.sweep(1)
+        U1 = lat.get_links()
+    oracle.sweep(L, BETA, 31, 0, 1, U0)  # in place: sweep t = 0 of the same chain
+    assert np.abs(U1 - U0).max() < 1e-12
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -151,20 +182,32 @@ def test_automatic_schedule_follows_the_waves():
                      ((32, 32, 32, 64), su3.SU3_SCHED_PHASES)):
         with su3.Lattice(L, BETA, 1, precision=su3.SU3_FP32_MIXED) as lat:
             assert lat.schedule == sched, L
+    # FP64 (384 links per SM in flight): 16^4 0.6 waves, 24^4 2.8, 32^4 9.0
+    for L, sched in (((16, 16, 16, 16), su3.SU3_SCHED_PHASES), ((24, 24, 24, 24), su3.SU3_SCHED_PER_DIRECTION),
+                     ((32, 32, 32, 32), su3.SU3_SCHED_PHASES)):
+        with su3.Lattice(L, BETA, 1, precision=su3.SU3_FP64) as lat:
+            assert lat.schedule == sched, L
 
 
 def test_schedule_applies_where_documented():
-    # FP64, a layer that is not a whole number of blocks (10 x 20 x 20 = 4000
+    # a layer that is not a whole number of blocks (10 x 20 x 20 = 4000
     # pairs, 128 threads), a lattice below 4 layers (L3 = 4), the four-lane
-    # kernel: the eight kernels, and SU3_SCHED_PERSISTENT is refused
-    for L, prec in (((16, 16, 16, 16), su3.SU3_FP64), ((20, 20, 20, 16), su3.SU3_FP32_MIXED),
-                    ((16, 16, 16, 4), su3.SU3_FP32_MIXED), ((8, 8, 8, 8), su3.SU3_FP32_EFT)):
+    # kernel: the eight kernels, and both persistent schedules are refused
+    for L, prec in (((20, 20, 20, 16), su3.SU3_FP32_MIXED), ((16, 16, 16, 4), su3.SU3_FP32_MIXED),
+                    ((8, 8, 8, 8), su3.SU3_FP32_EFT), ((8, 8, 8, 8), su3.SU3_FP64)):
         with su3.Lattice(L, BETA, 1, precision=prec) as lat:
             assert lat.schedule == su3.SU3_SCHED_PHASES, L
             for sched in SCHEDS:
                 with pytest.raises(su3.Su3Error) as e:
                     lat.set_schedule(sched)
                 assert e.value.code == su3.SU3_EINVAL
+    # FP64: one launch per direction only
+    with su3.Lattice((16, 16, 16, 16), BETA, 1, precision=su3.SU3_FP64) as lat:
+        with pytest.raises(su3.Su3Error) as e:
+            lat.set_schedule(su3.SU3_SCHED_PERSISTENT)
+        assert e.value.code == su3.SU3_EINVAL
+        lat.set_schedule(su3.SU3_SCHED_PER_DIRECTION)
+        assert lat.schedule == su3.SU3_SCHED_PER_DIRECTION
     with su3.Lattice((16, 16, 16, 16), BETA, 1, precision=su3.SU3_FP32_MIXED) as lat:
         with pytest.raises(su3.Su3Error):
             lat.set_schedule(7)
@@ -191,10 +234,16 @@ def test_schedule_applies_where_documented():
 # (mu = 0, odd sites), which in the per-direction form is waited on only by
 # the next launch, the programmatic dependent launch of mu = 1.
 @pytest.mark.parametrize("item", [0, 128])
-@pytest.mark.parametrize("sched", SCHEDS)
-def test_withheld_tile_times_out_without_fault(sched, item):
+@pytest.mark.parametrize("sched,prec", [(su3.SU3_SCHED_PERSISTENT, su3.SU3_FP32_MIXED),
+                                        (su3.SU3_SCHED_PER_DIRECTION, su3.SU3_FP32_MIXED),
+                                        (su3.SU3_SCHED_PER_DIRECTION, su3.SU3_FP64)])
+def test_withheld_tile_times_out_without_fault(sched, prec, item):
+    # FP64: 16^4 / 2 / 128 = 256 tiles per phase, so item 128 lies in phase 0
+    # too (waited on inside the launch); item 256 is the first of phase 1
     L = (16, 16, 16, 16)
-    with su3.Lattice(L, BETA, 2, precision=su3.SU3_FP32_MIXED) as lat:
+    if prec == su3.SU3_FP64 and item:
+        item = 256
+    with su3.Lattice(L, BETA, 2, precision=prec) as lat:
         lat.set_block_size(128)
         lat.set_schedule(sched)
         assert lat.schedule == sched
