@@ -83,34 +83,34 @@ def peaks():
 # stripped).  A line reports the figure only while that code still hashes the
 # same; otherwise its traffic is null and the line says why.
 _U_F64, _U_F32, _U_BATCH = ("su3_kernels.cu",), ("su3_kernels.cu", "su3_kernels_pair.cu"), ("su3_batch.cu",)
-_SHA_F64 = "48be9e23f569b94eb791d1af49fb19b7634a715695394eae81722bc525618667"
-_SHA_F32 = "887b6728cab8e701c3fc89494f50578773d4d929a00da5384dcb8bfecd5fac49"
-_SHA_BATCH = "5779843dda7303c1d3f222fa9ae2348752f0e8e80e170234be794c73a493f851"
+_SHA_F64 = "ce1ad7fc7b0cad21bbafe14d30eaa2670bedf711664835805d27385c4aa695b7"
+_SHA_F32 = "6563943ce31cb7116153c8475450555ab8238d9ff8b16a9ad8b3006ebd2fdecf"
+_SHA_BATCH = "fcb232bac6768fa1373d26311882a17dfdac6dc88e5cdf5f8b77f691969088e3"
 _NCU_METRICS = "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none"
 NCU_TRAFFIC = {
     # one launch of the default 32^4 FP32 sweep = one direction's two half-sweeps; the mean of the four
     # launches (mu = 0..3) of the second sweep
-    "fp32_mixed": {"bytes": 417740608 + 38512832, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_mixed": {"bytes": 417781568 + 38488960, "units": _U_F32, "sources_sha256": _SHA_F32,
                    "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 4 -c 4 python bench.py --profile fp32_mixed"},
-    "fp32_eft": {"bytes": 417833728 + 39475072, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_eft": {"bytes": 417805760 + 39486016, "units": _U_F32, "sources_sha256": _SHA_F32,
                  "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 4 -c 4 python bench.py --profile fp32_eft"},
-    "fp32_mixed_onelaunch": {"bytes": 1667349248 + 193181184, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_mixed_onelaunch": {"bytes": 1667384832 + 193136128, "units": _U_F32, "sources_sha256": _SHA_F32,
                              "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 1 -c 1 python bench.py --profile "
                                                        "fp32_mixed_onelaunch"},
-    "fp32_eft_onelaunch": {"bytes": 1668716544 + 193986816, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_eft_onelaunch": {"bytes": 1668767488 + 193925376, "units": _U_F32, "sources_sha256": _SHA_F32,
                            "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 1 -c 1 python bench.py --profile "
                                                      "fp32_eft_onelaunch"},
-    "fp32_mixed_phases": {"bytes": 207847424 + 14747392, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_mixed_phases": {"bytes": 207860224 + 14739200, "units": _U_F32, "sources_sha256": _SHA_F32,
                           "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile "
                                                     "fp32_mixed_phases"},
-    "fp32_eft_phases": {"bytes": 207865600 + 15510016, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_eft_phases": {"bytes": 207870720 + 15619840, "units": _U_F32, "sources_sha256": _SHA_F32,
                         "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile "
                                                   "fp32_eft_phases"},
-    "fp64": {"bytes": 621661184 + 64540928, "units": _U_F64, "sources_sha256": _SHA_F64,
+    "fp64": {"bytes": 624128000 + 64891392, "units": _U_F64, "sources_sha256": _SHA_F64,
              "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile fp64"},
-    "batched": {"bytes": 3033250304 + 488768256, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
+    "batched": {"bytes": 3033241088 + 488295424, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
                 "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 1 -c 1 python bench.py --profile batched"},
-    "batched_eft": {"bytes": 3033292800 + 488601856, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
+    "batched_eft": {"bytes": 3033286656 + 489709056, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
                     "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 1 -c 1 python bench.py --profile batched_eft"},
 }
 
