@@ -295,8 +295,11 @@ SU3_API int su3_decomp_info(su3_handle h, int* ndmpi, int* mpifactor, int* lbcex
 /* ---------------------------------------------------------------------------
  * Batches: n independent replicas, each with its own extents, beta and Philox
  * seed (the same counter layout, keyed by the replica's seed), swept together
- * by ONE kernel launch per sweep (one block per tile of a replica's
- * half-sweep, tiles taken in phase order), captured in a CUDA graph.  Each
+ * by four kernel launches per sweep, one per direction mu with the even and
+ * odd half-sweeps of every replica (one block per tile of a replica's
+ * half-sweep, tiles taken in phase order; launches 1-3 are programmatic
+ * dependent launches that start while the one before drains), captured in a
+ * CUDA graph.  Each
  * replica performs exactly the single-lattice sweep: replica r after k sweeps
  * equals a lattice created alone with dims[r], betas[r], seeds[r] after k
  * sweeps, bit for bit.
@@ -315,9 +318,9 @@ SU3_API int su3_batch_create(int n, const int (*dims)[4], const double* betas, c
                              int precision, void* cuda_stream, su3_handle* out);
 
 /* nsweeps sweeps of every replica; asynchronous, one graph replay (memset of
- * the arrival counters, the sweep kernel, the sweep-counter increment) per
- * sweep.  Inside the kernel, a tile of phase k of replica r
- * waits for all tiles of phase k-1 of r; the wait is bounded in time and, if
+ * the arrival counters, the four per-direction sweep kernels, the
+ * sweep-counter increment) per sweep.  A tile of phase k of replica r
+ * waits for all tiles of phase k-1 of r, in its own launch or the one before; the wait is bounded in time and, if
  * it runs out, the sweep stops and the next synchronising call returns
  * SU3_ETIMEOUT (the configuration is then incomplete). */
 SU3_API int su3_batch_sweep(su3_handle b, int nsweeps);
@@ -355,7 +358,8 @@ SU3_API int su3_batch_autotune(su3_handle b, int* threads, int* blocks_per_sm, i
 
 /* Fault-detection hook.  wait_limit_s (0 < limit <= 60) bounds each wait of
  * the batched sweep (default 2 s); withhold_item >= 0 makes that work item
- * (in dispatch order) never signal its completion, so that the waits on it
+ * (in the dispatch order of each direction's launch, which numbers its items
+ * from 0) never signal its completion, so that the waits on it
  * run out -- the way to test SU3_ETIMEOUT without faulting the GPU.  -1
  * disables withholding. */
 SU3_API int su3_batch_debug(su3_handle b, double wait_limit_s, int withhold_item);

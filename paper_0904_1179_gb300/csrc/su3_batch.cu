@@ -69,27 +69,15 @@ struct BatchArgs {
   int max_tries;      // SU(2) proposals per subgroup (1: one-hit heatbath)
 };
 
-template <typename T, bool EFT, bool REPEAT>
-__device__ __forceinline__ void update_item(int mu, const ReplicaDesc& rd, void* links, int h, int p, uint64_t t,
-                                            int max_tries) {
+// The update of link (h, MU) of a replica: one direction per launch (the
+// sweep's four launches each run one direction's code).
+template <typename T, bool EFT, bool REPEAT, int MU>
+__device__ __forceinline__ void update_item(const ReplicaDesc& rd, void* links, int h, int p, uint64_t t, int max_tries) {
   const UpdateConsts uc{rd.three_over_beta_f64, rd.three_over_beta, max_tries};
-  if constexpr (std::is_same<T, double>::value) {
-    double2* U = (double2*)links + rd.offset;
-    switch (mu) {
-      case 0: update_link_f64<0, true, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
-      case 1: update_link_f64<1, true, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
-      case 2: update_link_f64<2, true, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
-      default: update_link_f64<3, true, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
-    }
-  } else {
-    float4* U = (float4*)links + rd.offset;
-    switch (mu) {
-      case 0: update_link_f32<0, true, EFT, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
-      case 1: update_link_f32<1, true, EFT, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
-      case 2: update_link_f32<2, true, EFT, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
-      default: update_link_f32<3, true, EFT, REPEAT>(rd.g, U, h, p, t, rd.key, uc); break;
-    }
-  }
+  if constexpr (std::is_same<T, double>::value)
+    update_link_f64<MU, true, REPEAT>(rd.g, (double2*)links + rd.offset, h, p, t, rd.key, uc);
+  else
+    update_link_f32<MU, true, EFT, REPEAT>(rd.g, (float4*)links + rd.offset, h, p, t, rd.key, uc);
 }
 
 // Register budget of the FP32 instances: __launch_bounds__(threads, blocks per SM).
@@ -112,10 +100,18 @@ struct ParamReplicas {
   ReplicaDesc r[kParamReplicas];
 };
 
-// One work item (replica, phase, tile) of the sweep; reps: the descriptors
-// (kernel parameters or global memory).
-template <typename T, bool EFT, bool REPEAT, bool PARAM>
+// One work item (replica, phase, tile) of direction MU's launch; reps: the
+// descriptors (kernel parameters or global memory).  The sweep is four
+// launches, one per direction MU with the phases 2 MU (even sites) and
+// 2 MU + 1 (odd sites) of every replica; launches 1-3 are programmatic
+// dependent launches, scheduled once every block of the launch before has
+// started: a tile of phase 2 MU waits for its replica's phase 2 MU - 1 of the
+// launch before, as a tile of phase 2 MU + 1 waits for phase 2 MU.  Items go
+// out in order within each launch, and a launch's blocks start only when
+// every block of the one before is running or done, so no wait can deadlock.
+template <typename T, bool EFT, bool REPEAT, bool PARAM, int MU>
 __device__ __forceinline__ void batch_item(const BatchArgs& a, const ReplicaDesc* reps) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __shared__ int4 s_item;
   __shared__ int s_stop;
   __shared__ ReplicaDesc s_rep;  // global descriptors: the current item's, copied once per block
@@ -159,7 +155,7 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, const ReplicaDesc
   if (s_stop) return;
   const ReplicaDesc& rd = PARAM ? reps[it.x] : s_rep;
   const int h = it.z * (int)blockDim.x + (int)threadIdx.x;
-  if (h < rd.g.Vh) update_item<T, EFT, REPEAT>(it.y >> 1, rd, a.links, h, it.y & 1, t, a.max_tries);
+  if (h < rd.g.Vh) update_item<T, EFT, REPEAT, MU>(rd, a.links, h, it.y & 1, t, a.max_tries);
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -167,48 +163,66 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, const ReplicaDesc
   }
 }
 
-template <typename T, bool EFT, bool REPEAT>
+template <typename T, bool EFT, bool REPEAT, int MU>
 __global__ void __launch_bounds__(SU3_BATCH_LB_THREADS, std::is_same<T, float>::value ? SU3_BATCH_F32_MINBLOCKS : 1)
     k_batch_sweep(BatchArgs a) {
-  batch_item<T, EFT, REPEAT, false>(a, a.reps);
+  batch_item<T, EFT, REPEAT, false, MU>(a, a.reps);
 }
 
-template <typename T, bool EFT, bool REPEAT>
+template <typename T, bool EFT, bool REPEAT, int MU>
 __global__ void __launch_bounds__(SU3_BATCH_LB_THREADS, std::is_same<T, float>::value ? SU3_BATCH_F32_MINBLOCKS : 1)
     k_batch_sweep_c(const __grid_constant__ BatchArgs a, const __grid_constant__ ParamReplicas pr) {
-  batch_item<T, EFT, REPEAT, true>(a, pr.r);
+  batch_item<T, EFT, REPEAT, true, MU>(a, pr.r);
+}
+
+// Direction MU's launch: a plain launch for MU = 0, a programmatic dependent
+// launch of the one before for MU = 1..3.
+template <typename T, bool EFT, bool REPEAT, int MU>
+cudaError_t launch_mu(const BatchArgs& a, const ParamReplicas* pr, int threads, cudaStream_t s) {
+  if (a.n_items == 0) return cudaSuccess;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.n_items);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = MU > 0 ? 1 : 0;
+  return pr ? cudaLaunchKernelEx(&cfg, k_batch_sweep_c<T, EFT, REPEAT, MU>, a, *pr)
+            : cudaLaunchKernelEx(&cfg, k_batch_sweep<T, EFT, REPEAT, MU>, a);
 }
 
 template <typename T, bool EFT, bool REPEAT>
-void launch_kind(const BatchArgs& a, const ParamReplicas* pr, int threads, cudaStream_t s) {
-  if (pr)
-    k_batch_sweep_c<T, EFT, REPEAT><<<a.n_items, threads, 0, s>>>(a, *pr);
-  else
-    k_batch_sweep<T, EFT, REPEAT><<<a.n_items, threads, 0, s>>>(a);
+cudaError_t launch_kind(const BatchArgs* a, const ParamReplicas* pr, int threads, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = launch_mu<T, EFT, REPEAT, 0>(a[0], pr, threads, s)) != cudaSuccess) return e;
+  if ((e = launch_mu<T, EFT, REPEAT, 1>(a[1], pr, threads, s)) != cudaSuccess) return e;
+  if ((e = launch_mu<T, EFT, REPEAT, 2>(a[2], pr, threads, s)) != cudaSuccess) return e;
+  return launch_mu<T, EFT, REPEAT, 3>(a[3], pr, threads, s);
 }
 
-// One block per work item; pr: the descriptors as kernel parameters (batches
-// of at most kParamReplicas replicas), or null.
-cudaError_t launch_batch(const BatchArgs& a, const ParamReplicas* pr, int precision, int threads, cudaStream_t s) {
-  const bool rep = a.max_tries > 1;
-  if (precision == SU3_FP64) {
-    rep ? launch_kind<double, false, true>(a, pr, threads, s) : launch_kind<double, false, false>(a, pr, threads, s);
-  } else if (precision == SU3_FP32_EFT) {
-    rep ? launch_kind<float, true, true>(a, pr, threads, s) : launch_kind<float, true, false>(a, pr, threads, s);
-  } else {
-    rep ? launch_kind<float, false, true>(a, pr, threads, s) : launch_kind<float, false, false>(a, pr, threads, s);
-  }
-  return cudaGetLastError();
+// The sweep's four launches, a[mu] holding direction mu's work items; one
+// block per work item; pr: the descriptors as kernel parameters (batches of
+// at most kParamReplicas replicas), or null.
+cudaError_t launch_batch(const BatchArgs* a, const ParamReplicas* pr, int precision, int threads, cudaStream_t s) {
+  const bool rep = a[0].max_tries > 1;
+  if (precision == SU3_FP64)
+    return rep ? launch_kind<double, false, true>(a, pr, threads, s) : launch_kind<double, false, false>(a, pr, threads, s);
+  if (precision == SU3_FP32_EFT)
+    return rep ? launch_kind<float, true, true>(a, pr, threads, s) : launch_kind<float, true, false>(a, pr, threads, s);
+  return rep ? launch_kind<float, false, true>(a, pr, threads, s) : launch_kind<float, false, false>(a, pr, threads, s);
 }
 
 int max_blocks_per_sm(int precision, int threads) {
   int n = 0;
   cudaError_t e =
       precision == SU3_FP64
-          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep_c<double, false, false>, threads, 0)
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep_c<double, false, false, 0>, threads, 0)
           : precision == SU3_FP32_EFT
-                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep_c<float, true, false>, threads, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep_c<float, false, false>, threads, 0);
+                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep_c<float, true, false, 0>, threads, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep_c<float, false, false, 0>, threads, 0);
   return e == cudaSuccess ? n : 0;
 }
 
@@ -228,9 +242,9 @@ struct su3_batch {
   size_t elem_bytes = 0;
   ReplicaDesc* d_reps = nullptr;
   std::unique_ptr<ParamReplicas> param_reps;  // the same, as kernel parameters (n <= kParamReplicas)
-  int4* d_schedule = nullptr;
-  int n_items = 0;
-  unsigned* d_sync = nullptr;  // [0] queue, [1 + 8r + k] arrival counters
+  int4* d_schedule = nullptr;  // the work items of directions 0..3, one after another
+  int n_items_mu[4] = {0, 0, 0, 0};
+  unsigned* d_sync = nullptr;  // [mu] queue of direction mu's launch, [4 + 8r + k] arrival counters
   int* d_status = nullptr;
   int* h_status = nullptr;  // pinned
   double* d_plaq_n = nullptr;
@@ -296,13 +310,21 @@ int build_schedule(su3_lattice* h) {
     d.ntiles = tiles_of(d.g, b->threads);
     reps[r] = d;
   }
-  std::vector<int4> items;
+  // dispatch order: windows of replicas, phase-major inside a window; split
+  // by direction (phases 2 mu, 2 mu + 1) into the four launches, each keeping
+  // that order
+  std::vector<int4> by_mu[4];
   const int w = b->window > 0 ? b->window : b->n;
   for (int r0 = 0; r0 < b->n; r0 += w) {
     const int r1 = std::min(b->n, r0 + w);
     for (int k = 0; k < 8; ++k)
       for (int r = r0; r < r1; ++r)
-        for (int tl = 0; tl < reps[r].ntiles; ++tl) items.push_back(make_int4(r, k, tl, 0));
+        for (int tl = 0; tl < reps[r].ntiles; ++tl) by_mu[k >> 1].push_back(make_int4(r, k, tl, 0));
+  }
+  std::vector<int4> items;
+  for (int mu = 0; mu < 4; ++mu) {
+    b->n_items_mu[mu] = (int)by_mu[mu].size();
+    items.insert(items.end(), by_mu[mu].begin(), by_mu[mu].end());
   }
   cudaFree(b->d_schedule);
   b->d_schedule = nullptr;
@@ -315,7 +337,6 @@ int build_schedule(su3_lattice* h) {
     if (!b->param_reps) return fail(SU3_ENOMEM, "batch descriptors: host allocation failed");
     std::copy(reps.begin(), reps.end(), b->param_reps->r);
   }
-  b->n_items = (int)items.size();
   return SU3_OK;
 }
 
@@ -328,19 +349,24 @@ int resident_blocks_per_sm(su3_lattice* h) {
 
 int enqueue_batch_sweep(su3_lattice* h) {
   su3_batch* b = h->batch;
-  SU3_CUDA(cudaMemsetAsync(b->d_sync, 0, (1 + 8 * (size_t)b->n) * sizeof(unsigned), h->stream), "batch counters");
-  BatchArgs a{};
-  a.reps = b->d_reps;
-  a.schedule = b->d_schedule;
-  a.n_items = b->n_items;
-  a.queue = b->d_sync;
-  a.done = b->d_sync + 1;
-  a.status = b->d_status;
-  a.sweep = h->d_sweep;
-  a.links = h->links;
-  a.wait_ns = b->wait_ns;
-  a.withhold_item = b->withhold_item;
-  a.max_tries = h->max_tries;
+  SU3_CUDA(cudaMemsetAsync(b->d_sync, 0, (4 + 8 * (size_t)b->n) * sizeof(unsigned), h->stream), "batch counters");
+  BatchArgs a[4];
+  long long first = 0;
+  for (int mu = 0; mu < 4; ++mu) {
+    a[mu] = BatchArgs{};
+    a[mu].reps = b->d_reps;
+    a[mu].schedule = b->d_schedule + first;
+    a[mu].n_items = b->n_items_mu[mu];
+    a[mu].queue = b->d_sync + mu;
+    a[mu].done = b->d_sync + 4;
+    a[mu].status = b->d_status;
+    a[mu].sweep = h->d_sweep;
+    a[mu].links = h->links;
+    a[mu].wait_ns = b->wait_ns;
+    a[mu].withhold_item = b->withhold_item;
+    a[mu].max_tries = h->max_tries;
+    first += b->n_items_mu[mu];
+  }
   SU3_CUDA(launch_batch(a, b->param_reps.get(), h->precision, b->threads, h->stream), "batch sweep launch");
   SU3_CUDA(su3k_launch_increment(h->d_sweep, 1, h->stream), "sweep counter launch");
   return SU3_OK;
@@ -485,7 +511,7 @@ int su3_batch_create(int n, const int (*dims)[4], const double* betas, const uin
       (e = cudaMalloc(&h->d_partials, (size_t)su3k_plaquette_blocks(gmax) * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&h->d_stage, (size_t)chunk * 72 * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&b->d_reps, (size_t)n * sizeof(ReplicaDesc))) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_sync, (1 + 8 * (size_t)n) * sizeof(unsigned))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_sync, (4 + 8 * (size_t)n) * sizeof(unsigned))) != cudaSuccess ||
       (e = cudaMalloc(&b->d_status, sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc(&b->d_plaq_n, (size_t)n * sizeof(double))) != cudaSuccess ||
       (e = cudaMallocHost(&b->h_status, sizeof(int))) != cudaSuccess ||
