@@ -85,7 +85,7 @@ def peaks():
 _U_F64, _U_F32, _U_BATCH = ("su3_kernels.cu",), ("su3_kernels.cu", "su3_kernels_pair.cu"), ("su3_batch.cu",)
 _SHA_F64 = "ce1ad7fc7b0cad21bbafe14d30eaa2670bedf711664835805d27385c4aa695b7"
 _SHA_F32 = "6563943ce31cb7116153c8475450555ab8238d9ff8b16a9ad8b3006ebd2fdecf"
-_SHA_BATCH = "fcb232bac6768fa1373d26311882a17dfdac6dc88e5cdf5f8b77f691969088e3"
+_SHA_BATCH = "90e590e6418988950392eef43f6199eec6399d26f672b43789d400fa1dd054a6"
 _NCU_METRICS = "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none"
 NCU_TRAFFIC = {
     # one launch of the default 32^4 FP32 sweep = one direction's two half-sweeps; the mean of the four
@@ -108,10 +108,10 @@ NCU_TRAFFIC = {
                                                   "fp32_eft_phases"},
     "fp64": {"bytes": 624128000 + 64891392, "units": _U_F64, "sources_sha256": _SHA_F64,
              "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile fp64"},
-    "batched": {"bytes": 3033241088 + 488295424, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
+    "batched": {"bytes": 2831965440 + 442514432, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
                 "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 4 -c 4 python bench.py --profile batched "
                                           "(the four launches of the second sweep, summed)"},
-    "batched_eft": {"bytes": 3033286656 + 489709056, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
+    "batched_eft": {"bytes": 2836656128 + 441758464, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
                     "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 4 -c 4 python bench.py --profile batched_eft "
                                               "(the four launches of the second sweep, summed)"},
 }

@@ -379,7 +379,7 @@ def links_shape(L):
 
 
 class Batch:
-    """Owning wrapper of a batch handle: n replicas swept by one launch per sweep."""
+    """Owning wrapper of a batch handle: n replicas swept together (four chained launches per sweep)."""
 
     def __init__(self, dims, betas, seeds, start=SU3_HOT, precision=SU3_FP32_MIXED, stream=None):
         self.dims = [tuple(int(x) for x in L) for L in dims]
