@@ -111,9 +111,19 @@ def test_config_batch_runs_and_stays_su3():
             assert np.abs(np.einsum("nki,nkj->nij", M.conj(), M) - np.eye(3)).max() < 5e-7
 
 
-def test_withheld_arrival_times_out_without_fault():
+# The sweep runs four launches, one per direction; launch mu numbers its
+# items from 0, phase 2 mu of every replica first (window = all replicas).
+# Item 0 is the first tile of phase 0 of replica 0, waited on inside launch
+# 0; the item after all phase-0 tiles is the first tile of phase 1 of
+# replica 0, waited on only by phase 2 in the next launch, a programmatic
+# dependent launch.
+@pytest.mark.parametrize("cross_launch", [False, True])
+def test_withheld_arrival_times_out_without_fault(cross_launch):
+    threads = 64
+    first_phase1 = sum(-(-(int(np.prod(L)) // 2) // threads) for L in MIX)
     with su3.Batch(MIX, BETAS, SEEDS, start=su3.SU3_HOT) as b:
-        b.debug(0.2, withhold_item=0)  # the first tile of phase 0 of replica 0 never arrives
+        b.config(threads, 0, 0)
+        b.debug(0.2, withhold_item=first_phase1 if cross_launch else 0)
         b.sweep(1)
         with pytest.raises(su3.Su3Error) as e:
             b.status()
