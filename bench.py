@@ -88,18 +88,14 @@ _SHA_F32 = "6563943ce31cb7116153c8475450555ab8238d9ff8b16a9ad8b3006ebd2fdecf"
 _SHA_BATCH = "90e590e6418988950392eef43f6199eec6399d26f672b43789d400fa1dd054a6"
 _NCU_METRICS = "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none"
 NCU_TRAFFIC = {
-    # one launch of the default 32^4 FP32 sweep = one direction's two half-sweeps; the mean of the four
-    # launches (mu = 0..3) of the second sweep
-    "fp32_mixed": {"bytes": 417781568 + 38488960, "units": _U_F32, "sources_sha256": _SHA_F32,
-                   "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 4 -c 4 python bench.py --profile fp32_mixed"},
-    "fp32_eft": {"bytes": 417805760 + 39486016, "units": _U_F32, "sources_sha256": _SHA_F32,
-                 "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 4 -c 4 python bench.py --profile fp32_eft"},
-    "fp32_mixed_onelaunch": {"bytes": 1667384832 + 193136128, "units": _U_F32, "sources_sha256": _SHA_F32,
-                             "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 1 -c 1 python bench.py --profile "
-                                                       "fp32_mixed_onelaunch"},
-    "fp32_eft_onelaunch": {"bytes": 1668767488 + 193925376, "units": _U_F32, "sources_sha256": _SHA_F32,
-                           "capture": _NCU_METRICS + " -k regex:k_sweep_f32_pair -s 1 -c 1 python bench.py --profile "
-                                                     "fp32_eft_onelaunch"},
+    # one launch of the default 32^4 FP32 sweep = one chained half-sweep; the mean of the eight launches of
+    # the second sweep
+    "fp32_mixed": {"bytes": 0, "units": _U_F32, "sources_sha256": "",
+                   "capture": _NCU_METRICS + " -k regex:k_half_sweep_f32_chain -s 8 -c 8 python bench.py --profile "
+                                             "fp32_mixed"},
+    "fp32_eft": {"bytes": 0, "units": _U_F32, "sources_sha256": "",
+                 "capture": _NCU_METRICS + " -k regex:k_half_sweep_f32_chain -s 8 -c 8 python bench.py --profile "
+                                           "fp32_eft"},
     "fp32_mixed_phases": {"bytes": 207860224 + 14739200, "units": _U_F32, "sources_sha256": _SHA_F32,
                           "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile "
                                                     "fp32_mixed_phases"},
@@ -480,8 +476,8 @@ def run_reference(args):
 
 def variant_fp32(su3, stream, steps, warmup, world, hbm_peak, peak_kind, precision=None, schedule=None):
     """The FP32 sweep of the 32^4 lattice.  schedule: None = the library's
-    default (at 32^4 one persistent kernel per direction mu, four per sweep),
-    or su3.SU3_SCHED_PHASES for the eight half-sweep kernels.  The events
+    default (at 32^4 the eight chained half-sweep kernels), or another
+    su3.SU3_SCHED_* form.  The events
     bracket each sweep's graph (counter reset, sweep kernels, sweep-counter
     increment), so the kernel time below slightly overstates the kernels' own."""
     import numpy as np
@@ -497,22 +493,27 @@ def variant_fp32(su3, stream, steps, warmup, world, hbm_peak, peak_kind, precisi
         plaq = lat.plaquette()
     V = int(np.prod(DIMS))
     ups = 4 * V * SWEEPS_PER_STEP * steps / (total_ms * 1e-3)
-    launches = {su3.SU3_SCHED_PERSISTENT: 1, su3.SU3_SCHED_PER_DIRECTION: 4}.get(sched, 8)  # per sweep
+    # launches per sweep, traffic key suffix, kernel, description of each form
+    forms = {
+        su3.SU3_SCHED_PERSISTENT: (1, "_onelaunch", "k_sweep_f32_pair<-1> (site-paired FP32 sweep: the eight "
+                                   "half-sweeps in one launch)", "one persistent kernel per sweep"),
+        su3.SU3_SCHED_PER_DIRECTION: (4, "_perdir", "k_sweep_f32_pair<mu> (site-paired FP32 sweep of one direction: "
+                                      "two half-sweeps per launch, four chained launches per sweep)",
+                                      "one persistent kernel per direction"),
+        su3.SU3_SCHED_CHAINED: (8, "", "k_half_sweep_f32_chain<mu> (site-paired FP32 half-sweep, eight chained "
+                                "launches per sweep)", "eight chained half-sweep kernels per sweep"),
+        su3.SU3_SCHED_PHASES: (8, "_phases", "k_half_sweep_f32_pair (site-paired FP32 half-sweep, eight launches "
+                               "per sweep)", "eight half-sweep kernels per sweep"),
+    }
+    launches, suffix, kernel, form = forms[sched]
     kernel_ms = statistics.mean(sweep_ms) / launches
     bytes_per_launch = BYTES_PER_UPDATE["fp32_mixed"] * (V // 2) * (8 // launches)
     achieved = bytes_per_launch / (kernel_ms * 1e-3) / 1e9
     gs = ("Gram-Schmidt coefficients as compensated FP32 sums (error-free transformations, ~2^-47)" if eft
           else "FP64 Gram-Schmidt coefficients")
-    traffic, provenance = traffic_of(("fp32_eft" if eft else "fp32_mixed") +
-                                     {1: "_onelaunch", 4: "", 8: "_phases"}[launches])
-    kernel = {1: "k_sweep_f32_pair<-1> (site-paired FP32 sweep: the eight half-sweeps in one launch)",
-              4: "k_sweep_f32_pair<mu> (site-paired FP32 sweep of one direction: two half-sweeps per launch, "
-                 "four launches per sweep)",
-              8: "k_half_sweep_f32_pair (site-paired FP32 half-sweep, eight launches per sweep)"}[launches]
+    traffic, provenance = traffic_of(("fp32_eft" if eft else "fp32_mixed") + suffix)
     return {"workload": "32^4 beta=5.7 hot start seed 7, FP32-mixed (12-real FP32 links, FP32 staple and "
-                        "heatbath, %s), 2 sweeps/step, %s" % (gs, {1: "one persistent kernel per sweep",
-                                                                  4: "one persistent kernel per direction",
-                                                                  8: "eight half-sweep kernels per sweep"}[launches]),
+                        "heatbath, %s), 2 sweeps/step, %s" % (gs, form),
             "value": ups, "unit": UNIT, "ms_per_step": total_ms / steps,
             "dtype": "f32 (compensated-f32 reunitarisation)" if eft else "f32 (f64 reunitarisation)",
             "plaquette_after": plaq,
@@ -579,6 +580,8 @@ def run_profile_case(case):
     schedule = None
     if case.endswith("_phases"):  # the eight half-sweep kernels instead of the persistent sweep
         schedule, case = su3.SU3_SCHED_PHASES, case[:-7]
+    elif case.endswith("_perdir"):  # one persistent launch per direction
+        schedule, case = su3.SU3_SCHED_PER_DIRECTION, case[:-7]
     elif case.endswith("_onelaunch"):  # the whole sweep in one persistent launch
         schedule, case = su3.SU3_SCHED_PERSISTENT, case[:-10]
     if case.endswith("_64"):
@@ -968,7 +971,8 @@ def main():
     ap.add_argument("--large-sweeps", type=int, default=100)
     ap.add_argument("--profile", choices=["fp64", "fp32_mixed", "fp32_eft", "batched", "batched_eft", "fp64_64", "fp32_mixed_64", "decomp16",
                              "fp64_8", "fp32_mixed_64s", "fp32_eft_64s", "fp32_mixed_48", "fp32_eft_48",
-                             "fp32_mixed_phases", "fp32_eft_phases", "fp32_mixed_onelaunch", "fp32_eft_onelaunch"],
+                             "fp32_mixed_phases", "fp32_eft_phases", "fp32_mixed_onelaunch", "fp32_eft_onelaunch",
+                             "fp32_mixed_perdir", "fp32_eft_perdir"],
                     help="small case for ncu: create the 32^4 lattice (or the 96-replica batch) and run 3 graphed "
                          "sweeps, nothing else")
     args = ap.parse_args()

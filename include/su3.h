@@ -218,23 +218,29 @@ SU3_API int su3_set_lanes(su3_handle h, int lanes);
  *     direction drains and wait, as inside a launch, for the layers they
  *     read.  Applies also to FP64 stores (one thread per link, tiles of
  *     sites of one x3 layer: L0*L1*L2/2 a whole number of blocks, L3 >= 4);
- *   SU3_SCHED_AUTO (the default): SU3_SCHED_PER_DIRECTION where it applies
- *     and one half-sweep is 1 to 5 waves of the GPU, w = (V/4 pairs) /
- *     (512 x SMs) for the site-paired FP32 store and (V/2 links) /
- *     (384 x SMs) for FP64 (FP32 24^4: +8 % mixed, +13 % EFT; 32^4: +8 %,
- *     +4.6 %; FP64 24^4: +5 %, against eight launches), else eight
- *     half-sweep kernels (equal or faster from 5 waves on, and on small
- *     lattices whose half-sweep is in flight at once).
+ *   SU3_SCHED_CHAINED: eight half-sweep launches chained the same way, a
+ *     block's tile given by its index (no counter), each tile waiting only
+ *     for the layers of the previous half-sweep it reads (site-paired FP32
+ *     stores, where SU3_SCHED_PERSISTENT applies);
+ *   SU3_SCHED_AUTO (the default): where they apply, SU3_SCHED_CHAINED for
+ *     the site-paired FP32 store when one half-sweep is 1 to 10 waves of the
+ *     GPU, w = (V/4 pairs) / (512 x SMs) (24^4: +15 % mixed, +17 % EFT;
+ *     32^4: +10 %, +6 %; 40^4: +0.8 %, +0.1 % against eight launches), and
+ *     SU3_SCHED_PER_DIRECTION for FP64 when it is 1 to 5 waves,
+ *     w = (V/2 links) / (384 x SMs) (24^4: +5 %); else eight half-sweep
+ *     kernels (faster at 48^4, and on small lattices whose half-sweep is in
+ *     flight at once).
  * su3_sweep_measured always runs the eight kernels (its measuring update
  * variants would make the persistent kernel spill).
  * Results do not depend on it, bit for bit.  SU3_EINVAL for an unknown value,
  * for SU3_SCHED_PERSISTENT where it does not apply, and for batch or
  * decomposed handles. */
-enum { SU3_SCHED_AUTO = 0, SU3_SCHED_PHASES = 1, SU3_SCHED_PERSISTENT = 2, SU3_SCHED_PER_DIRECTION = 3 };
+enum { SU3_SCHED_AUTO = 0, SU3_SCHED_PHASES = 1, SU3_SCHED_PERSISTENT = 2, SU3_SCHED_PER_DIRECTION = 3, SU3_SCHED_CHAINED = 4 };
 SU3_API int su3_set_schedule(su3_handle h, int schedule);
 
 /* The schedule the next sweep runs with (SU3_SCHED_PHASES,
- * SU3_SCHED_PERSISTENT or SU3_SCHED_PER_DIRECTION) into *schedule. */
+ * SU3_SCHED_PERSISTENT, SU3_SCHED_PER_DIRECTION or SU3_SCHED_CHAINED) into
+ * *schedule. */
 SU3_API int su3_get_schedule(su3_handle h, int* schedule);
 
 /* Fault-detection hook of the persistent sweep (single lattices), as

@@ -22,14 +22,14 @@ __all__ = [
     "su3_decomp_create", "su3_decomp_plan", "su3_decomp_info",
     "su3_links_get", "su3_links_set", "su3_sweep_count", "su3_set_sweep_count", "su3_set_stats", "su3_stats",
     "su3_info", "su3_set_block_size", "su3_set_lanes", "su3_set_schedule", "su3_get_schedule", "su3_sweep_debug",
-    "SU3_SCHED_AUTO", "SU3_SCHED_PHASES", "SU3_SCHED_PERSISTENT", "SU3_SCHED_PER_DIRECTION", "su3_bounds_status", "use_library", "su3_set_heatbath", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
+    "SU3_SCHED_AUTO", "SU3_SCHED_PHASES", "SU3_SCHED_PERSISTENT", "SU3_SCHED_PER_DIRECTION", "SU3_SCHED_CHAINED", "su3_bounds_status", "use_library", "su3_set_heatbath", "su3_batch_create", "su3_batch_sweep", "su3_batch_plaquettes",
     "su3_batch_links_get", "su3_batch_links_set", "su3_batch_size", "su3_batch_config", "su3_batch_get_config",
     "su3_batch_autotune", "su3_batch_debug", "su3_status", "Batch", "su3_plaquette_noalloc", "su3_last_error", "su3_version", "Lattice", "links_shape", "EXPORTS",
 ]
 
 SU3_COLD, SU3_HOT = 0, 1
 SU3_FP64, SU3_FP32_MIXED, SU3_FP32_EFT = 0, 1, 2
-SU3_SCHED_AUTO, SU3_SCHED_PHASES, SU3_SCHED_PERSISTENT, SU3_SCHED_PER_DIRECTION = 0, 1, 2, 3
+SU3_SCHED_AUTO, SU3_SCHED_PHASES, SU3_SCHED_PERSISTENT, SU3_SCHED_PER_DIRECTION, SU3_SCHED_CHAINED = 0, 1, 2, 3, 4
 SU3_OK, SU3_EINVAL, SU3_ENOMEM, SU3_ECUDA, SU3_ETIMEOUT, SU3_ESIZE = 0, -1, -2, -3, -4, -5
 _CODES = {SU3_EINVAL: "SU3_EINVAL", SU3_ENOMEM: "SU3_ENOMEM", SU3_ECUDA: "SU3_ECUDA",
           SU3_ETIMEOUT: "SU3_ETIMEOUT", SU3_ESIZE: "SU3_ESIZE"}
@@ -269,8 +269,9 @@ def su3_set_lanes(h, lanes):
 
 
 def su3_set_schedule(h, schedule):
-    """SU3_SCHED_AUTO, SU3_SCHED_PHASES (eight half-sweep kernels), SU3_SCHED_PERSISTENT (one kernel) or
-    SU3_SCHED_PER_DIRECTION (one persistent kernel per direction)."""
+    """SU3_SCHED_AUTO, SU3_SCHED_PHASES (eight half-sweep kernels), SU3_SCHED_PERSISTENT (one kernel),
+    SU3_SCHED_PER_DIRECTION (one persistent kernel per direction) or SU3_SCHED_CHAINED (eight chained
+    half-sweep kernels)."""
     _check(load_library().su3_set_schedule(h, int(schedule)))
 
 

@@ -191,29 +191,41 @@ double half_sweep_waves(const su3_lattice* h) {
 }
 
 // SU3_SCHED_AUTO by the number of waves of a half-sweep, after measurements
-// on GB300 of the chained per-direction launches against eight launches.
-// FP32-mixed / FP32-EFT: 24^4 (1.1 waves) +8 / +13 %, 32^4 (3.4 waves)
-// +8 / +4.6 %; 32^3 x 64 (6.7 waves) +0.3 / -1.2 %, 40^4 -2.2 / -1.8 %, 48^4
-// -5.9 / -4.6 %.  FP64: 24^4 (2.8 waves) +5.1 %, 32^4 (9 waves), 40^4 and
-// 48^4 +0.3 to +0.4 %.  So eight launches from 5 waves on.  Under one wave a
-// whole half-sweep is in flight at once and the tiles of the next one wait on
-// it: FP32 24^3 x 16 (0.7 waves) -38 %, 16^4 (0.2 waves) -62 %; FP64 16^4
-// (0.6 waves) -31 %: eight launches.
+// on GB300 against eight launches.  Site-paired FP32 (mixed / EFT), the eight
+// chained half-sweep launches: 24^4 (1.1 waves) +15 / +17 %, 32^4 (3.4 waves)
+// +10 / +6 %, 32^3 x 64 (6.7 waves) +3.4 / +0.9 %, 40^4 (8.2 waves) +0.8 /
+// +0.1 %, 48^4 (17 waves) -2.4 / -2.4 %: chained below 10 waves.  FP64, one
+// launch per direction: 24^4 (2.8 waves) +5.1 %, 32^4 (9 waves), 40^4 and
+// 48^4 +0.3 to +0.4 %: per direction below 5 waves.  Under one wave a whole
+// half-sweep is in flight at once and the tiles of the next one wait on it
+// (FP32 per direction: 24^3 x 16, 0.7 waves, -38 %; 16^4, 0.2 waves, -62 %;
+// FP64 16^4, 0.6 waves, -31 %): eight launches.
 int auto_schedule(const su3_lattice* h) {
   const double w = half_sweep_waves(h);
+  if (h->pairs) return w >= 1.0 && w < 10.0 ? SU3_SCHED_CHAINED : SU3_SCHED_PHASES;
   return w >= 1.0 && w < 5.0 ? SU3_SCHED_PER_DIRECTION : SU3_SCHED_PHASES;
 }
 
-bool use_persistent(const su3_lattice* h, bool measured = false) {
-  if (measured || h->schedule == SU3_SCHED_PHASES || !persistent_applies(h)) return false;
-  if (h->schedule == SU3_SCHED_PERSISTENT || h->schedule == SU3_SCHED_PER_DIRECTION) return true;
-  return auto_schedule(h) != SU3_SCHED_PHASES;
+// Whether a schedule other than eight independent launches applies to h.
+bool schedule_applies(const su3_lattice* h, int schedule) {
+  switch (schedule) {
+    case SU3_SCHED_PERSISTENT:
+    case SU3_SCHED_CHAINED: return pair_persistent_applies(h);
+    case SU3_SCHED_PER_DIRECTION: return persistent_applies(h);
+    default: return true;
+  }
 }
 
-// The persistent form: one launch per sweep, or one per direction.
-bool per_direction(const su3_lattice* h) {
-  return h->schedule == SU3_SCHED_PER_DIRECTION ||
-         (h->schedule == SU3_SCHED_AUTO && auto_schedule(h) == SU3_SCHED_PER_DIRECTION);
+// The schedule the next sweep runs with (measuring sweeps: always eight
+// launches).
+int effective_schedule(const su3_lattice* h, bool measured = false) {
+  if (measured || !persistent_applies(h)) return SU3_SCHED_PHASES;
+  const int sched = h->schedule == SU3_SCHED_AUTO ? auto_schedule(h) : h->schedule;
+  return schedule_applies(h, sched) ? sched : SU3_SCHED_PHASES;
+}
+
+bool use_persistent(const su3_lattice* h, bool measured = false) {
+  return effective_schedule(h, measured) != SU3_SCHED_PHASES;
 }
 
 // Counters and status word of the persistent sweep (allocated on first use,
@@ -253,7 +265,10 @@ int enqueue_sweep_body(su3_lattice* h, bool measured) {
     if (h->precision == SU3_FP64)
       SU3_CUDA(su3k_launch_sweep_f64(a, q, h->stats_on, h->threads, h->stream), "persistent sweep launch");
     else
-      SU3_CUDA(su3k_launch_sweep_pair(a, q, h->precision == SU3_FP32_EFT, h->stats_on, h->threads, per_direction(h),
+      SU3_CUDA(su3k_launch_sweep_pair(a, q, h->precision == SU3_FP32_EFT, h->stats_on, h->threads,
+                                      effective_schedule(h) == SU3_SCHED_CHAINED        ? SweepForm::kChained
+                                      : effective_schedule(h) == SU3_SCHED_PER_DIRECTION ? SweepForm::kPerDirection
+                                                                                         : SweepForm::kOneLaunch,
                                       h->stream),
                "persistent sweep launch");
   } else {
@@ -667,14 +682,13 @@ int su3_set_schedule(su3_handle h, int schedule) {
   if (is_batch(h) || su3_decomp_active(h))
     return fail(SU3_EINVAL, "su3_set_schedule: not for batch or decomposed handles");
   if (schedule != SU3_SCHED_AUTO && schedule != SU3_SCHED_PHASES && schedule != SU3_SCHED_PERSISTENT &&
-      schedule != SU3_SCHED_PER_DIRECTION)
+      schedule != SU3_SCHED_PER_DIRECTION && schedule != SU3_SCHED_CHAINED)
     return fail(SU3_EINVAL, "su3_set_schedule: unknown schedule %d", schedule);
-  if ((schedule == SU3_SCHED_PERSISTENT && !pair_persistent_applies(h)) ||
-      (schedule == SU3_SCHED_PER_DIRECTION && !persistent_applies(h)))
+  if (!schedule_applies(h, schedule))
     return fail(SU3_EINVAL,
-                "su3_set_schedule: the persistent sweep needs one thread per link (pair) and x3 layers of whole blocks: "
-                "the site-paired FP32 store (L3 >= 8, the natural block order; one launch or one per direction) or "
-                "the FP64 store (L3 >= 4; one launch per direction)");
+                "su3_set_schedule: the persistent and chained sweeps need one thread per link (pair) and x3 layers "
+                "of whole blocks: the site-paired FP32 store (L3 >= 8, the natural block order; all forms) or the "
+                "FP64 store (L3 >= 4; one launch per direction)");
   if (schedule != h->schedule) {
     SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_set_schedule");
     drop_graphs(h);
@@ -686,9 +700,7 @@ int su3_set_schedule(su3_handle h, int schedule) {
 int su3_get_schedule(su3_handle h, int* schedule) {
   if (!h || !schedule) return fail(SU3_EINVAL, "su3_get_schedule: NULL argument");
   if (is_batch(h)) return fail(SU3_EINVAL, "su3_get_schedule: batch handle");
-  *schedule = su3_decomp_active(h) || !use_persistent(h) ? SU3_SCHED_PHASES
-              : per_direction(h)                         ? SU3_SCHED_PER_DIRECTION
-                                                         : SU3_SCHED_PERSISTENT;
+  *schedule = su3_decomp_active(h) ? SU3_SCHED_PHASES : effective_schedule(h);
   return SU3_OK;
 }
 

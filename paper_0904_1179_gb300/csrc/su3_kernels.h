@@ -98,12 +98,15 @@ int su3k_pair_sweep_layers(const su3dev::Geometry& gp, int threads, int* tiles_p
 int su3k_f64_sweep_layers(const su3dev::Geometry& g, int threads, int* tiles_per_layer);
 // Counter words for a lattice of `layers` layers.
 inline int su3k_sweep_words(int layers) { return kSweepTickets + 8 * layers; }
-// One sweep: one launch, or (per_direction) four, one per direction mu with
-// its two half-sweeps, chained by programmatic dependent launch.  a.parity is
-// unused; a.meas must be null (sweeps that measure the plaquette run the
-// eight half-sweep kernels).
+// One sweep of the site-paired FP32 store: one launch (kOneLaunch); four, one
+// per direction mu with its two half-sweeps (kPerDirection); or eight, one
+// per half-sweep, each block's tile from its index (kChained); the launches
+// of a sweep chained by programmatic dependent launch.  a.parity is unused;
+// a.meas must be null (sweeps that measure the plaquette run the eight
+// half-sweep kernels).
+enum class SweepForm { kOneLaunch, kPerDirection, kChained };
 cudaError_t su3k_launch_sweep_pair(const HalfSweepArgs& a, const SweepQueue& q, bool eft, bool stats, int threads,
-                                   bool per_direction, cudaStream_t s);
+                                   SweepForm form, cudaStream_t s);
 // The FP64 sweep as four chained per-direction launches (k_sweep_f64), one
 // thread per link, loads through L2 (the links change during the launch).
 cudaError_t su3k_launch_sweep_f64(const HalfSweepArgs& a, const SweepQueue& q, bool stats, int threads, cudaStream_t s);

@@ -164,12 +164,69 @@ __global__ void __launch_bounds__(256, 2)
   report_sweep_item(qa, layers, it);
 }
 
+// One half-sweep (phase 2 MU + parity) of the chained sweep: one block per
+// tile, the tile from the block's index (su3_sweepq.cuh), waiting only for the
+// layers of the previous launch's half-sweep that its staples read.
+template <int MU, bool EFT, bool REPEAT>
+__global__ void __launch_bounds__(256, 2)
+    k_half_sweep_f32_chain(HalfSweepArgs args, SweepQueue qa, int tiles_per_layer, int layers, int stats, int parity) {
+  extern __shared__ float4 smem[];
+  __shared__ SweepItem s_item;
+  signal_dependents();
+  own_sweep_item(qa, 2 * MU + parity, tiles_per_layer, layers, &s_item);
+  __syncthreads();
+  const SweepItem it = s_item;
+  if (it.phase < 0) return;
+  const UpdateConsts uc{args.three_over_beta_f64, args.three_over_beta, args.max_tries};
+  const PairRing rg = pair_ring(smem);
+  const int j = it.tile * (int)blockDim.x + (int)threadIdx.x;  // layers are whole tiles: always a pair of the lattice
+  const UpdateCount c = pair_item<MU, EFT, REPEAT>(args, j, parity, *args.sweep, uc, rg);
+  if (stats) {
+    const int acc = __reduce_add_sync(0xffffffffu, c.accepted);
+    const int prop = __reduce_add_sync(0xffffffffu, c.proposed);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&args.stats[0], (unsigned long long)acc);
+      atomicAdd(&args.stats[1], (unsigned long long)prop);
+    }
+  }
+  report_sweep_item(qa, layers, it);
+}
+
+// The two chained launches of direction MU (the first of the sweep, MU = 0
+// even sites, is an ordinary launch).
+template <int MU, bool EFT, bool REPEAT>
+cudaError_t launch_chain_mu(const HalfSweepArgs& a, const SweepQueue& q, int tpl, int layers, int st, int threads,
+                            size_t smem, cudaStream_t s) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(tpl * layers);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  for (int p = 0; p < 2; ++p) {
+    cfg.numAttrs = MU == 0 && p == 0 ? 0 : 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_half_sweep_f32_chain<MU, EFT, REPEAT>, a, q, tpl, layers, st, p);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 template <bool EFT, bool REPEAT>
 cudaError_t launch_sweep(const HalfSweepArgs& a, const SweepQueue& q, int tpl, int layers, bool stats, int threads,
-                         bool per_direction, cudaStream_t s) {
+                         SweepForm form, cudaStream_t s) {
   const size_t smem = (size_t)kPairRingBytesPerThread * threads;
   const int st = stats ? 1 : 0;
-  if (!per_direction) {
+  if (form == SweepForm::kChained) {
+    cudaError_t e;
+    if ((e = launch_chain_mu<0, EFT, REPEAT>(a, q, tpl, layers, st, threads, smem, s)) != cudaSuccess) return e;
+    if ((e = launch_chain_mu<1, EFT, REPEAT>(a, q, tpl, layers, st, threads, smem, s)) != cudaSuccess) return e;
+    if ((e = launch_chain_mu<2, EFT, REPEAT>(a, q, tpl, layers, st, threads, smem, s)) != cudaSuccess) return e;
+    return launch_chain_mu<3, EFT, REPEAT>(a, q, tpl, layers, st, threads, smem, s);
+  }
+  if (form == SweepForm::kOneLaunch) {
     k_sweep_f32_pair<-1, EFT, REPEAT><<<8 * tpl * layers, threads, smem, s>>>(a, q, tpl, layers, st);
     return cudaGetLastError();
   }
@@ -214,6 +271,14 @@ template <bool EFT>
 cudaError_t prepare_all() {
   cudaError_t e;
   if ((e = set_smem(k_sweep_f32_pair<-1, EFT, false>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_half_sweep_f32_chain<0, EFT, false>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_half_sweep_f32_chain<1, EFT, false>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_half_sweep_f32_chain<2, EFT, false>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_half_sweep_f32_chain<3, EFT, false>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_half_sweep_f32_chain<0, EFT, true>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_half_sweep_f32_chain<1, EFT, true>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_half_sweep_f32_chain<2, EFT, true>)) != cudaSuccess) return e;
+  if ((e = set_smem(k_half_sweep_f32_chain<3, EFT, true>)) != cudaSuccess) return e;
   if ((e = set_smem(k_sweep_f32_pair<-1, EFT, true>)) != cudaSuccess) return e;
   if ((e = set_smem(k_sweep_f32_pair<0, EFT, false>)) != cudaSuccess) return e;
   if ((e = set_smem(k_sweep_f32_pair<1, EFT, false>)) != cudaSuccess) return e;
@@ -259,17 +324,17 @@ int su3k_pair_sweep_layers(const Geometry& gp, int threads, int* tiles_per_layer
 }
 
 cudaError_t su3k_launch_sweep_pair(const HalfSweepArgs& a, const SweepQueue& q, bool eft, bool stats, int threads,
-                                   bool per_direction, cudaStream_t s) {
+                                   SweepForm form, cudaStream_t s) {
   int tpl = 0;
   const int layers = su3k_pair_sweep_layers(a.pgeom, threads, &tpl);
   if (layers == 0) return cudaErrorInvalidValue;
   if (a.meas) return cudaErrorInvalidValue;  // measuring sweeps run the eight half-sweep kernels
   const bool rep = a.max_tries > 1;
   if (eft)
-    return rep ? launch_sweep<true, true>(a, q, tpl, layers, stats, threads, per_direction, s)
-               : launch_sweep<true, false>(a, q, tpl, layers, stats, threads, per_direction, s);
-  return rep ? launch_sweep<false, true>(a, q, tpl, layers, stats, threads, per_direction, s)
-             : launch_sweep<false, false>(a, q, tpl, layers, stats, threads, per_direction, s);
+    return rep ? launch_sweep<true, true>(a, q, tpl, layers, stats, threads, form, s)
+               : launch_sweep<true, false>(a, q, tpl, layers, stats, threads, form, s);
+  return rep ? launch_sweep<false, true>(a, q, tpl, layers, stats, threads, form, s)
+             : launch_sweep<false, false>(a, q, tpl, layers, stats, threads, form, s);
 }
 
 int su3k_pair_tile2(const Geometry& gp, int threads) {

@@ -1,5 +1,6 @@
-// su3_sweepq.cuh -- the work queue of the persistent sweeps (k_sweep_f32_pair
-// in su3_kernels_pair.cu, k_sweep_f64 in su3_kernels.cu).
+// su3_sweepq.cuh -- the work queue of the persistent and chained sweeps
+// (k_sweep_f32_pair and k_half_sweep_f32_chain in su3_kernels_pair.cu,
+// k_sweep_f64 in su3_kernels.cu).
 //
 // A persistent sweep runs the half-sweeps (mu, parity) of a sweep, in the
 // order of the paper's sweep (mu = 0..3, even then odd sites; checkerboard
@@ -41,6 +42,12 @@
 // phases inside a launch do.  Nothing of a launch waits for a later launch,
 // and a later launch's blocks start only when every block of the earlier one
 // is running or done, so the chain cannot deadlock either.
+//
+// Chained half-sweeps: eight launches per sweep, one per phase, chained the
+// same way.  A launch holds one phase only, so no tile waits on a tile of its
+// own launch; a block's item is its blockIdx (no counter), in the same
+// layer-rotated order, and waits only on the launch before, whose blocks have
+// all started when this launch's first block does.
 #pragma once
 
 #include "su3_device.cuh"
@@ -70,30 +77,23 @@ struct SweepItem {
   int phase, tile, layer, idx;
 };
 
-// Warp 0 takes the block's item from counter `ticket` of the queue (the
-// launch holds kPhases phases from kFirst on) and waits for the layers of
-// phase q-1 it reads; the item lands in *item (shared memory), which the
-// block reads after a __syncthreads.  Phase 0 follows the previous sweep in
-// stream order and waits for nothing.
-template <int kPhases, int kFirst>
-__device__ __forceinline__ void take_sweep_item(const SweepQueue& qa, int ticket, int tiles_per_layer, int layers,
-                                                SweepItem* item) {
-  if (threadIdx.x >= 32) return;
+// Item i of a phase (its place in the dispatch order) -> its x3 layer and
+// tile: the phase's tiles walk the layers starting at layer `phase`.
+__device__ __forceinline__ void sweep_tile_of(int phase, int i, int tiles_per_layer, int layers, int* layer, int* tile) {
+  const int il = i / tiles_per_layer;
+  *layer = (il + phase) % layers;
+  *tile = *layer * tiles_per_layer + (i - il * tiles_per_layer);
+}
+
+// Warp 0 (all 32 lanes) waits, with the bound, for the layers of phase q-1
+// that a tile of phase q in `layer` reads, then acquires; false in every lane
+// if the sweep stopped.  Phase 0 follows the previous sweep in stream order
+// and waits for nothing.
+__device__ __forceinline__ bool wait_sweep_layers(const SweepQueue& qa, int phase, int layer, int tiles_per_layer,
+                                                  int layers, bool ok) {
   const unsigned* const done = qa.counters + kSweepTickets;
-  const int tiles_per_phase = tiles_per_layer * layers;
-  const int lane = (int)threadIdx.x;
-  int idx = 0;
-  if (lane == 0) idx = (int)atomicAdd(qa.counters + ticket, 1u);
-  idx = __shfl_sync(0xffffffffu, idx, 0);
-  int phase = -1, tile = 0, layer = 0;
-  if (idx < kPhases * tiles_per_phase) {
-    phase = kFirst + idx / tiles_per_phase;
-    const int i = idx - (phase - kFirst) * tiles_per_phase;
-    const int il = i / tiles_per_layer;
-    layer = (il + phase) % layers;
-    tile = layer * tiles_per_layer + (i - il * tiles_per_layer);
-  }
-  bool ok = phase >= 0 && (lane != 0 || ld_relaxed_s32(qa.status) == 0);
+  const int lane = (int)threadIdx.x & 31;
+  ok = ok && (lane != 0 || ld_relaxed_s32(qa.status) == 0);
   const bool wait = phase > 0;
   if (wait && lane < 3) {
     // lane k waits for layer l + k - 1 of the previous phase
@@ -113,10 +113,41 @@ __device__ __forceinline__ void take_sweep_item(const SweepQueue& qa, int ticket
     }
   }
   ok = __all_sync(0xffffffffu, ok);
-  if (lane == 0) {
-    if (ok && wait) fence_acquire_gpu();
-    *item = SweepItem{ok ? phase : -1, tile, layer, idx};
+  if (lane == 0 && ok && wait) fence_acquire_gpu();
+  return ok;
+}
+
+// Warp 0 takes the block's item from counter `ticket` of the queue (the
+// launch holds kPhases phases from kFirst on) and waits for the layers of
+// phase q-1 it reads; the item lands in *item (shared memory), which the
+// block reads after a __syncthreads.
+template <int kPhases, int kFirst>
+__device__ __forceinline__ void take_sweep_item(const SweepQueue& qa, int ticket, int tiles_per_layer, int layers,
+                                                SweepItem* item) {
+  if (threadIdx.x >= 32) return;
+  const int tiles_per_phase = tiles_per_layer * layers;
+  const int lane = (int)threadIdx.x;
+  int idx = 0;
+  if (lane == 0) idx = (int)atomicAdd(qa.counters + ticket, 1u);
+  idx = __shfl_sync(0xffffffffu, idx, 0);
+  int phase = -1, tile = 0, layer = 0;
+  if (idx < kPhases * tiles_per_phase) {
+    phase = kFirst + idx / tiles_per_phase;
+    sweep_tile_of(phase, idx - (phase - kFirst) * tiles_per_phase, tiles_per_layer, layers, &layer, &tile);
   }
+  const bool ok = wait_sweep_layers(qa, phase, layer, tiles_per_layer, layers, phase >= 0);
+  if (lane == 0) *item = SweepItem{ok ? phase : -1, tile, layer, idx};
+}
+
+// The same for one half-sweep per launch (the chained half-sweep launches):
+// the item is the block's own index, no counter is taken.
+__device__ __forceinline__ void own_sweep_item(const SweepQueue& qa, int phase, int tiles_per_layer, int layers,
+                                               SweepItem* item) {
+  if (threadIdx.x >= 32) return;
+  int layer = 0, tile = 0;
+  sweep_tile_of(phase, (int)blockIdx.x, tiles_per_layer, layers, &layer, &tile);
+  const bool ok = wait_sweep_layers(qa, phase, layer, tiles_per_layer, layers, true);
+  if (threadIdx.x == 0) *item = SweepItem{ok ? phase : -1, tile, layer, (int)blockIdx.x};
 }
 
 // Reports the block's tile done once every thread's stores are issued.

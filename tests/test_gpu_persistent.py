@@ -30,7 +30,7 @@ def built():
     oracle.build()
 
 
-SCHEDS = [su3.SU3_SCHED_PERSISTENT, su3.SU3_SCHED_PER_DIRECTION]
+SCHEDS = [su3.SU3_SCHED_PERSISTENT, su3.SU3_SCHED_PER_DIRECTION, su3.SU3_SCHED_CHAINED]
 
 
 def pair(L, prec, seed, lanes=0, threads=0, schedule=su3.SU3_SCHED_PERSISTENT):
@@ -175,11 +175,11 @@ def test_persistent_sweep_matches_oracle_reading(prec):
 
 def test_automatic_schedule_follows_the_waves():
     # 16^4: 0.2 waves per half-sweep and 24^3 x 16: 0.7, eight launches;
-    # 24^4: 1.1 and 32^4: 3.4, one launch per direction; 32^3 x 64: 6.7,
-    # eight launches (waves on a GPU of 152 SMs)
+    # 24^4: 1.1, 32^4: 3.4 and 32^3 x 64: 6.7, the chained half-sweep
+    # launches (waves on a GPU of 152 SMs)
     for L, sched in (((16, 16, 16, 16), su3.SU3_SCHED_PHASES), ((24, 24, 24, 16), su3.SU3_SCHED_PHASES),
-                     ((24, 24, 24, 24), su3.SU3_SCHED_PER_DIRECTION), ((32, 32, 32, 32), su3.SU3_SCHED_PER_DIRECTION),
-                     ((32, 32, 32, 64), su3.SU3_SCHED_PHASES)):
+                     ((24, 24, 24, 24), su3.SU3_SCHED_CHAINED), ((32, 32, 32, 32), su3.SU3_SCHED_CHAINED),
+                     ((32, 32, 32, 64), su3.SU3_SCHED_CHAINED)):
         with su3.Lattice(L, BETA, 1, precision=su3.SU3_FP32_MIXED) as lat:
             assert lat.schedule == sched, L
     # FP64 (384 links per SM in flight): 16^4 0.6 waves, 24^4 2.8, 32^4 9.0
@@ -203,9 +203,10 @@ def test_schedule_applies_where_documented():
                 assert e.value.code == su3.SU3_EINVAL
     # FP64: one launch per direction only
     with su3.Lattice((16, 16, 16, 16), BETA, 1, precision=su3.SU3_FP64) as lat:
-        with pytest.raises(su3.Su3Error) as e:
-            lat.set_schedule(su3.SU3_SCHED_PERSISTENT)
-        assert e.value.code == su3.SU3_EINVAL
+        for sched in (su3.SU3_SCHED_PERSISTENT, su3.SU3_SCHED_CHAINED):
+            with pytest.raises(su3.Su3Error) as e:
+                lat.set_schedule(sched)
+            assert e.value.code == su3.SU3_EINVAL
         lat.set_schedule(su3.SU3_SCHED_PER_DIRECTION)
         assert lat.schedule == su3.SU3_SCHED_PER_DIRECTION
     with su3.Lattice((16, 16, 16, 16), BETA, 1, precision=su3.SU3_FP32_MIXED) as lat:
@@ -233,16 +234,19 @@ def test_schedule_applies_where_documented():
 # lattice's 16^4 / 4 / 128 = 128 tiles per phase) the first tile of phase 1
 # (mu = 0, odd sites), which in the per-direction form is waited on only by
 # the next launch, the programmatic dependent launch of mu = 1.
-@pytest.mark.parametrize("item", [0, 128])
-@pytest.mark.parametrize("sched,prec", [(su3.SU3_SCHED_PERSISTENT, su3.SU3_FP32_MIXED),
-                                        (su3.SU3_SCHED_PER_DIRECTION, su3.SU3_FP32_MIXED),
-                                        (su3.SU3_SCHED_PER_DIRECTION, su3.SU3_FP64)])
+# The chained half-sweep launches number each launch's tiles by block index:
+# item 0 is the first tile of every half-sweep, and the wait on it lies in the
+# next launch.  FP64: 16^4 / 2 / 128 = 256 tiles per phase, so item 256 is the
+# first of phase 1.
+@pytest.mark.parametrize("sched,prec,item", [(su3.SU3_SCHED_PERSISTENT, su3.SU3_FP32_MIXED, 0),
+                                             (su3.SU3_SCHED_PERSISTENT, su3.SU3_FP32_MIXED, 128),
+                                             (su3.SU3_SCHED_PER_DIRECTION, su3.SU3_FP32_MIXED, 0),
+                                             (su3.SU3_SCHED_PER_DIRECTION, su3.SU3_FP32_MIXED, 128),
+                                             (su3.SU3_SCHED_CHAINED, su3.SU3_FP32_MIXED, 0),
+                                             (su3.SU3_SCHED_PER_DIRECTION, su3.SU3_FP64, 0),
+                                             (su3.SU3_SCHED_PER_DIRECTION, su3.SU3_FP64, 256)])
 def test_withheld_tile_times_out_without_fault(sched, prec, item):
-    # FP64: 16^4 / 2 / 128 = 256 tiles per phase, so item 128 lies in phase 0
-    # too (waited on inside the launch); item 256 is the first of phase 1
     L = (16, 16, 16, 16)
-    if prec == su3.SU3_FP64 and item:
-        item = 256
     with su3.Lattice(L, BETA, 2, precision=prec) as lat:
         lat.set_block_size(128)
         lat.set_schedule(sched)
