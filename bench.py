@@ -83,31 +83,31 @@ def peaks():
 # stripped).  A line reports the figure only while that code still hashes the
 # same; otherwise its traffic is null and the line says why.
 _U_F64, _U_F32, _U_BATCH = ("su3_kernels.cu",), ("su3_kernels.cu", "su3_kernels_pair.cu"), ("su3_batch.cu",)
-_SHA_F64 = "ce1ad7fc7b0cad21bbafe14d30eaa2670bedf711664835805d27385c4aa695b7"
-_SHA_F32 = "6563943ce31cb7116153c8475450555ab8238d9ff8b16a9ad8b3006ebd2fdecf"
-_SHA_BATCH = "90e590e6418988950392eef43f6199eec6399d26f672b43789d400fa1dd054a6"
+_SHA_F64 = "bc2fc81987d68cacce2cddcfc3e85f43b65d65b6e7b608794c49e6dc2e84e4de"
+_SHA_F32 = "83217854b97956506f625ddf58573e28304cedc22db9ba3edab7c2e21e87d4bc"
+_SHA_BATCH = "d9029b824bda46a252b5670089d82c5b7d10b27581aefd95730e21efa98e8ad2"
 _NCU_METRICS = "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none"
 NCU_TRAFFIC = {
     # one launch of the default 32^4 FP32 sweep = one chained half-sweep; the mean of the eight launches of
     # the second sweep
-    "fp32_mixed": {"bytes": 0, "units": _U_F32, "sources_sha256": "",
+    "fp32_mixed": {"bytes": 209044832 + 12846112, "units": _U_F32, "sources_sha256": _SHA_F32,
                    "capture": _NCU_METRICS + " -k regex:k_half_sweep_f32_chain -s 8 -c 8 python bench.py --profile "
                                              "fp32_mixed"},
-    "fp32_eft": {"bytes": 0, "units": _U_F32, "sources_sha256": "",
+    "fp32_eft": {"bytes": 209055200 + 13582624, "units": _U_F32, "sources_sha256": _SHA_F32,
                  "capture": _NCU_METRICS + " -k regex:k_half_sweep_f32_chain -s 8 -c 8 python bench.py --profile "
                                            "fp32_eft"},
-    "fp32_mixed_phases": {"bytes": 207860224 + 14739200, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_mixed_phases": {"bytes": 207742464 + 15238400, "units": _U_F32, "sources_sha256": _SHA_F32,
                           "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile "
                                                     "fp32_mixed_phases"},
-    "fp32_eft_phases": {"bytes": 207870720 + 15619840, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_eft_phases": {"bytes": 207814656 + 15916800, "units": _U_F32, "sources_sha256": _SHA_F32,
                         "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile "
                                                   "fp32_eft_phases"},
-    "fp64": {"bytes": 624128000 + 64891392, "units": _U_F64, "sources_sha256": _SHA_F64,
+    "fp64": {"bytes": 623182848 + 64833024, "units": _U_F64, "sources_sha256": _SHA_F64,
              "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile fp64"},
-    "batched": {"bytes": 2831965440 + 442514432, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
+    "batched": {"bytes": 2830772736 + 442051584, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
                 "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 4 -c 4 python bench.py --profile batched "
                                           "(the four launches of the second sweep, summed)"},
-    "batched_eft": {"bytes": 2836656128 + 441758464, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
+    "batched_eft": {"bytes": 2829066240 + 442415616, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
                     "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 4 -c 4 python bench.py --profile batched_eft "
                                               "(the four launches of the second sweep, summed)"},
 }
