@@ -221,7 +221,8 @@ SU3_API int su3_set_lanes(su3_handle h, int lanes);
  *   SU3_SCHED_CHAINED: eight half-sweep launches chained the same way, a
  *     block's tile given by its index (no counter), each tile waiting only
  *     for the layers of the previous half-sweep it reads (site-paired FP32
- *     stores, where SU3_SCHED_PERSISTENT applies);
+ *     stores where SU3_SCHED_PERSISTENT applies, FP64 stores where
+ *     SU3_SCHED_PER_DIRECTION does);
  *   SU3_SCHED_AUTO (the default): where they apply, SU3_SCHED_CHAINED for
  *     the site-paired FP32 store when one half-sweep is 1 to 10 waves of the
  *     GPU, w = (V/4 pairs) / (512 x SMs) (24^4: +15 % mixed, +17 % EFT;

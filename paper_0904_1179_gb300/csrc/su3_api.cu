@@ -209,8 +209,8 @@ int auto_schedule(const su3_lattice* h) {
 // Whether a schedule other than eight independent launches applies to h.
 bool schedule_applies(const su3_lattice* h, int schedule) {
   switch (schedule) {
-    case SU3_SCHED_PERSISTENT:
-    case SU3_SCHED_CHAINED: return pair_persistent_applies(h);
+    case SU3_SCHED_PERSISTENT: return pair_persistent_applies(h);
+    case SU3_SCHED_CHAINED:
     case SU3_SCHED_PER_DIRECTION: return persistent_applies(h);
     default: return true;
   }
@@ -263,7 +263,9 @@ int enqueue_sweep_body(su3_lattice* h, bool measured) {
     SU3_CUDA(cudaMemsetAsync(h->d_pq, 0, (size_t)h->pq_words * sizeof(unsigned int), h->stream),
              "sweep counters reset");
     if (h->precision == SU3_FP64)
-      SU3_CUDA(su3k_launch_sweep_f64(a, q, h->stats_on, h->threads, h->stream), "persistent sweep launch");
+      SU3_CUDA(su3k_launch_sweep_f64(a, q, h->stats_on, h->threads, effective_schedule(h) == SU3_SCHED_CHAINED,
+                                     h->stream),
+               "persistent sweep launch");
     else
       SU3_CUDA(su3k_launch_sweep_pair(a, q, h->precision == SU3_FP32_EFT, h->stats_on, h->threads,
                                       effective_schedule(h) == SU3_SCHED_CHAINED        ? SweepForm::kChained
@@ -688,7 +690,7 @@ int su3_set_schedule(su3_handle h, int schedule) {
     return fail(SU3_EINVAL,
                 "su3_set_schedule: the persistent and chained sweeps need one thread per link (pair) and x3 layers "
                 "of whole blocks: the site-paired FP32 store (L3 >= 8, the natural block order; all forms) or the "
-                "FP64 store (L3 >= 4; one launch per direction)");
+                "FP64 store (L3 >= 4; per direction or chained half-sweeps)");
   if (schedule != h->schedule) {
     SU3_CUDA(cudaStreamSynchronize(h->stream), "su3_set_schedule");
     drop_graphs(h);

@@ -99,6 +99,27 @@ __global__ void __launch_bounds__(kMaxSweepThreads)
   report_sweep_item(qa, layers, it);
 }
 
+// One FP64 half-sweep (phase 2 MU + parity) of the chained sweep: one block
+// per tile of sites of one x3 layer, the tile from the block's index
+// (su3_sweepq.cuh), waiting only for the layers of the previous launch's
+// half-sweep that its staples read.
+template <int MU, bool REPEAT>
+__global__ void __launch_bounds__(kMaxSweepThreads)
+    k_half_sweep_f64_chain(HalfSweepArgs args, SweepQueue qa, int tiles_per_layer, int layers, int stats, int parity) {
+  __shared__ SweepItem s_item;
+  signal_dependents();
+  own_sweep_item(qa, 2 * MU + parity, tiles_per_layer, layers, &s_item);
+  __syncthreads();
+  const SweepItem it = s_item;
+  if (it.phase < 0) return;
+  const UpdateConsts uc{args.three_over_beta_f64, args.three_over_beta, args.max_tries};
+  const int h = it.tile * (int)blockDim.x + (int)threadIdx.x;  // layers are whole tiles: always a site of the lattice
+  const UpdateCount c =
+      update_link_f64<MU, true, REPEAT, false>(args.geom, (double2*)args.links, h, parity, *args.sweep, args.key, uc);
+  if (stats) count_stats<true>(c, args.stats);
+  report_sweep_item(qa, layers, it);
+}
+
 // A small lattice's half-sweep has too few links to fill the GPU, and each
 // link's FP64 update is a long dependent chain: the time is its latency.
 // Here four lanes share one link: lanes 0, 1, 2 compute rows 0,1 of the two
@@ -487,10 +508,37 @@ __global__ void k_store_to_canon(ConvArgs args) {
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
+template <int MU, bool REPEAT>
+static cudaError_t launch_chain_f64_mu(const HalfSweepArgs& a, const SweepQueue& q, int tpl, int layers, int st,
+                                       int threads, cudaStream_t s) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(tpl * layers);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  for (int p = 0; p < 2; ++p) {
+    cfg.numAttrs = MU == 0 && p == 0 ? 0 : 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_half_sweep_f64_chain<MU, REPEAT>, a, q, tpl, layers, st, p);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 template <bool REPEAT>
 static cudaError_t launch_sweep_f64(const HalfSweepArgs& a, const SweepQueue& q, int tpl, int layers, bool stats,
-                                    int threads, cudaStream_t s) {
+                                    int threads, bool chained, cudaStream_t s) {
   const int blocks = 2 * tpl * layers, st = stats ? 1 : 0;
+  if (chained) {
+    cudaError_t e;
+    if ((e = launch_chain_f64_mu<0, REPEAT>(a, q, tpl, layers, st, threads, s)) != cudaSuccess) return e;
+    if ((e = launch_chain_f64_mu<1, REPEAT>(a, q, tpl, layers, st, threads, s)) != cudaSuccess) return e;
+    if ((e = launch_chain_f64_mu<2, REPEAT>(a, q, tpl, layers, st, threads, s)) != cudaSuccess) return e;
+    return launch_chain_f64_mu<3, REPEAT>(a, q, tpl, layers, st, threads, s);
+  }
   k_sweep_f64<0, REPEAT><<<blocks, threads, 0, s>>>(a, q, tpl, layers, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -580,12 +628,13 @@ int su3k_f64_sweep_layers(const Geometry& g, int threads, int* tiles_per_layer) 
   return g.L3;
 }
 
-cudaError_t su3k_launch_sweep_f64(const HalfSweepArgs& a, const SweepQueue& q, bool stats, int threads, cudaStream_t s) {
+cudaError_t su3k_launch_sweep_f64(const HalfSweepArgs& a, const SweepQueue& q, bool stats, int threads, bool chained,
+                                  cudaStream_t s) {
   int tpl = 0;
   const int layers = su3k_f64_sweep_layers(a.geom, threads, &tpl);
   if (layers == 0 || a.meas || a.split) return cudaErrorInvalidValue;
-  return a.max_tries > 1 ? launch_sweep_f64<true>(a, q, tpl, layers, stats, threads, s)
-                         : launch_sweep_f64<false>(a, q, tpl, layers, stats, threads, s);
+  return a.max_tries > 1 ? launch_sweep_f64<true>(a, q, tpl, layers, stats, threads, chained, s)
+                         : launch_sweep_f64<false>(a, q, tpl, layers, stats, threads, chained, s);
 }
 
 cudaError_t su3k_launch_half_sweep(const HalfSweepArgs& a, int mu, int precision, bool stats, int threads, cudaStream_t s) {

@@ -107,9 +107,11 @@ inline int su3k_sweep_words(int layers) { return kSweepTickets + 8 * layers; }
 enum class SweepForm { kOneLaunch, kPerDirection, kChained };
 cudaError_t su3k_launch_sweep_pair(const HalfSweepArgs& a, const SweepQueue& q, bool eft, bool stats, int threads,
                                    SweepForm form, cudaStream_t s);
-// The FP64 sweep as four chained per-direction launches (k_sweep_f64), one
-// thread per link, loads through L2 (the links change during the launch).
-cudaError_t su3k_launch_sweep_f64(const HalfSweepArgs& a, const SweepQueue& q, bool stats, int threads, cudaStream_t s);
+// The FP64 sweep as four chained per-direction launches (k_sweep_f64) or,
+// with `chained`, eight chained half-sweep launches (k_half_sweep_f64_chain);
+// one thread per link, loads through L2 (the links change during the launch).
+cudaError_t su3k_launch_sweep_f64(const HalfSweepArgs& a, const SweepQueue& q, bool stats, int threads, bool chained,
+                                  cudaStream_t s);
 
 // Status words of the bounds-checked build, one per translation unit with
 // kernels (su3_device.cuh, link_ok); 0 in the product build.

@@ -72,10 +72,11 @@ def test_persistent_sweep_equals_eight_kernels(L, lanes, prec, sched):
 # 12^3 x 8 (8 layers of 864 sites: 27 tiles of 32), 16^4, 32^4 (the bench
 # lattice: 32 layers of 128 tiles of 128); one thread per link (the
 # four-lane form of the smallest lattices is switched off).
+@pytest.mark.parametrize("sched", [su3.SU3_SCHED_PER_DIRECTION, su3.SU3_SCHED_CHAINED])
 @pytest.mark.parametrize("L,threads", [((8, 8, 8, 4), 128), ((12, 12, 12, 8), 32), ((16, 16, 16, 16), 0),
                                        ((32, 32, 32, 32), 0)])
-def test_fp64_per_direction_equals_eight_kernels(L, threads):
-    a, b = pair(L, su3.SU3_FP64, 23, lanes=1, threads=threads, schedule=su3.SU3_SCHED_PER_DIRECTION)
+def test_fp64_per_direction_equals_eight_kernels(L, threads, sched):
+    a, b = pair(L, su3.SU3_FP64, 23, lanes=1, threads=threads, schedule=sched)
     with a, b:
         for lat in (a, b):
             lat.set_stats(True)
@@ -201,14 +202,14 @@ def test_schedule_applies_where_documented():
                 with pytest.raises(su3.Su3Error) as e:
                     lat.set_schedule(sched)
                 assert e.value.code == su3.SU3_EINVAL
-    # FP64: one launch per direction only
+    # FP64: per direction or chained half-sweeps, not one launch per sweep
     with su3.Lattice((16, 16, 16, 16), BETA, 1, precision=su3.SU3_FP64) as lat:
-        for sched in (su3.SU3_SCHED_PERSISTENT, su3.SU3_SCHED_CHAINED):
-            with pytest.raises(su3.Su3Error) as e:
-                lat.set_schedule(sched)
-            assert e.value.code == su3.SU3_EINVAL
-        lat.set_schedule(su3.SU3_SCHED_PER_DIRECTION)
-        assert lat.schedule == su3.SU3_SCHED_PER_DIRECTION
+        with pytest.raises(su3.Su3Error) as e:
+            lat.set_schedule(su3.SU3_SCHED_PERSISTENT)
+        assert e.value.code == su3.SU3_EINVAL
+        for sched in (su3.SU3_SCHED_PER_DIRECTION, su3.SU3_SCHED_CHAINED):
+            lat.set_schedule(sched)
+            assert lat.schedule == sched
     with su3.Lattice((16, 16, 16, 16), BETA, 1, precision=su3.SU3_FP32_MIXED) as lat:
         with pytest.raises(su3.Su3Error):
             lat.set_schedule(7)
@@ -244,7 +245,8 @@ def test_schedule_applies_where_documented():
                                              (su3.SU3_SCHED_PER_DIRECTION, su3.SU3_FP32_MIXED, 128),
                                              (su3.SU3_SCHED_CHAINED, su3.SU3_FP32_MIXED, 0),
                                              (su3.SU3_SCHED_PER_DIRECTION, su3.SU3_FP64, 0),
-                                             (su3.SU3_SCHED_PER_DIRECTION, su3.SU3_FP64, 256)])
+                                             (su3.SU3_SCHED_PER_DIRECTION, su3.SU3_FP64, 256),
+                                             (su3.SU3_SCHED_CHAINED, su3.SU3_FP64, 0)])
 def test_withheld_tile_times_out_without_fault(sched, prec, item):
     L = (16, 16, 16, 16)
     with su3.Lattice(L, BETA, 2, precision=prec) as lat:
