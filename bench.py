@@ -83,26 +83,26 @@ def peaks():
 # stripped).  A line reports the figure only while that code still hashes the
 # same; otherwise its traffic is null and the line says why.
 _U_F64, _U_F32, _U_BATCH = ("su3_kernels.cu",), ("su3_kernels.cu", "su3_kernels_pair.cu"), ("su3_batch.cu",)
-_SHA_F64 = "bc2fc81987d68cacce2cddcfc3e85f43b65d65b6e7b608794c49e6dc2e84e4de"
-_SHA_F32 = "83217854b97956506f625ddf58573e28304cedc22db9ba3edab7c2e21e87d4bc"
+_SHA_F64 = "885129abed2f07dcf526279300c7e616b6ab6d05d7f194316ac183375be7f880"
+_SHA_F32 = "b69b3efb95b8c7b71cd98f8e15af6aec0aaf08bce33ea207b3a093f079754790"
 _SHA_BATCH = "d9029b824bda46a252b5670089d82c5b7d10b27581aefd95730e21efa98e8ad2"
 _NCU_METRICS = "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none"
 NCU_TRAFFIC = {
     # one launch of the default 32^4 FP32 sweep = one chained half-sweep; the mean of the eight launches of
     # the second sweep
-    "fp32_mixed": {"bytes": 209044832 + 12846112, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_mixed": {"bytes": 208961760 + 12656192, "units": _U_F32, "sources_sha256": _SHA_F32,
                    "capture": _NCU_METRICS + " -k regex:k_half_sweep_f32_chain -s 8 -c 8 python bench.py --profile "
                                              "fp32_mixed"},
-    "fp32_eft": {"bytes": 209055200 + 13582624, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_eft": {"bytes": 208966496 + 13336640, "units": _U_F32, "sources_sha256": _SHA_F32,
                  "capture": _NCU_METRICS + " -k regex:k_half_sweep_f32_chain -s 8 -c 8 python bench.py --profile "
                                            "fp32_eft"},
-    "fp32_mixed_phases": {"bytes": 207742464 + 15238400, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_mixed_phases": {"bytes": 207816192 + 15345664, "units": _U_F32, "sources_sha256": _SHA_F32,
                           "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile "
                                                     "fp32_mixed_phases"},
-    "fp32_eft_phases": {"bytes": 207814656 + 15916800, "units": _U_F32, "sources_sha256": _SHA_F32,
+    "fp32_eft_phases": {"bytes": 207962880 + 15926528, "units": _U_F32, "sources_sha256": _SHA_F32,
                         "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile "
                                                   "fp32_eft_phases"},
-    "fp64": {"bytes": 623182848 + 64833024, "units": _U_F64, "sources_sha256": _SHA_F64,
+    "fp64": {"bytes": 624059904 + 64907520, "units": _U_F64, "sources_sha256": _SHA_F64,
              "capture": _NCU_METRICS + " -k regex:k_half_sweep -s 8 -c 1 python bench.py --profile fp64"},
     "batched": {"bytes": 2830772736 + 442051584, "units": _U_BATCH, "sources_sha256": _SHA_BATCH,
                 "capture": _NCU_METRICS + " -k regex:k_batch_sweep -s 4 -c 4 python bench.py --profile batched "
