@@ -99,13 +99,17 @@ cudaError_t launch_pair_mu(const HalfSweepArgs& a, bool stats, int threads, cuda
 }
 
 // ---------------------------------------------------------------------------
-// The persistent sweep.  Each of the eight half-sweep launches of a sweep
-// leaves its SMs partly idle while its last blocks drain and the next launch
-// ramps up (at 32^4, 3.4 waves of 152 SMs x 4 blocks, the SMs hold no warp
-// for about a tenth of each launch).  Here the tiles of the half-sweeps are
-// handed out from a device counter, each waiting only for the x3 layers of
-// the pair lattice that its staples read (su3_sweepq.cuh; on the pair
-// lattice a step across the x3 boundary stays in a neighbouring layer).
+// The persistent and chained sweeps.  Each of the eight half-sweep launches
+// of a sweep leaves its SMs partly idle while its last blocks drain and the
+// next launch ramps up (at 32^4, 3.4 waves of 152 SMs x 4 blocks, the SMs
+// hold no warp for about a tenth of each launch).  Here a tile of a
+// half-sweep waits only for the x3 layers of the pair lattice that its
+// staples read, so the next half-sweep's tiles fill the SMs while the
+// previous one drains (su3_sweepq.cuh; on the pair lattice a step across the
+// x3 boundary stays in a neighbouring layer): the tiles handed out from a
+// device counter in one persistent launch per sweep or per direction
+// (k_sweep_f32_pair), or taken by block index in eight chained launches
+// (k_half_sweep_f32_chain, the default).
 // ---------------------------------------------------------------------------
 
 template <int MU, bool EFT, bool REPEAT>
@@ -234,7 +238,7 @@ cudaError_t launch_sweep(const HalfSweepArgs& a, const SweepQueue& q, int tpl, i
   k_sweep_f32_pair<0, EFT, REPEAT><<<blocks, threads, smem, s>>>(a, q, tpl, layers, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // directions 1-3: programmatic dependent launches (see the section comment)
+  // directions 1-3: programmatic dependent launches (su3_sweepq.cuh)
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
