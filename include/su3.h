@@ -246,9 +246,11 @@ SU3_API int su3_get_schedule(su3_handle h, int* schedule);
 
 /* Fault-detection hook of the persistent sweep (single lattices), as
  * su3_batch_debug for batches: wait_limit_s (0 < limit <= 60) bounds each
- * wait (default 2 s); withhold_item >= 0 makes that work item (in dispatch
- * order: phase * tiles per phase + position) never report completion, so
- * that the waits on it run out; -1 disables withholding. */
+ * wait (default 2 s); withhold_item >= 0 makes that work item of every
+ * launch of the sweep (in the launch's dispatch order, from 0: phase *
+ * tiles per phase + position for the phases the launch holds; a chained
+ * half-sweep's tiles by block index) never report completion, so that the
+ * waits on it run out; -1 disables withholding. */
 SU3_API int su3_sweep_debug(su3_handle h, double wait_limit_s, int withhold_item);
 
 /* ---------------------------------------------------------------------------
