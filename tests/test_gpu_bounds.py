@@ -2,8 +2,8 @@
 load and store of every kernel checks its direction, parity and index against
 the extent of the store it addresses -- the single lattice, one replica of a
 batch, one sublattice's extended box -- and records, never traps, an access
-out of range.  The decomposed, batched and single-lattice parity cases run
-through it in a separate process; no access may be out of range, and the
+out of range.  The decomposed, batched and single-lattice parity cases, and
+the persistent and chained schedules, run through it in a separate process; no access may be out of range, and the
 results must equal those of the product build (the checks change no
 arithmetic)."""
 import json
@@ -49,6 +49,19 @@ for L in [(4, 4, 4, 4), (6, 4, 10, 8), (10, 14, 6, 10), (2, 2, 2, 2), (8, 8, 8, 
             U = lat.get_links()
             lat.set_links(U)
             out["plain %%s %%d" %% (L, prec)] = lat.plaquette()
+# the persistent and chained schedules (one lane per link; 8 x3 layers of the
+# pair lattice, or 16 of the FP64 lattice, in tiles of 64)
+for prec in P:
+    with su3.Lattice((8, 8, 8, 16), 5.7, 4, start=su3.SU3_HOT, precision=prec) as lat:
+        lat.set_lanes(1)
+        lat.set_block_size(64)
+        scheds = [su3.SU3_SCHED_CHAINED, su3.SU3_SCHED_PER_DIRECTION]
+        if prec != su3.SU3_FP64:
+            scheds.append(su3.SU3_SCHED_PERSISTENT)
+        for sched in scheds:
+            lat.set_schedule(sched)
+            lat.sweep(1)
+        out["schedules %%d" %% prec] = lat.plaquette()
 # decomposed lattices, every sublattice and ghost layer
 for dec in [(1, 2, 1), (2, 2, 1), (3, 2, 1), (4, 2, 1), (2, 4, 1), (1, 1, 0)]:
     for prec in P:
